@@ -1,0 +1,407 @@
+/*
+ * CPU oracle for the population-dynamics (cloning) estimator of psi(s) for the
+ * activity of the symmetric simple exclusion process (SSEP) on a ring.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain, obviously-correct
+ * statement of what the GPU path computes.  Only tests/, the smoke check and the
+ * CPU-baseline leg of the benchmark may load it; the product library never does,
+ * and this file shares no code, header, table or constant generator with it.
+ *
+ * What it follows (arXiv:1711.05095, Brewer, Clark, Bradford, Jack):
+ *   - Sec. 2.3 "Cloning algorithm": N_c clones, M = t_obs/dt intervals, each a
+ *     dynamical stage followed by a cloning stage; eq. (upsbdef) per-interval
+ *     weight; eq. (psihat) estimator of psi.
+ *   - Sec. 3.1: SSEP on a ring of L sites, N particles, every particle hops with
+ *     rate 1 to each empty neighbour; the activity K counts successful hops.
+ *   - Sec. 4 (first paragraph): BKL continuous-time Monte Carlo.
+ *   - Sec. 4.1, eq. (alpha-Ups): [eq] clone selection with one shared d in (0,1).
+ *   - Sec. 4.2, eq. (khat): the cumulative K is carried with the clone.
+ *
+ * The lattice is held here as one byte per site (n_i in {0,1}); the GPU path
+ * uses packed bitmasks.  Conversion between the two is done by the tests.
+ *
+ * Readings of points the paper leaves open (each also listed in the design notes):
+ *   R1 random numbers: Philox4x32-10 (Salmon et al., SC'11) replaces the paper's
+ *      Mersenne Twister.  key = 64-bit seed; counter = (c0, c1, c2, c3):
+ *        init     (site t, 0,    slot j, 1)
+ *        evolve   (draw e, beta, slot j, 2)   beta = 1..M, e = 0,1,... per interval
+ *        resample (0,      beta, 0,      3)
+ *      The slot j is the clone's position in the population, after resampling.
+ *   R2 exponential variate: u = (2*w0 + 1) / 2^33 from the first output word;
+ *      E = -ln(u) by the FP32 logarithm defined in neg_ln_u() below (written from
+ *      ln(m 2^n) = n ln 2 + 2 atanh((m-1)/(m+1)); no library log).
+ *   R3 time arithmetic in FP32: tau = E * (1/r) with 1/r rounded to float,
+ *      t_new = t + tau; the interval ends when t_new >= (float)dt (no hop).
+ *   R4 bond choice: k = floor(U64 * r / 2^64) with U64 = w3*2^32 + w2; the hop is
+ *      across the k-th active bond counted from bond 0; bond i joins sites i and
+ *      (i+1) mod L and is active when exactly one of the two is occupied.
+ *   R5 initial condition: a uniform N-subset of the L sites per clone, by
+ *      selection sampling (site t taken iff floor(U64*(L-t)/2^64) < N - taken).
+ *   R6 fixed-point weights: F = 61 - ceil(log2 N_c); k_ref = min dK (s >= 0) or
+ *      max dK (s < 0); w = nearest-integer(2^F exp(-|s| |dK - k_ref|)), computed
+ *      with FP64 exp; |dK - k_ref| >= 4096 is a range error.  The quantised
+ *      weights only steer selection; the psi term uses exact FP64 (eq. psihat).
+ *   R7 [eq] selection with exact integers: d = (2U+1)/2^33 with U the resample
+ *      word; alpha_j = floor((2^33 j + 2U + 1) T / (2^33 N_c)) for j = 0..N_c-1;
+ *      the ancestor is the 0-based k with S_k <= alpha_j < S_{k+1}, S the
+ *      exclusive prefix sums of the weights (the printed index is off by one).
+ *
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared (see oracle/build.py).
+ * Contraction must stay off: every float operation below is a separately rounded
+ * IEEE-754 operation, or an explicit fmaf().
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_TAG_INIT 1u
+#define ORC_TAG_EVOLVE 2u
+#define ORC_TAG_RESAMPLE 3u
+#define ORC_KCAP 4096
+
+#define ORC_OK 0
+#define ORC_ERR_ARG -1
+#define ORC_ERR_RANGE -3
+
+typedef unsigned __int128 u128;
+
+/* ---------------------------------------------------------------------------
+ * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+ * as 1, 2, 3", SC'11): ten rounds of the Philox S-box with the two published
+ * round multipliers, the key advanced by the two Weyl constants between rounds.
+ * ------------------------------------------------------------------------- */
+void orc_philox(const uint32_t ctr[4], uint64_t seed, uint32_t out[4]) {
+  uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+  uint32_t k0 = (uint32_t)(seed & 0xffffffffu);
+  uint32_t k1 = (uint32_t)(seed >> 32);
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t y0 = hi1 ^ x1 ^ k0;
+    uint32_t y1 = lo1;
+    uint32_t y2 = hi0 ^ x3 ^ k1;
+    uint32_t y3 = lo0;
+    x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+  }
+  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+static void philox_at(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                      uint64_t seed, uint32_t out[4]) {
+  uint32_t ctr[4] = {c0, c1, c2, c3};
+  orc_philox(ctr, seed, out);
+}
+
+/* floor(a * b / 2^64) for 64-bit a, b */
+static uint64_t mul_hi_64(uint64_t a, uint64_t b) {
+  return (uint64_t)(((u128)a * (u128)b) >> 64);
+}
+
+/* ---------------------------------------------------------------------------
+ * Reading R2: E = -ln(u), u = (2w+1)/2^33, in FP32.
+ * v = 2w+1 is rounded once to float (round-to-nearest-even), v = m 2^e with m in
+ * [1,2), folded to m in (sqrt(1/2), sqrt(2)].  Then
+ *   ln u = (e - 33) ln 2 + ln m,   ln m = 2 atanh(f),  f = (m-1)/(m+1),
+ *   2 atanh(f) = f (2 + 2/3 z + 2/5 z^2 + 2/7 z^3 + 2/9 z^4 + ...),  z = f^2,
+ * truncated after the z^4 term (|f| <= 0.1716, so the first dropped term is
+ * below 1e-9 relative).  ln 2 is split into a 15-bit head (exact products with
+ * |e-33| <= 33) and a float tail.
+ * ------------------------------------------------------------------------- */
+static const float ORC_SQRT2 = 0x1.6a09e6p+0f;
+static const float ORC_LN2_HI = 0x1.62e4p-1f;
+static const float ORC_LN2_LO = 0x1.7f7d1cp-20f;
+static const float ORC_C3 = 0x1.555556p-1f; /* 2/3 */
+static const float ORC_C5 = 0x1.99999ap-2f; /* 2/5 */
+static const float ORC_C7 = 0x1.24924ap-2f; /* 2/7 */
+static const float ORC_C9 = 0x1.c71c72p-3f; /* 2/9 */
+
+float orc_neg_ln_u(uint32_t w) {
+  uint64_t v = 2u * (uint64_t)w + 1u;
+  float vf = (float)v;
+  uint32_t bits;
+  memcpy(&bits, &vf, sizeof bits);
+  int e = (int)((bits >> 23) & 0xffu) - 127;
+  uint32_t mbits = (bits & 0x007fffffu) | 0x3f800000u;
+  float m;
+  memcpy(&m, &mbits, sizeof m);
+  if (m > ORC_SQRT2) {
+    m = m * 0.5f;
+    e += 1;
+  }
+  float f = (m - 1.0f) / (m + 1.0f);
+  float z = f * f;
+  float p = fmaf(ORC_C9, z, ORC_C7);
+  p = fmaf(p, z, ORC_C5);
+  p = fmaf(p, z, ORC_C3);
+  p = fmaf(p, z, 2.0f);
+  float ln_m = f * p;
+  float n = (float)(e - 33);
+  float ln_u = fmaf(n, ORC_LN2_LO, ln_m);
+  ln_u = fmaf(n, ORC_LN2_HI, ln_u);
+  return -ln_u;
+}
+
+/* ---------------------------------------------------------------------------
+ * Reading R5: initial configurations, independent uniform N-subsets per clone
+ * (steady state of the SSEP at fixed N: Sec. 2.1 takes the initial condition from
+ * the steady state; Sec. 3.1 says that state is uniform).
+ * sites: n_clones * L bytes, clone-major.  K is set to zero.
+ * ------------------------------------------------------------------------- */
+int orc_init(int32_t L, int32_t N, int64_t n_clones, uint64_t seed,
+             uint8_t* sites, int32_t* K) {
+  if (L < 3 || N < 0 || N > L || n_clones < 1) return ORC_ERR_ARG;
+  for (int64_t j = 0; j < n_clones; ++j) {
+    uint8_t* n = sites + j * (int64_t)L;
+    int taken = 0;
+    for (int t = 0; t < L; ++t) {
+      n[t] = 0;
+      int need = N - taken;
+      if (need <= 0) continue;
+      uint32_t r[4];
+      philox_at((uint32_t)t, 0u, (uint32_t)j, ORC_TAG_INIT, seed, r);
+      uint64_t u = ((uint64_t)r[1] << 32) | r[0];
+      if (mul_hi_64(u, (uint64_t)(L - t)) < (uint64_t)need) {
+        n[t] = 1;
+        ++taken;
+      }
+    }
+    K[j] = 0;
+  }
+  return ORC_OK;
+}
+
+/* number of active bonds: bond i joins sites i and (i+1) mod L */
+static int count_active(const uint8_t* n, int L) {
+  int r = 0;
+  for (int i = 0; i < L; ++i) r += (n[i] != n[(i + 1) % L]);
+  return r;
+}
+
+/* ---------------------------------------------------------------------------
+ * Dynamical stage of interval beta for every clone (Sec. 2.3; Sec. 3.1 rates;
+ * Sec. 4 BKL): plain SSEP rates (1 per active bond), so the escape rate is the
+ * number of active bonds r.  Readings R2-R4 fix the arithmetic.
+ * On return sites hold the configurations at the end of the interval, K the
+ * cumulative activity and dK the activity K^beta of this interval.
+ * ------------------------------------------------------------------------- */
+int orc_evolve(int32_t L, int64_t n_clones, double dt, uint32_t beta, uint64_t seed,
+               uint8_t* sites, int32_t* K, int32_t* dK) {
+  if (L < 3 || n_clones < 1 || !(dt > 0.0)) return ORC_ERR_ARG;
+  const float dt_f = (float)dt;
+  for (int64_t j = 0; j < n_clones; ++j) {
+    uint8_t* n = sites + j * (int64_t)L;
+    float t = 0.0f;
+    uint32_t e = 0;
+    int32_t hops = 0;
+    for (;;) {
+      int r = count_active(n, L);
+      if (r == 0) break;
+      uint32_t w[4];
+      philox_at(e, beta, (uint32_t)j, ORC_TAG_EVOLVE, seed, w);
+      ++e;
+      float E = orc_neg_ln_u(w[0]);
+      float inv_r = 1.0f / (float)r;
+      float tau = E * inv_r;
+      float t_new = t + tau;
+      if (t_new >= dt_f) break;
+      t = t_new;
+      uint64_t u = ((uint64_t)w[3] << 32) | w[2];
+      uint64_t k = mul_hi_64(u, (uint64_t)r);
+      /* the k-th active bond, counting from bond 0 */
+      int b = -1;
+      uint64_t seen = 0;
+      for (int i = 0; i < L; ++i) {
+        if (n[i] != n[(i + 1) % L]) {
+          if (seen == k) { b = i; break; }
+          ++seen;
+        }
+      }
+      int b1 = (b + 1) % L;
+      uint8_t tmp = n[b];
+      n[b] = n[b1];
+      n[b1] = tmp;
+      ++hops;
+    }
+    dK[j] = hops;
+    K[j] += hops;
+  }
+  return ORC_OK;
+}
+
+static int ceil_log2_i64(int64_t x) {
+  int c = 0;
+  while (((int64_t)1 << c) < x) ++c;
+  return c;
+}
+
+/* Reading R6: the fixed-point weight scale F and the reference activity. */
+int32_t orc_weight_scale(int64_t n_clones) { return 61 - ceil_log2_i64(n_clones); }
+
+int32_t orc_k_ref(double s, int64_t n_clones, const int32_t* dK) {
+  int32_t ref = dK[0];
+  for (int64_t j = 1; j < n_clones; ++j) {
+    if (s >= 0.0) { if (dK[j] < ref) ref = dK[j]; }
+    else          { if (dK[j] > ref) ref = dK[j]; }
+  }
+  return ref;
+}
+
+/* ---------------------------------------------------------------------------
+ * Weights Upsilon^beta = exp(-s K^beta) (eq. upsbdef with U = 0), quantised per
+ * reading R6: Upsilon_j / Upsilon_max = exp(-|s| |dK_j - k_ref|).
+ * ------------------------------------------------------------------------- */
+int orc_weights(double s, int64_t n_clones, const int32_t* dK, uint64_t* w) {
+  if (n_clones < 1) return ORC_ERR_ARG;
+  const int F = orc_weight_scale(n_clones);
+  const int32_t ref = orc_k_ref(s, n_clones, dK);
+  int status = ORC_OK;
+  for (int64_t j = 0; j < n_clones; ++j) {
+    int64_t k = (int64_t)dK[j] - ref;
+    if (k < 0) k = -k;
+    if (k >= ORC_KCAP) { w[j] = 0; status = ORC_ERR_RANGE; continue; }
+    double x = ldexp(exp(-fabs(s) * (double)k), F);
+    w[j] = (uint64_t)nearbyint(x);
+  }
+  return status;
+}
+
+/* Compensated (Neumaier) summation: sum and running correction. */
+typedef struct { double sum, comp; } orc_ksum;
+static void ksum_add(orc_ksum* a, double x) {
+  double t = a->sum + x;
+  if (fabs(a->sum) >= fabs(x)) a->comp += (a->sum - t) + x;
+  else a->comp += (x - t) + a->sum;
+  a->sum = t;
+}
+
+/* ---------------------------------------------------------------------------
+ * One term of eq. (psihat): ln( (1/N_c) sum_j exp(-s dK_j) ), in FP64.
+ * Factoring out exp(-s k_ref), with q_j = exp(-|s| |dK_j - k_ref|) in (0, 1]:
+ *   term = -s k_ref + ln( mean_j q_j ).
+ * When mean q is near 1 the logarithm is taken as log1p(mean_j expm1(.)), which is
+ * the same number without the cancellation of ln(1 + small).
+ * ------------------------------------------------------------------------- */
+double orc_psi_term(double s, int64_t n_clones, const int32_t* dK) {
+  const int32_t ref = orc_k_ref(s, n_clones, dK);
+  orc_ksum a = {0.0, 0.0}, b = {0.0, 0.0};
+  for (int64_t j = 0; j < n_clones; ++j) {
+    int64_t k = (int64_t)dK[j] - ref;
+    if (k < 0) k = -k;
+    double x = -fabs(s) * (double)k;
+    ksum_add(&a, expm1(x));
+    ksum_add(&b, exp(x));
+  }
+  double mean_q = (b.sum + b.comp) / (double)n_clones;
+  double ln_mean = (mean_q > 0.5) ? log1p((a.sum + a.comp) / (double)n_clones) : log(mean_q);
+  return -s * (double)ref + ln_mean;
+}
+
+/* The [eq] offset word U of interval beta (reading R7). */
+uint32_t orc_resample_word(uint32_t beta, uint64_t seed) {
+  uint32_t r[4];
+  philox_at(0u, beta, 0u, ORC_TAG_RESAMPLE, seed, r);
+  return r[0];
+}
+
+/* ---------------------------------------------------------------------------
+ * [eq] clone selection, eq. (alpha-Ups) with reading R7, in exact integers.
+ * anc[j] = 0-based index of the old clone that new clone j is pulled from.
+ * Returns ORC_ERR_ARG if every weight is zero.
+ * ------------------------------------------------------------------------- */
+int orc_ancestors(int64_t n_clones, const uint64_t* w, uint32_t beta, uint64_t seed,
+                  int32_t* anc) {
+  if (n_clones < 1) return ORC_ERR_ARG;
+  uint64_t* S = (uint64_t*)malloc((size_t)(n_clones + 1) * sizeof(uint64_t));
+  if (!S) return ORC_ERR_ARG;
+  S[0] = 0;
+  for (int64_t k = 0; k < n_clones; ++k) S[k + 1] = S[k] + w[k];
+  const uint64_t T = S[n_clones];
+  if (T == 0) { free(S); return ORC_ERR_ARG; }
+  const uint64_t U = orc_resample_word(beta, seed);
+  const u128 c = 2 * (u128)U + 1;
+  const u128 denom = ((u128)n_clones) << 33;
+  for (int64_t j = 0; j < n_clones; ++j) {
+    u128 num = ((((u128)j) << 33) + c) * (u128)T;
+    uint64_t alpha = (uint64_t)(num / denom);
+    /* largest k in [0, N_c) with S_k <= alpha; then alpha < S_{k+1} */
+    int64_t lo = 0, hi = n_clones - 1;
+    while (lo < hi) {
+      int64_t mid = lo + (hi - lo + 1) / 2;
+      if (S[mid] <= alpha) lo = mid; else hi = mid - 1;
+    }
+    anc[j] = (int32_t)lo;
+  }
+  free(S);
+  return ORC_OK;
+}
+
+/* Pull copy of the population (Sec. 6.1: new and old populations are separate). */
+void orc_gather(int32_t L, int64_t n_clones, const int32_t* anc,
+                const uint8_t* sites_old, const int32_t* K_old,
+                uint8_t* sites_new, int32_t* K_new) {
+  for (int64_t j = 0; j < n_clones; ++j) {
+    memcpy(sites_new + j * (int64_t)L, sites_old + (int64_t)anc[j] * L, (size_t)L);
+    K_new[j] = K_old[anc[j]];
+  }
+}
+
+/* ---------------------------------------------------------------------------
+ * A full run of the cloning algorithm (Sec. 2.3): init, then M intervals of
+ * (dynamical stage, cloning stage).  psi_hat = (1/t_obs) sum_beta term_beta
+ * (eq. psihat, all M intervals); k_hat = (1/(N_c L t_obs)) sum_j K_j over the
+ * final population (eq. khat with the 1/N_c of eq. avedef).
+ * events (optional) receives the number of hops executed by all clones.
+ * If sites_out / K_out are given, the final population is written there.
+ * ------------------------------------------------------------------------- */
+int orc_run(int32_t L, int32_t N, int64_t n_clones, uint64_t seed, double s, double dt,
+            int64_t M, double* psi_hat, double* k_hat, uint64_t* events,
+            uint8_t* sites_out, int32_t* K_out) {
+  if (L < 3 || N < 0 || N > L || n_clones < 1 || !(dt > 0.0) || M < 1) return ORC_ERR_ARG;
+  size_t nbytes = (size_t)n_clones * (size_t)L;
+  uint8_t* a = (uint8_t*)malloc(nbytes);
+  uint8_t* b = (uint8_t*)malloc(nbytes);
+  int32_t* Ka = (int32_t*)malloc((size_t)n_clones * sizeof(int32_t));
+  int32_t* Kb = (int32_t*)malloc((size_t)n_clones * sizeof(int32_t));
+  int32_t* dK = (int32_t*)malloc((size_t)n_clones * sizeof(int32_t));
+  uint64_t* w = (uint64_t*)malloc((size_t)n_clones * sizeof(uint64_t));
+  int32_t* anc = (int32_t*)malloc((size_t)n_clones * sizeof(int32_t));
+  int status = ORC_OK;
+  if (!a || !b || !Ka || !Kb || !dK || !w || !anc) { status = ORC_ERR_ARG; goto done; }
+  orc_init(L, N, n_clones, seed, a, Ka);
+  double acc = 0.0;
+  uint64_t ev = 0;
+  for (int64_t beta = 1; beta <= M; ++beta) {
+    orc_evolve(L, n_clones, dt, (uint32_t)beta, seed, a, Ka, dK);
+    for (int64_t j = 0; j < n_clones; ++j) ev += (uint64_t)dK[j];
+    acc += orc_psi_term(s, n_clones, dK);
+    int st = orc_weights(s, n_clones, dK, w);
+    if (st != ORC_OK) status = st;
+    if (orc_ancestors(n_clones, w, (uint32_t)beta, seed, anc) != ORC_OK) {
+      status = ORC_ERR_RANGE;
+      goto done;
+    }
+    orc_gather(L, n_clones, anc, a, Ka, b, Kb);
+    uint8_t* ts = a; a = b; b = ts;
+    int32_t* tk = Ka; Ka = Kb; Kb = tk;
+  }
+  {
+    double t_obs = (double)M * dt;
+    double ksum = 0.0;
+    for (int64_t j = 0; j < n_clones; ++j) ksum += (double)Ka[j];
+    if (psi_hat) *psi_hat = acc / t_obs;
+    if (k_hat) *k_hat = ksum / ((double)n_clones * (double)L * t_obs);
+    if (events) *events = ev;
+    if (sites_out) memcpy(sites_out, a, nbytes);
+    if (K_out) memcpy(K_out, Ka, (size_t)n_clones * sizeof(int32_t));
+  }
+done:
+  free(a); free(b); free(Ka); free(Kb); free(dK); free(w); free(anc);
+  return status;
+}

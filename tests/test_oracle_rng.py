@@ -1,0 +1,119 @@
+"""Pins of the oracle's random-number and variate code (not the GPU path).
+
+* Philox4x32-10 is checked against Triton's own Philox4x32-10, run on the CPU by
+  Triton's interpreter in a child process: an implementation of the published
+  algorithm that shares nothing with ours.
+* The specified FP32 -ln(u) is checked against FP64 numpy.log, and its variates
+  against the moments of the unit exponential distribution.
+"""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import oracle
+
+TRITON_CHILD = r"""
+import json, os, sys
+os.environ["TRITON_INTERPRET"] = "1"
+import torch, triton, triton.language as tl
+
+@triton.jit
+def _k(c0, c1, c2, c3, k0p, k1p, out, n: tl.constexpr):
+    i = tl.arange(0, n)
+    a = tl.load(c0 + i); b = tl.load(c1 + i); c = tl.load(c2 + i); d = tl.load(c3 + i)
+    k0 = tl.load(k0p + i); k1 = tl.load(k1p + i)
+    r0, r1, r2, r3 = tl.philox_impl(a, b, c, d, k0, k1, 10)
+    tl.store(out + 4 * i + 0, r0); tl.store(out + 4 * i + 1, r1)
+    tl.store(out + 4 * i + 2, r2); tl.store(out + 4 * i + 3, r3)
+
+cases = json.loads(sys.stdin.read())
+n = len(cases)
+cols = [torch.tensor([c[0][q] for c in cases], dtype=torch.int64).to(torch.uint32) for q in range(4)]
+k0 = torch.tensor([c[1] & 0xffffffff for c in cases], dtype=torch.int64).to(torch.uint32)
+k1 = torch.tensor([c[1] >> 32 for c in cases], dtype=torch.int64).to(torch.uint32)
+out = torch.zeros(4 * n, dtype=torch.uint32)
+_k[(1,)](*cols, k0, k1, out, n)
+print(json.dumps([int(v) for v in out.to(torch.int64)]))
+"""
+
+
+def _triton_available():
+    try:
+        import triton  # noqa: F401
+        import torch  # noqa: F401
+        return True
+    except Exception:
+        return False
+
+
+@pytest.mark.skipif(not _triton_available(), reason="triton not importable")
+def test_philox_matches_independent_implementation():
+    rng = np.random.default_rng(20171105)
+    cases = []
+    # structured counters the path uses (tags 1..3) and arbitrary ones
+    for tag in (1, 2, 3):
+        for e in range(4):
+            cases.append(([e, 7, 123, tag], 0x0123456789ABCDEF))
+    cases.append(([0, 0, 0, 0], 0))
+    cases.append(([0xFFFFFFFF] * 4, 0xFFFFFFFFFFFFFFFF))
+    while len(cases) < 64:
+        ctr = [int(v) for v in rng.integers(0, 2**32, size=4, dtype=np.uint64)]
+        key = int(rng.integers(0, 2**63, dtype=np.uint64)) * 2 + int(rng.integers(0, 2))
+        cases.append((ctr, key))
+    proc = subprocess.run([sys.executable, "-c", TRITON_CHILD], input=json.dumps(cases),
+                          capture_output=True, text=True, timeout=600,
+                          env=dict(os.environ, TRITON_INTERPRET="1"))
+    assert proc.returncode == 0, proc.stderr[-2000:]
+    ref = json.loads(proc.stdout.strip().splitlines()[-1])
+    for q, (ctr, key) in enumerate(cases):
+        got = [int(v) for v in oracle.philox(ctr, key)]
+        assert got == ref[4 * q:4 * q + 4], (ctr, hex(key))
+
+
+def test_philox_output_is_uniform():
+    # 64k words from consecutive counters: bit balance and byte histogram
+    words = np.concatenate([oracle.philox([e, 1, 2, 2], 99) for e in range(16384)])
+    bits = np.unpackbits(words.view(np.uint8))
+    assert abs(bits.mean() - 0.5) < 5 * 0.5 / np.sqrt(bits.size)
+    hist = np.bincount(words.view(np.uint8), minlength=256)
+    exp = words.size * 4 / 256
+    chi2 = float(((hist - exp) ** 2 / exp).sum())
+    assert chi2 < 255 + 6 * np.sqrt(2 * 255)
+
+
+EDGE_WORDS = [0, 1, 2, 3, 1000, 2**23, 2**24 - 1, 2**24, 0x3504F333, 0x3504F334,
+              0x6A09E667, 0x6A09E668, 2**31 - 1, 2**31, 0xB504F333, 0xB504F334,
+              2**32 - 2**9, 2**32 - 2, 2**32 - 1]
+
+
+def test_neg_ln_u_against_fp64_log():
+    rng = np.random.default_rng(7)
+    ws = list(rng.integers(0, 2**32, size=20000, dtype=np.uint64)) + EDGE_WORDS
+    # also sweep every binade of u
+    ws += [(1 << k) + d for k in range(0, 32) for d in (-1, 0, 1) if 0 <= (1 << k) + d < 2**32]
+    for w in ws:
+        w = int(w)
+        got = float(oracle.neg_ln_u(w))
+        u = (2.0 * w + 1.0) / 2.0**33
+        exact = -np.log(u)
+        # one rounding of v = 2w+1 to 24 bits perturbs ln u by up to 2^-24, then
+        # a few float ulps of the result
+        tol = 2.0**-24 + 4 * np.spacing(np.float32(exact))
+        assert abs(got - exact) <= tol, (w, got, exact)
+        assert got >= 0.0
+
+
+def test_neg_ln_u_is_unit_exponential():
+    words = np.concatenate([oracle.philox([e, 3, 0, 2], 5) for e in range(50000)])[::4]
+    E = np.array([float(oracle.neg_ln_u(int(w))) for w in words])
+    n = E.size
+    assert abs(E.mean() - 1.0) < 5 / np.sqrt(n)
+    assert abs(E.var() - 1.0) < 5 * np.sqrt(8.0 / n)
+    # P(E > 2) = e^-2
+    p = (E > 2.0).mean()
+    q = np.exp(-2.0)
+    assert abs(p - q) < 5 * np.sqrt(q * (1 - q) / n)
