@@ -24,17 +24,20 @@
  *   R1 random numbers: Philox4x32-10 (Salmon et al., SC'11) replaces the paper's
  *      Mersenne Twister.  key = 64-bit seed; counter = (c0, c1, c2, c3):
  *        init     (site t, 0,    slot j, 1)
- *        evolve   (draw e, beta, slot j, 2)   beta = 1..M, e = 0,1,... per interval
+ *        evolve   (draw q, beta, slot j, 2)   beta = 1..M, q = 0,1,... per interval
  *        resample (0,      beta, 0,      3)
  *      The slot j is the clone's position in the population, after resampling.
- *   R2 exponential variate: u = (2*w0 + 1) / 2^33 from the first output word;
+ *      One evolve draw serves two BKL steps: step e of the interval uses draw
+ *      q = e/2, words (w0, w1) when e is even and (w2, w3) when e is odd.
+ *   R2 exponential variate: u = (2*wa + 1) / 2^33 from the step's first word wa;
  *      E = -ln(u) by the FP32 logarithm defined in neg_ln_u() below (written from
  *      ln(m 2^n) = n ln 2 + 2 atanh((m-1)/(m+1)); no library log).
  *   R3 time arithmetic in FP32: tau = E * (1/r) with 1/r rounded to float,
  *      t_new = t + tau; the interval ends when t_new >= (float)dt (no hop).
- *   R4 bond choice: k = floor(U64 * r / 2^64) with U64 = w3*2^32 + w2; the hop is
- *      across the k-th active bond counted from bond 0; bond i joins sites i and
- *      (i+1) mod L and is active when exactly one of the two is occupied.
+ *   R4 bond choice: k = floor(wb * r / 2^32) with wb the step's second word (a
+ *      bias of at most r / 2^32 per bond); the hop is across the k-th active bond
+ *      counted from bond 0; bond i joins sites i and (i+1) mod L and is active
+ *      when exactly one of the two is occupied.
  *   R5 initial condition: a uniform N-subset of the L sites per clone, by
  *      selection sampling (site t taken iff floor(U64*(L-t)/2^64) < N - taken).
  *   R6 fixed-point weights: F = 61 - ceil(log2 N_c); k_ref = min dK (s >= 0) or
@@ -204,16 +207,17 @@ int orc_evolve(int32_t L, int64_t n_clones, double dt, uint32_t beta, uint64_t s
       int r = count_active(n, L);
       if (r == 0) break;
       uint32_t w[4];
-      philox_at(e, beta, (uint32_t)j, ORC_TAG_EVOLVE, seed, w);
+      philox_at(e / 2u, beta, (uint32_t)j, ORC_TAG_EVOLVE, seed, w);
+      uint32_t wa = (e % 2u == 0u) ? w[0] : w[2];
+      uint32_t wb = (e % 2u == 0u) ? w[1] : w[3];
       ++e;
-      float E = orc_neg_ln_u(w[0]);
+      float E = orc_neg_ln_u(wa);
       float inv_r = 1.0f / (float)r;
       float tau = E * inv_r;
       float t_new = t + tau;
       if (t_new >= dt_f) break;
       t = t_new;
-      uint64_t u = ((uint64_t)w[3] << 32) | w[2];
-      uint64_t k = mul_hi_64(u, (uint64_t)r);
+      uint64_t k = ((uint64_t)wb * (uint64_t)r) >> 32;
       /* the k-th active bond, counting from bond 0 */
       int b = -1;
       uint64_t seen = 0;
