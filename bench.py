@@ -1,0 +1,340 @@
+#!/usr/bin/env python3
+"""Benchmark of the SSEP cloning estimator on GB300: clone-events per second.
+
+Workload (the batched s-sweep): 64 populations of the SSEP on a ring of L = 50 sites
+with N = 25 particles, biases lambda = s L^2 evenly spaced in [-20, 40], N_c = 16384
+clones each (2^20 clones), cloning interval dt = 0.1, t_obs = 1000 (M = 10000
+intervals).  One step is one whole run: pop_init (initial configurations), M
+intervals of dynamical + cloning stages (pop_run, captured CUDA graphs), and
+pop_estimate_psi.  clone-events = BKL hops executed by all clones (arXiv:1711.05095
+measures the serial and parallel cost of exactly this loop, Sec. 6).
+
+Prints one JSON line.  --impl reference times the CPU oracle on a bounded sample of
+the same workload instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "clone-events/s"
+UNIT = "events/s"
+
+# Algorithmic 32-bit operations per BKL step (one waiting time, and for a hop one
+# bond choice and the two-site flip), counted from the step's definition, not from
+# compiled code:
+#   Philox4x32-10 shared by two steps: (10 rounds x (2 widening products = 4 ops,
+#     2 three-input XORs = 4 ops) + 9 x 2 key additions) / 2              = 49
+#   -ln(u): 2w+1 (2), int->float (1), exponent/mantissa split (3), fold (2),
+#     m-1, m+1, divide (3), z (1), 4 fma, f*p (1), exponent to float (2), 2 fma = 21
+#   time: 1/r lookup, multiply, add, compare                                   = 4
+#   active bonds and rate: rotate (4), xor (1), popc (1), r == 0 test (1)      = 7
+#   bond choice: multiply-high (1), k-th set bit of 64 bits (6 levels x 4)    = 25
+#   hop: b+1 mod L (3), two bit masks (3), xor (1)                              = 7
+#   loop bookkeeping (step and hop counters, exit test)                         = 3
+OPS_HOP = 49 + 21 + 4 + 7 + 25 + 7 + 3          # a step that hops: 116
+OPS_STOP = OPS_HOP - 25 - 7 - 1                 # the step that ends the interval: 83
+N_SM = 152
+ISSUE_OPS_PER_SM_CLK = 128                      # 4 schedulers x 32 lanes
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--intervals", type=int, default=None,
+                    help="override M (profiling runs only; the bench line then names it)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-intervals", type=int, default=200)
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=10)
+        except Exception:
+            self.proc.kill()
+            return None
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_sample(w, pop_idx, M):
+    """The oracle as it stands, single-threaded, on the listed populations for M
+    intervals.  Returns (events, seconds)."""
+    import oracle
+    oracle.lib()
+    events, t0 = 0, time.perf_counter()
+    for p in pop_idx:
+        q = w["pops"][p]
+        r = oracle.run(q["L"], q["N"], q["n_clones"], q["seed"], w["s"][p], w["dt"], M)
+        events += r["events"]
+    return events, time.perf_counter() - t0
+
+
+def reference_arm(args, w, world, rank):
+    if rank != 0:
+        return
+    pops = [0, 32]
+    M = 40
+    steps = []
+    for i in range(args.warmup + args.steps):
+        ev, sec = cpu_oracle_sample(w, pops, M)
+        if i >= args.warmup:
+            steps.append((ev, sec))
+    ev = sum(e for e, _ in steps)
+    sec = sum(s for _, s in steps)
+    value = ev / sec
+    sample = "populations %s of the 64 (N_c=16384 each), first %d of 10000 intervals, per step" % (pops, M)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sec / len(steps), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "s_sweep L=50 N=25 64 biases N_c=16384 dt=0.1 t_obs=1000",
+                   "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    w = workloads.s_sweep()
+    if args.intervals is not None:
+        w["M"] = int(args.intervals)
+        w["t_obs"] = w["M"] * w["dt"]
+    if args.impl == "reference":
+        return reference_arm(args, w, world, rank)
+
+    import torch
+    import paper_1711_05095_gb300 as pg
+    from paper_1711_05095_gb300 import build as pbuild
+    pbuild.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    # weak scaling: every rank runs its own 64-population batch with its own seeds
+    pops = [dict(q, seed=q["seed"] + 100000 * rank) for q in w["pops"]]
+    s, dt, M = w["s"], w["dt"], w["M"]
+    P = len(pops)
+    nbytes = pg.workspace_bytes(pops)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    flush = torch.empty(512 * 2**20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    def one_step():
+        b = pg.PopulationBatch(pops, device=dev, stream=stream, workspace=ws)
+        b.run(dt, s, M)
+        psi, kh, t = b.estimate_psi()
+        ev = int(b.events().sum())
+        b.close()
+        return ev, psi
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        one_step()
+    sampler = ClockSampler(local)
+    barrier()
+    sampler.start()
+    t_wall0 = time.perf_counter()
+    ev_total, ms = 0, []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ev, psi = one_step()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        ev_total += ev
+    barrier()
+    wall = time.perf_counter() - t_wall0
+    clocks = sampler.stop()
+    t_dev = sum(ms) / 1e3
+    if dist is not None:
+        t = torch.tensor([t_dev], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e = torch.tensor([ev_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(e, op=dist.ReduceOp.SUM)
+        t_dev, ev_all = float(t.item()), float(e.item())
+    else:
+        ev_all = float(ev_total)
+    value = ev_all / t_dev
+
+    # end to end through the C ABI with host buffers: initial configurations from
+    # pinned host memory (pop_set_state), the run, estimates back to the host
+    host_lat = []
+    for q in pops:
+        arr = workloads.random_subsets(q["L"], q["N"], q["n_clones"], seed=q["seed"])
+        pinned = torch.empty(arr.shape, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+        pinned[...] = arr
+        kz = torch.zeros(q["n_clones"], dtype=torch.int32, pin_memory=True).numpy()
+        host_lat.append((pinned, kz))
+    W = pg.lattice_words(pops)
+    h2d = sum(q["n_clones"] * (8 * W + 4) for q in pops)
+    d2h = P * (48 + 8)      # per-population state record and K sum read by pop_estimate_psi
+
+    def e2e_step():
+        b = pg.PopulationBatch(pops, device=dev, stream=stream, workspace=ws)
+        for p in range(P):
+            b.set_state(p, host_lat[p][0], host_lat[p][1])
+        b.run(dt, s, M)
+        psi, kh, t = b.estimate_psi()
+        ev = int(b.events().sum())
+        b.close()
+        return ev
+
+    e2e_step()
+    barrier()
+    e2e_ev, e2e_t = 0, 0.0
+    for _ in range(max(1, min(args.steps, 2))):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        e2e_ev += e2e_step()
+        e2e_t += time.perf_counter() - t0
+    e2e_value = e2e_ev / e2e_t
+    if dist is not None:
+        t = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e = torch.tensor([e2e_ev], dtype=torch.float64, device=dev)
+        dist.all_reduce(e, op=dist.ReduceOp.SUM)
+        e2e_value = float(e.item()) / float(t.item())
+
+    # dominant kernel: k_evolve, timed with CUDA events on the launching stream
+    R = args.kernel_intervals
+    b = pg.PopulationBatch(pops, device=dev, stream=stream, workspace=ws)
+    b.run(dt, s, 64)
+    ev_before = int(b.events().sum())
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+            torch.cuda.Event(enable_timing=True)) for _ in range(R)]
+    for a0, a1, a2 in evs:
+        a0.record(stream)
+        b.evolve(dt, s)
+        a1.record(stream)
+        b.resample()
+        a2.record(stream)
+    torch.cuda.synchronize(dev)
+    ev_k = int(b.events().sum()) - ev_before
+    b.close()
+    t_ev = sum(a0.elapsed_time(a1) for a0, a1, _ in evs) / R / 1e3
+    t_rs = sum(a1.elapsed_time(a2) for _, a1, a2 in evs) / R / 1e3
+    clone_intervals = sum(q["n_clones"] for q in pops)
+    ops_per_launch = (OPS_HOP * ev_k + OPS_STOP * clone_intervals * R) / R
+    peaks, peak_kind = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_gops = N_SM * ISSUE_OPS_PER_SM_CLK * sm_max * 1e6 / 1e9
+    achieved = ops_per_launch / t_ev / 1e9
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "s_sweep L=50 N=25 64 biases lambda in [-20,40] N_c=16384 each "
+                               "dt=0.1 t_obs=%g (M=%d)" % (w["t_obs"], M),
+                   "populations": P, "clones": clone_intervals, "intervals": M,
+                   "l2": "flushed (512 MB write) between timed steps",
+                   "parallelism": "replicas%d" % world},
+        "gpu_launches": (3 * M + 2) * args.steps,
+        "roofline": {"bound": "alu", "kernel": "k_evolve", "achieved": achieved, "peak": peak_gops,
+                     "unit": "Gop/s", "frac": achieved / peak_gops, "traffic": None,
+                     "peak_kind": "issue rate 152 SM x 128 lanes x %.0f MHz (%s max clock)"
+                                  % (sm_max, peak_kind),
+                     "launch_ms": 1e3 * t_ev, "resample_ms": 1e3 * t_rs,
+                     "ops_per_launch": ops_per_launch},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "clocks": clocks,
+        "wall_s_timed": wall,
+        "psi_check": {"lambda=-20": float(psi[0]), "lambda=40": float(psi[-1])},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        idx = list(range(0, 64, 8))
+        ev_c, sec_c = cpu_oracle_sample(w, idx, 40)
+        line["cpu_baseline"] = {"value": ev_c / sec_c, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "populations %s (N_c=16384 each), first 40 of the "
+                                          "10000 intervals; %.1f s" % (idx, sec_c)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

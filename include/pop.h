@@ -1,0 +1,164 @@
+/*
+ * pop.h -- C ABI of the GB300 population-dynamics (cloning) library.
+ *
+ * The library estimates the scaled cumulant generating function psi(s) of the
+ * activity K (number of particle hops) of the symmetric simple exclusion process
+ * (SSEP) on a ring by the cloning algorithm of arXiv:1711.05095:
+ *   - Sec. 2.3: a population of N_c clones, M = t_obs/dt intervals, each a
+ *     dynamical stage (independent evolution) followed by a cloning stage
+ *     (resampling in proportion to the weights Upsilon, eq. upsbdef);
+ *   - eq. (psihat): psi_hat = (1/t_obs) sum_beta ln( (1/N_c) sum_i Upsilon_i^beta );
+ *   - Sec. 4.1, eq. (alpha-Ups): [eq] selection with equally spaced points;
+ *   - eq. (khat): k_hat from the cumulative activity carried with each clone.
+ * A handle holds a BATCH of independent populations (each its own L, N, N_c,
+ * seed and bias s) that advance through the intervals together.
+ *
+ * Conventions
+ *   - Every call returns an int status: POP_OK (0) or a negative POP_ERR_*.
+ *   - Device memory is owned by the caller: pop_init carves one caller-allocated
+ *     device workspace of pop_workspace_bytes() bytes; pop_free never frees it.
+ *   - Work is enqueued on the CUDA stream given to pop_init.  pop_evolve,
+ *     pop_resample and pop_run return once their kernels are enqueued; the
+ *     host-reading calls (pop_estimate_psi, pop_copy_state, pop_events) wait for
+ *     the stream.  Kernel-side errors (an activity outside the weight table, a
+ *     spin-wait that gave up) are sticky in device memory and are returned by the
+ *     next host-reading call.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ *   - Lattices: site i of a clone is bit (i mod 64) of 64-bit word (i div 64); a
+ *     clone occupies W = ceil(max_p L_p / 64) consecutive words (bits >= L zero).
+ *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) keyed by the
+ *     population's 64-bit seed, counter (c0, c1, c2, c3) =
+ *       initial state   (site t, 0,        clone slot j, 1)
+ *       dynamical stage (draw q, interval, clone slot j, 2)  step e uses draw e/2
+ *       cloning stage   (0,      interval, 0,            3)
+ *     Intervals are numbered from 1.  Results are reproducible bit for bit for a
+ *     given batch, independent of the launch configuration.
+ */
+#ifndef POP_H
+#define POP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define POP_OK 0
+#define POP_ERR_ARG (-1)     /* an argument is out of its documented range */
+#define POP_ERR_CUDA (-2)    /* a CUDA runtime call failed (no device, launch failure) */
+#define POP_ERR_RANGE (-3)   /* an interval activity differed from the reference by >= POP_KCAP */
+#define POP_ERR_TIMEOUT (-4) /* a device-side wait gave up after its iteration limit */
+#define POP_ERR_STATE (-5)   /* call out of order, or s changed during a run */
+
+/* weight modes (eq. upsdef) */
+#define POP_PLAIN 0    /* unmodified SSEP rates, Upsilon = exp(-s dK) (eq. upsbdef, U = 0) */
+#define POP_MODIFIED 1 /* rates times e^-s, eq. (def-ups-ssep); not available yet */
+
+/* clone selection (Sec. 4.1) */
+#define POP_EQ 0  /* equally spaced alpha_j, eq. (alpha-Ups) */
+#define POP_IID 1 /* independent alpha_j; not available yet */
+
+#define POP_KCAP 4096     /* size of the fixed-point weight table */
+#define POP_MAX_L 128     /* largest ring handled by the one-clone-per-thread evolve */
+#define POP_MAX_CLONES (1LL << 30)
+
+/* One population of the batch. */
+typedef struct pop_params {
+  int32_t L;           /* ring length, 3 <= L <= POP_MAX_L */
+  int32_t N;           /* particles, 0 <= N <= L */
+  int64_t n_clones;    /* N_c, 1 <= N_c <= POP_MAX_CLONES */
+  uint64_t seed;       /* Philox key of this population's streams */
+  int32_t weight_mode; /* POP_PLAIN */
+  int32_t selection;   /* POP_EQ */
+} pop_params;
+
+typedef struct pop_batch pop_t;
+
+/*
+ * Device workspace needed for a batch of n_pops populations (bytes, a multiple of
+ * 256).  Returns 0 if the parameters are invalid.  Host-only; touches no device.
+ */
+size_t pop_workspace_bytes(const pop_params* params, int32_t n_pops);
+
+/*
+ * Create a batch and draw its initial configurations (Sec. 2.1: initial condition
+ * from the steady state, which for the SSEP at fixed N is a uniform N-subset of the
+ * sites; Sec. 3.1).  params: host array of n_pops entries (copied).  d_workspace:
+ * caller-owned device memory of at least pop_workspace_bytes(params, n_pops) bytes,
+ * 256-byte aligned, that must outlive the handle.  cuda_stream: a cudaStream_t (NULL
+ * = legacy default stream).  On success *out receives the handle; on failure *out is
+ * NULL and nothing needs freeing.
+ */
+int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_workspace,
+             size_t workspace_bytes, void* cuda_stream);
+
+/*
+ * Replace the configurations of population p (0-based) by caller-supplied ones
+ * (host memory): h_lattice holds N_c * W words (clone-major), h_K the N_c cumulative
+ * activities (NULL = zeros).  Every clone must hold exactly N particles and no bit at
+ * or above L (else POP_ERR_ARG, nothing copied).  Allowed before the first interval
+ * only.  Waits for the copies.
+ */
+int pop_set_state(pop_t* pop, int32_t p, const uint64_t* h_lattice, const int32_t* h_K);
+
+/*
+ * Dynamical stage of the next interval (Sec. 2.3; Sec. 4: BKL continuous-time Monte
+ * Carlo of the SSEP for a time dt).  s: host array of n_pops biases; the first call
+ * fixes them for the run (a later call with a different s returns POP_ERR_STATE).
+ * dt > 0 may change between intervals; t_obs is their sum.
+ */
+int pop_evolve(pop_t* pop, double dt, const double* s);
+
+/*
+ * Cloning stage of the interval just evolved (Sec. 2.3, Sec. 4.1): the weights, the
+ * psi term ln((1/N_c) sum Upsilon) accumulated in FP64 (eq. psihat), exact 64-bit
+ * fixed-point prefix sums, [eq] ancestors (eq. alpha-Ups) and the gather of lattices
+ * and cumulative activities.  POP_ERR_STATE unless pop_evolve came just before.
+ */
+int pop_resample(pop_t* pop);
+
+/*
+ * n_intervals full intervals (dynamical stage then cloning stage), identical in
+ * result to n_intervals pairs of pop_evolve/pop_resample, launched as captured CUDA
+ * graphs.  Same rules for s and dt as pop_evolve.
+ */
+int pop_run(pop_t* pop, double dt, const double* s, int64_t n_intervals);
+
+/*
+ * Estimates after the intervals run so far (host arrays of n_pops each; any may be
+ * NULL): psi[p] = eq. (psihat); k_hat[p] = (1/(N_c L t_obs)) sum_i K_i over the
+ * current population (eq. khat with the 1/N_c of eq. avedef); t_obs = sum of dt.
+ * Waits for the stream.  POP_ERR_STATE before the first complete interval.
+ */
+int pop_estimate_psi(pop_t* pop, double* psi, double* k_hat, double* t_obs);
+
+/*
+ * Copy population p to host memory (any pointer may be NULL):
+ *   h_lattice  N_c * W words   current configurations
+ *   h_K        N_c             cumulative activities
+ *   h_anc      N_c             ancestors of the last cloning stage (0-based)
+ *   h_dK       N_c             activities of the last dynamical stage
+ * Between pop_evolve and pop_resample the lattices/K are the evolved ones.
+ * Waits for the stream.
+ */
+int pop_copy_state(pop_t* pop, int32_t p, uint64_t* h_lattice, int32_t* h_K,
+                   int32_t* h_anc, int32_t* h_dK);
+
+/* Executed hops (BKL events) per population since pop_init (host array of n_pops). */
+int pop_events(pop_t* pop, uint64_t* h_events);
+
+/* Lattice words per clone, W, of a batch (0 if the parameters are invalid). */
+int32_t pop_lattice_words(const pop_params* params, int32_t n_pops);
+
+/* Static description of a status code. */
+const char* pop_strerror(int status);
+
+/* Release the handle (host state and CUDA graphs); never the caller's workspace. */
+void pop_free(pop_t* pop);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POP_H */

@@ -1,0 +1,213 @@
+"""GB300 (sm_103a) population-dynamics estimator of psi(s) for the SSEP activity.
+
+Thin Python binding of the C ABI in ``include/pop.h`` (arXiv:1711.05095, Sec. 2.3
+cloning algorithm; Sec. 4 BKL dynamics and [eq] selection).  This module only
+marshals arguments: every step of the path runs in the CUDA library
+``_build/libpopgb300.so``.  PyTorch supplies device memory (the workspace) and the
+CUDA stream.  There is no CPU fallback: if the library is not built, or no CUDA
+device is present, the calls raise.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libpopgb300.so")
+
+POP_OK = 0
+POP_ERR_ARG = -1
+POP_ERR_CUDA = -2
+POP_ERR_RANGE = -3
+POP_ERR_TIMEOUT = -4
+POP_ERR_STATE = -5
+POP_PLAIN = 0
+POP_MODIFIED = 1
+POP_EQ = 0
+POP_IID = 1
+POP_KCAP = 4096
+POP_MAX_L = 128
+
+# every symbol include/pop.h declares
+EXPORTS = ("pop_workspace_bytes", "pop_init", "pop_set_state", "pop_evolve", "pop_resample",
+           "pop_run", "pop_estimate_psi", "pop_copy_state", "pop_events", "pop_lattice_words",
+           "pop_strerror", "pop_free")
+
+
+class PopParams(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("N", ctypes.c_int32), ("n_clones", ctypes.c_int64),
+                ("seed", ctypes.c_uint64), ("weight_mode", ctypes.c_int32),
+                ("selection", ctypes.c_int32)]
+
+
+class PopError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s failed: %s (%d)" % (where, strerror(status), status))
+
+
+_lib = None
+_f64p = ctypes.POINTER(ctypes.c_double)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+
+
+def library():
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("CUDA library %s is missing: build it with "
+                           "paper_1711_05095_gb300.build.build()" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    pp = ctypes.POINTER(PopParams)
+    L.pop_workspace_bytes.argtypes = [pp, ctypes.c_int32]
+    L.pop_workspace_bytes.restype = ctypes.c_size_t
+    L.pop_lattice_words.argtypes = [pp, ctypes.c_int32]
+    L.pop_lattice_words.restype = ctypes.c_int32
+    L.pop_init.argtypes = [ctypes.POINTER(ctypes.c_void_p), pp, ctypes.c_int32, ctypes.c_void_p,
+                           ctypes.c_size_t, ctypes.c_void_p]
+    L.pop_init.restype = ctypes.c_int
+    L.pop_set_state.argtypes = [ctypes.c_void_p, ctypes.c_int32, _u64p, _i32p]
+    L.pop_set_state.restype = ctypes.c_int
+    L.pop_evolve.argtypes = [ctypes.c_void_p, ctypes.c_double, _f64p]
+    L.pop_evolve.restype = ctypes.c_int
+    L.pop_resample.argtypes = [ctypes.c_void_p]
+    L.pop_resample.restype = ctypes.c_int
+    L.pop_run.argtypes = [ctypes.c_void_p, ctypes.c_double, _f64p, ctypes.c_int64]
+    L.pop_run.restype = ctypes.c_int
+    L.pop_estimate_psi.argtypes = [ctypes.c_void_p, _f64p, _f64p, _f64p]
+    L.pop_estimate_psi.restype = ctypes.c_int
+    L.pop_copy_state.argtypes = [ctypes.c_void_p, ctypes.c_int32, _u64p, _i32p, _i32p, _i32p]
+    L.pop_copy_state.restype = ctypes.c_int
+    L.pop_events.argtypes = [ctypes.c_void_p, _u64p]
+    L.pop_events.restype = ctypes.c_int
+    L.pop_strerror.argtypes = [ctypes.c_int]
+    L.pop_strerror.restype = ctypes.c_char_p
+    L.pop_free.argtypes = [ctypes.c_void_p]
+    L.pop_free.restype = None
+    _lib = L
+    return L
+
+
+def strerror(status):
+    try:
+        return library().pop_strerror(int(status)).decode()
+    except RuntimeError:
+        return "status %d" % status
+
+
+def _check(rc, where):
+    if rc != POP_OK:
+        raise PopError(rc, where)
+
+
+def make_params(pops):
+    """pops: sequence of dicts with L, N, n_clones, seed (weight_mode, selection optional)."""
+    arr = (PopParams * len(pops))()
+    for i, q in enumerate(pops):
+        arr[i] = PopParams(int(q["L"]), int(q["N"]), int(q["n_clones"]), int(q["seed"]),
+                           int(q.get("weight_mode", POP_PLAIN)), int(q.get("selection", POP_EQ)))
+    return arr
+
+
+def workspace_bytes(pops):
+    arr = make_params(pops)
+    return int(library().pop_workspace_bytes(arr, len(pops)))
+
+
+def lattice_words(pops):
+    arr = make_params(pops)
+    return int(library().pop_lattice_words(arr, len(pops)))
+
+
+class PopulationBatch:
+    """A batch of independent clone populations on one GPU (C ABI ``pop_*``).
+
+    ``pops`` is a list of dicts (L, N, n_clones, seed).  The workspace is a torch
+    uint8 tensor on ``device``; work is queued on ``stream`` (default: the current
+    torch stream of that device).
+    """
+
+    def __init__(self, pops, device="cuda", stream=None, workspace=None):
+        import torch
+        self.pops = [dict(q) for q in pops]
+        self.n_pops = len(pops)
+        self._lib = library()
+        self._params = make_params(self.pops)
+        nbytes = int(self._lib.pop_workspace_bytes(self._params, self.n_pops))
+        if nbytes == 0:
+            raise PopError(POP_ERR_ARG, "pop_workspace_bytes")
+        self.W = int(self._lib.pop_lattice_words(self._params, self.n_pops))
+        self.device = torch.device(device)
+        if workspace is not None:
+            if workspace.numel() * workspace.element_size() < nbytes or workspace.device.type != "cuda":
+                raise PopError(POP_ERR_ARG, "workspace")
+            self.workspace = workspace
+        else:
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._h = ctypes.c_void_p()
+        rc = self._lib.pop_init(ctypes.byref(self._h), self._params, self.n_pops,
+                                ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                ctypes.c_void_p(self.stream.cuda_stream))
+        _check(rc, "pop_init")
+
+    def _s(self, s):
+        s = np.ascontiguousarray(np.broadcast_to(np.asarray(s, dtype=np.float64), (self.n_pops,)))
+        return s, s.ctypes.data_as(_f64p)
+
+    def set_state(self, p, lattice, K=None):
+        lat = np.ascontiguousarray(np.asarray(lattice, dtype=np.uint64).reshape(-1))
+        kp = None
+        if K is not None:
+            K = np.ascontiguousarray(np.asarray(K, dtype=np.int32))
+            kp = K.ctypes.data_as(_i32p)
+        _check(self._lib.pop_set_state(self._h, int(p), lat.ctypes.data_as(_u64p), kp), "pop_set_state")
+
+    def evolve(self, dt, s):
+        s, sp = self._s(s)
+        _check(self._lib.pop_evolve(self._h, float(dt), sp), "pop_evolve")
+
+    def resample(self):
+        _check(self._lib.pop_resample(self._h), "pop_resample")
+
+    def run(self, dt, s, n_intervals):
+        s, sp = self._s(s)
+        _check(self._lib.pop_run(self._h, float(dt), sp, int(n_intervals)), "pop_run")
+
+    def estimate_psi(self):
+        psi = np.zeros(self.n_pops)
+        kh = np.zeros(self.n_pops)
+        t = ctypes.c_double(0.0)
+        _check(self._lib.pop_estimate_psi(self._h, psi.ctypes.data_as(_f64p), kh.ctypes.data_as(_f64p),
+                                          ctypes.byref(t)), "pop_estimate_psi")
+        return psi, kh, t.value
+
+    def copy_state(self, p):
+        n = int(self.pops[p]["n_clones"])
+        lat = np.zeros((n, self.W), dtype=np.uint64)
+        K = np.zeros(n, dtype=np.int32)
+        anc = np.zeros(n, dtype=np.int32)
+        dK = np.zeros(n, dtype=np.int32)
+        _check(self._lib.pop_copy_state(self._h, int(p), lat.ctypes.data_as(_u64p), K.ctypes.data_as(_i32p),
+                                        anc.ctypes.data_as(_i32p), dK.ctypes.data_as(_i32p)),
+               "pop_copy_state")
+        return dict(lattice=lat, K=K, anc=anc, dK=dK)
+
+    def events(self):
+        ev = np.zeros(self.n_pops, dtype=np.uint64)
+        _check(self._lib.pop_events(self._h, ev.ctypes.data_as(_u64p)), "pop_events")
+        return ev
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.pop_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,470 @@
+// Host side of the C ABI declared in include/pop.h.
+//
+// A handle owns only host state; every device buffer is carved out of the
+// caller's workspace.  Layout of the workspace (each region 256-byte aligned):
+//   PopDesc[P]  PopState[P]  tile_pop[ntiles]  wtab[P][4096] u64  inv_rate[P][129] f32
+//   hist[P][4096] u32  tile_status[2][ntiles] u64  ticket[2]  beta  ksum[P]
+//   X, Y lattices [nslots][W] u64   KX, KY, dK, anc [nslots] i32   S [nslots] u64
+// where every population starts on a 1024-slot tile and nslots is the padded total.
+//
+// One interval = k_evolve, k_scan, k_gather on the caller's stream.  pop_run captures
+// kGraphIntervals intervals into a CUDA graph once (on a private capture stream) and
+// replays it on the caller's stream; the kernels read the interval number and every
+// other changing quantity from device memory, so replays need no new arguments.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pop.h"
+#include "pop_device.cuh"
+
+using namespace popgpu;
+
+namespace {
+
+constexpr int kGraphIntervals = 32;
+
+struct Layout {
+  int32_t P = 0, W = 0, ntiles = 0;
+  int64_t nslots = 0;
+  size_t o_pops, o_st, o_tile_pop, o_wtab, o_inv, o_hist, o_status, o_ticket, o_beta,
+      o_ksum, o_X, o_Y, o_KX, o_KY, o_dK, o_anc, o_S, total;
+};
+
+size_t align256(size_t x) { return (x + 255u) & ~(size_t)255u; }
+
+bool valid_params(const pop_params* params, int32_t n_pops) {
+  if (params == nullptr || n_pops < 1 || n_pops > (1 << 20)) return false;
+  for (int32_t p = 0; p < n_pops; ++p) {
+    const pop_params& q = params[p];
+    if (q.L < 3 || q.L > POP_MAX_L) return false;
+    if (q.N < 0 || q.N > q.L) return false;
+    if (q.n_clones < 1 || q.n_clones > POP_MAX_CLONES) return false;
+    if (q.weight_mode != POP_PLAIN) return false;
+    if (q.selection != POP_EQ) return false;
+  }
+  return true;
+}
+
+bool make_layout(const pop_params* params, int32_t n_pops, Layout* lay) {
+  if (!valid_params(params, n_pops)) return false;
+  Layout l;
+  l.P = n_pops;
+  int32_t maxL = 0;
+  int64_t ntiles = 0;
+  for (int32_t p = 0; p < n_pops; ++p) {
+    maxL = params[p].L > maxL ? params[p].L : maxL;
+    ntiles += (params[p].n_clones + kTile - 1) / kTile;
+  }
+  if (ntiles > (int64_t)INT32_MAX / 2) return false;
+  l.W = (maxL + 63) / 64;
+  l.ntiles = (int32_t)ntiles;
+  l.nslots = ntiles * kTile;
+  const size_t P = (size_t)n_pops, ns = (size_t)l.nslots, nt = (size_t)l.ntiles;
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };
+  l.o_pops = take(P * sizeof(PopDesc));
+  l.o_st = take(P * sizeof(PopState));
+  l.o_tile_pop = take(nt * sizeof(int32_t));
+  l.o_wtab = take(P * kKcap * sizeof(unsigned long long));
+  l.o_inv = take(P * kInvStride * sizeof(float));
+  l.o_hist = take(P * kKcap * sizeof(unsigned int));
+  l.o_status = take(2 * nt * sizeof(unsigned long long));
+  l.o_ticket = take(2 * sizeof(unsigned int));
+  l.o_beta = take(sizeof(unsigned int));
+  l.o_ksum = take(P * sizeof(long long));
+  l.o_X = take(ns * (size_t)l.W * sizeof(unsigned long long));
+  l.o_Y = take(ns * (size_t)l.W * sizeof(unsigned long long));
+  l.o_KX = take(ns * sizeof(int32_t));
+  l.o_KY = take(ns * sizeof(int32_t));
+  l.o_dK = take(ns * sizeof(int32_t));
+  l.o_anc = take(ns * sizeof(int32_t));
+  l.o_S = take(ns * sizeof(unsigned long long));
+  l.total = o;
+  *lay = l;
+  return true;
+}
+
+int ceil_log2(int64_t x) {
+  int c = 0;
+  while (((int64_t)1 << c) < x) ++c;
+  return c;
+}
+
+enum Phase { kReady = 0, kEvolved = 1 };
+
+}  // namespace
+
+struct pop_batch {
+  Layout lay;
+  std::vector<pop_params> params;
+  std::vector<PopDesc> desc;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  float graph_dt = 0.0f;
+  unsigned char* ws = nullptr;
+  Batch B{};
+  bool s_fixed = false;
+  std::vector<double> s;
+  Phase phase = kReady;
+  int64_t intervals = 0;
+  double t_obs = 0.0;
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? POP_OK : POP_ERR_CUDA; }
+
+#define POP_CUDA(call)                              \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return POP_ERR_CUDA;     \
+  } while (0)
+
+int fix_biases(pop_t* h, const double* s) {
+  if (s == nullptr) return POP_ERR_ARG;
+  for (int32_t p = 0; p < h->lay.P; ++p)
+    if (!std::isfinite(s[p])) return POP_ERR_ARG;
+  if (h->s_fixed) {
+    for (int32_t p = 0; p < h->lay.P; ++p)
+      if (s[p] != h->s[p]) return POP_ERR_STATE;
+    return POP_OK;
+  }
+  // Fixed-point weights (64-bit): F = 61 - ceil(log2 N_c), so N_c weights of at most
+  // 2^F sum to at most 2^61; wtab[k] = nearest integer to 2^F exp(-|s| k).
+  std::vector<unsigned long long> wtab((size_t)h->lay.P * kKcap);
+  for (int32_t p = 0; p < h->lay.P; ++p) {
+    const int F = 61 - ceil_log2(h->params[p].n_clones);
+    const double a = std::fabs(s[p]);
+    for (int k = 0; k < kKcap; ++k)
+      wtab[(size_t)p * kKcap + k] =
+          (unsigned long long)std::nearbyint(std::ldexp(std::exp(-a * (double)k), F));
+    h->desc[p].s = s[p];
+    h->desc[p].abs_s = a;
+  }
+  POP_CUDA(cudaMemcpyAsync(h->ws + h->lay.o_wtab, wtab.data(),
+                           wtab.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                           h->stream));
+  POP_CUDA(cudaMemcpyAsync(h->ws + h->lay.o_pops, h->desc.data(),
+                           h->desc.size() * sizeof(PopDesc), cudaMemcpyHostToDevice, h->stream));
+  POP_CUDA(cudaStreamSynchronize(h->stream));
+  h->s.assign(s, s + h->lay.P);
+  h->s_fixed = true;
+  return POP_OK;
+}
+
+bool valid_dt(double dt) { return std::isfinite(dt) && dt > 0.0 && dt < 1e30; }
+
+int launch_evolve(pop_t* h, cudaStream_t st, float dt_f) {
+  const unsigned grid = (unsigned)(h->lay.nslots / kThreads);
+  if (h->lay.W == 1) k_evolve<1><<<grid, kThreads, 0, st>>>(h->B, dt_f);
+  else k_evolve<2><<<grid, kThreads, 0, st>>>(h->B, dt_f);
+  return cuda_status(cudaGetLastError());
+}
+
+int launch_resample(pop_t* h, cudaStream_t st) {
+  k_scan<<<(unsigned)h->lay.ntiles, kThreads, 0, st>>>(h->B);
+  const unsigned grid = (unsigned)(h->lay.nslots / kThreads);
+  if (h->lay.W == 1) k_gather<1><<<grid, kThreads, 0, st>>>(h->B);
+  else k_gather<2><<<grid, kThreads, 0, st>>>(h->B);
+  return cuda_status(cudaGetLastError());
+}
+
+int check_device_errors(pop_t* h, std::vector<PopState>* out) {
+  std::vector<PopState> st((size_t)h->lay.P);
+  POP_CUDA(cudaMemcpyAsync(st.data(), h->ws + h->lay.o_st, st.size() * sizeof(PopState),
+                           cudaMemcpyDeviceToHost, h->stream));
+  POP_CUDA(cudaStreamSynchronize(h->stream));
+  for (const PopState& q : st)
+    if (q.err != 0) return q.err;
+  if (out) *out = std::move(st);
+  return POP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t pop_workspace_bytes(const pop_params* params, int32_t n_pops) {
+  Layout l;
+  if (!make_layout(params, n_pops, &l)) return 0;
+  return l.total;
+}
+
+int32_t pop_lattice_words(const pop_params* params, int32_t n_pops) {
+  Layout l;
+  if (!make_layout(params, n_pops, &l)) return 0;
+  return l.W;
+}
+
+int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_workspace,
+             size_t workspace_bytes, void* cuda_stream) {
+  if (out == nullptr) return POP_ERR_ARG;
+  *out = nullptr;
+  Layout lay;
+  if (!make_layout(params, n_pops, &lay)) return POP_ERR_ARG;
+  if (d_workspace == nullptr || workspace_bytes < lay.total) return POP_ERR_ARG;
+  if (((uintptr_t)d_workspace & 255u) != 0) return POP_ERR_ARG;
+
+  pop_t* h = new (std::nothrow) pop_batch();
+  if (h == nullptr) return POP_ERR_ARG;
+  h->lay = lay;
+  h->params.assign(params, params + n_pops);
+  h->stream = (cudaStream_t)cuda_stream;
+  h->ws = (unsigned char*)d_workspace;
+  auto fail = [&](int rc) { pop_free(h); return rc; };
+  if (cudaGetDevice(&h->device) != cudaSuccess) return fail(POP_ERR_CUDA);
+  if (cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(POP_ERR_CUDA);
+
+  // per-population descriptors and the tile map
+  std::vector<int32_t> tile_pop((size_t)lay.ntiles);
+  h->desc.resize((size_t)n_pops);
+  int32_t tile = 0;
+  for (int32_t p = 0; p < n_pops; ++p) {
+    PopDesc& d = h->desc[p];
+    d.L = params[p].L;
+    d.N = params[p].N;
+    d.nc = params[p].n_clones;
+    d.seed = params[p].seed;
+    d.first_tile = tile;
+    d.ntiles = (int32_t)((params[p].n_clones + kTile - 1) / kTile);
+    d.off = (int64_t)tile * kTile;
+    d.s = 0.0;
+    d.abs_s = 0.0;
+    for (int32_t t = 0; t < d.ntiles; ++t) tile_pop[(size_t)tile + t] = p;
+    tile += d.ntiles;
+  }
+  // float(1/r): the plain SSEP escape rate is the number r of active bonds
+  std::vector<float> inv((size_t)n_pops * kInvStride, 0.0f);
+  for (int32_t p = 0; p < n_pops; ++p)
+    for (int r = 1; r <= params[p].L; ++r) inv[(size_t)p * kInvStride + r] = 1.0f / (float)r;
+  std::vector<PopState> st((size_t)n_pops);
+  for (PopState& q : st) {
+    std::memset(&q, 0, sizeof q);
+    q.dk_min = INT_MAX;
+    q.dk_max = INT_MIN;
+  }
+  const unsigned int beta0 = 1u;
+
+  unsigned char* ws = h->ws;
+  if (cudaMemsetAsync(ws, 0, lay.total, h->stream) != cudaSuccess) return fail(POP_ERR_CUDA);
+  if (cudaMemcpyAsync(ws + lay.o_pops, h->desc.data(), h->desc.size() * sizeof(PopDesc),
+                      cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(ws + lay.o_st, st.data(), st.size() * sizeof(PopState),
+                      cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(ws + lay.o_tile_pop, tile_pop.data(), tile_pop.size() * sizeof(int32_t),
+                      cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(ws + lay.o_inv, inv.data(), inv.size() * sizeof(float),
+                      cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(ws + lay.o_beta, &beta0, sizeof beta0, cudaMemcpyHostToDevice,
+                      h->stream) != cudaSuccess)
+    return fail(POP_ERR_CUDA);
+
+  Batch& B = h->B;
+  B.pops = (const PopDesc*)(ws + lay.o_pops);
+  B.st = (PopState*)(ws + lay.o_st);
+  B.tile_pop = (const int32_t*)(ws + lay.o_tile_pop);
+  B.wtab = (const unsigned long long*)(ws + lay.o_wtab);
+  B.inv_rate = (const float*)(ws + lay.o_inv);
+  B.hist = (unsigned int*)(ws + lay.o_hist);
+  B.tile_status = (unsigned long long*)(ws + lay.o_status);
+  B.ticket = (unsigned int*)(ws + lay.o_ticket);
+  B.beta = (unsigned int*)(ws + lay.o_beta);
+  B.ksum = (long long*)(ws + lay.o_ksum);
+  B.X = (unsigned long long*)(ws + lay.o_X);
+  B.Y = (unsigned long long*)(ws + lay.o_Y);
+  B.KX = (int32_t*)(ws + lay.o_KX);
+  B.KY = (int32_t*)(ws + lay.o_KY);
+  B.dK = (int32_t*)(ws + lay.o_dK);
+  B.anc = (int32_t*)(ws + lay.o_anc);
+  B.S = (unsigned long long*)(ws + lay.o_S);
+  B.ntiles = lay.ntiles;
+  B.nslots = lay.nslots;
+
+  const unsigned grid = (unsigned)(lay.nslots / kThreads);
+  if (lay.W == 1) k_init<1><<<grid, kThreads, 0, h->stream>>>(B);
+  else k_init<2><<<grid, kThreads, 0, h->stream>>>(B);
+  if (cudaGetLastError() != cudaSuccess) return fail(POP_ERR_CUDA);
+  // host tables above are stack vectors: wait until their copies have landed
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(POP_ERR_CUDA);
+  *out = h;
+  return POP_OK;
+}
+
+int pop_set_state(pop_t* h, int32_t p, const uint64_t* h_lattice, const int32_t* h_K) {
+  if (h == nullptr || p < 0 || p >= h->lay.P || h_lattice == nullptr) return POP_ERR_ARG;
+  if (h->intervals != 0 || h->phase != kReady) return POP_ERR_STATE;
+  const pop_params& q = h->params[p];
+  const int W = h->lay.W;
+  for (int64_t j = 0; j < q.n_clones; ++j) {
+    int n = 0;
+    for (int w = 0; w < W; ++w) {
+      uint64_t v = h_lattice[j * W + w];
+      const int lo = 64 * w;
+      if (q.L < lo + 64) {
+        const int keep = q.L - lo;
+        const uint64_t mask = keep <= 0 ? 0ull : (keep >= 64 ? ~0ull : ((1ull << keep) - 1ull));
+        if (v & ~mask) return POP_ERR_ARG;
+      }
+      n += __builtin_popcountll(v);
+    }
+    if (n != q.N) return POP_ERR_ARG;
+  }
+  const PopDesc& d = h->desc[p];
+  POP_CUDA(cudaMemcpyAsync(h->B.Y + d.off * W, h_lattice, (size_t)q.n_clones * W * 8u,
+                           cudaMemcpyHostToDevice, h->stream));
+  if (h_K != nullptr) {
+    POP_CUDA(cudaMemcpyAsync(h->B.KY + d.off, h_K, (size_t)q.n_clones * 4u,
+                             cudaMemcpyHostToDevice, h->stream));
+  } else {
+    POP_CUDA(cudaMemsetAsync(h->B.KY + d.off, 0, (size_t)q.n_clones * 4u, h->stream));
+  }
+  POP_CUDA(cudaStreamSynchronize(h->stream));
+  return POP_OK;
+}
+
+int pop_evolve(pop_t* h, double dt, const double* s) {
+  if (h == nullptr || !valid_dt(dt)) return POP_ERR_ARG;
+  if (h->phase != kReady) return POP_ERR_STATE;
+  const int rc = fix_biases(h, s);
+  if (rc != POP_OK) return rc;
+  const int lr = launch_evolve(h, h->stream, (float)dt);
+  if (lr != POP_OK) return lr;
+  h->phase = kEvolved;
+  h->t_obs += dt;
+  return POP_OK;
+}
+
+int pop_resample(pop_t* h) {
+  if (h == nullptr) return POP_ERR_ARG;
+  if (h->phase != kEvolved) return POP_ERR_STATE;
+  const int lr = launch_resample(h, h->stream);
+  if (lr != POP_OK) return lr;
+  h->phase = kReady;
+  h->intervals += 1;
+  return POP_OK;
+}
+
+int pop_run(pop_t* h, double dt, const double* s, int64_t n_intervals) {
+  if (h == nullptr || !valid_dt(dt) || n_intervals < 0) return POP_ERR_ARG;
+  if (h->phase != kReady) return POP_ERR_STATE;
+  int rc = fix_biases(h, s);
+  if (rc != POP_OK) return rc;
+  if (n_intervals == 0) return POP_OK;
+  const float dt_f = (float)dt;
+  int64_t n_graph = n_intervals / kGraphIntervals;
+  const int64_t n_rest = n_intervals % kGraphIntervals;
+  if (n_graph > 0 && (h->graph == nullptr || h->graph_dt != dt_f)) {
+    if (h->graph != nullptr) {
+      cudaGraphExecDestroy(h->graph);
+      h->graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    POP_CUDA(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
+    int lr = POP_OK;
+    for (int i = 0; i < kGraphIntervals && lr == POP_OK; ++i) {
+      lr = launch_evolve(h, h->capture_stream, dt_f);
+      if (lr == POP_OK) lr = launch_resample(h, h->capture_stream);
+    }
+    const cudaError_t ec = cudaStreamEndCapture(h->capture_stream, &g);
+    if (lr != POP_OK || ec != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return POP_ERR_CUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      h->graph = nullptr;
+      return POP_ERR_CUDA;
+    }
+    h->graph_dt = dt_f;
+  }
+  for (int64_t i = 0; i < n_graph; ++i) POP_CUDA(cudaGraphLaunch(h->graph, h->stream));
+  for (int64_t i = 0; i < n_rest; ++i) {
+    rc = launch_evolve(h, h->stream, dt_f);
+    if (rc == POP_OK) rc = launch_resample(h, h->stream);
+    if (rc != POP_OK) return rc;
+  }
+  h->intervals += n_intervals;
+  h->t_obs += (double)n_intervals * dt;
+  return POP_OK;
+}
+
+int pop_estimate_psi(pop_t* h, double* psi, double* k_hat, double* t_obs) {
+  if (h == nullptr) return POP_ERR_ARG;
+  if (h->phase != kReady || h->intervals == 0) return POP_ERR_STATE;
+  POP_CUDA(cudaMemsetAsync(h->B.ksum, 0, (size_t)h->lay.P * sizeof(long long), h->stream));
+  k_ksum<<<(unsigned)(h->lay.nslots / kThreads), kThreads, 0, h->stream>>>(h->B);
+  POP_CUDA(cudaGetLastError());
+  std::vector<long long> ks((size_t)h->lay.P);
+  POP_CUDA(cudaMemcpyAsync(ks.data(), h->B.ksum, ks.size() * sizeof(long long),
+                           cudaMemcpyDeviceToHost, h->stream));
+  std::vector<PopState> st;
+  const int rc = check_device_errors(h, &st);
+  if (rc != POP_OK) return rc;
+  for (int32_t p = 0; p < h->lay.P; ++p) {
+    const pop_params& q = h->params[p];
+    if (psi) psi[p] = st[p].psi_acc / h->t_obs;
+    if (k_hat) k_hat[p] = (double)ks[p] / ((double)q.n_clones * (double)q.L * h->t_obs);
+  }
+  if (t_obs) *t_obs = h->t_obs;
+  return POP_OK;
+}
+
+int pop_copy_state(pop_t* h, int32_t p, uint64_t* h_lattice, int32_t* h_K, int32_t* h_anc,
+                   int32_t* h_dK) {
+  if (h == nullptr || p < 0 || p >= h->lay.P) return POP_ERR_ARG;
+  const PopDesc& d = h->desc[p];
+  const int W = h->lay.W;
+  const bool evolved = h->phase == kEvolved;
+  const unsigned long long* lat = evolved ? h->B.X : h->B.Y;
+  const int32_t* K = evolved ? h->B.KX : h->B.KY;
+  if (h_lattice)
+    POP_CUDA(cudaMemcpyAsync(h_lattice, lat + d.off * W, (size_t)d.nc * W * 8u,
+                             cudaMemcpyDeviceToHost, h->stream));
+  if (h_K)
+    POP_CUDA(cudaMemcpyAsync(h_K, K + d.off, (size_t)d.nc * 4u, cudaMemcpyDeviceToHost,
+                             h->stream));
+  if (h_anc)
+    POP_CUDA(cudaMemcpyAsync(h_anc, h->B.anc + d.off, (size_t)d.nc * 4u,
+                             cudaMemcpyDeviceToHost, h->stream));
+  if (h_dK)
+    POP_CUDA(cudaMemcpyAsync(h_dK, h->B.dK + d.off, (size_t)d.nc * 4u, cudaMemcpyDeviceToHost,
+                             h->stream));
+  return check_device_errors(h, nullptr);
+}
+
+int pop_events(pop_t* h, uint64_t* h_events) {
+  if (h == nullptr || h_events == nullptr) return POP_ERR_ARG;
+  std::vector<PopState> st;
+  const int rc = check_device_errors(h, &st);
+  if (rc != POP_OK) return rc;
+  for (int32_t p = 0; p < h->lay.P; ++p) h_events[p] = st[p].events;
+  return POP_OK;
+}
+
+const char* pop_strerror(int status) {
+  switch (status) {
+    case POP_OK: return "ok";
+    case POP_ERR_ARG: return "invalid argument";
+    case POP_ERR_CUDA: return "CUDA runtime error";
+    case POP_ERR_RANGE: return "interval activity outside the weight table";
+    case POP_ERR_TIMEOUT: return "device-side wait gave up";
+    case POP_ERR_STATE: return "call out of order or bias changed during a run";
+    default: return "unknown status";
+  }
+}
+
+void pop_free(pop_t* h) {
+  if (h == nullptr) return;
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,70 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds, loads and
+exports every function include/pop.h declares, and argument validation happens
+before any device work."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1711_05095_gb300 as pg
+from paper_1711_05095_gb300 import build as pbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pbuild.build()
+    return pg.library()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "pop.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pop_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert set(names) == set(pg.EXPORTS)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def P(**kw):
+    d = dict(L=20, N=10, n_clones=1000, seed=1)
+    d.update(kw)
+    return d
+
+
+def test_workspace_bytes(lib):
+    a = pg.workspace_bytes([P()])
+    b = pg.workspace_bytes([P(n_clones=5000)])
+    assert a > 0 and a % 256 == 0 and b > a
+    assert pg.lattice_words([P(L=64)]) == 1
+    assert pg.lattice_words([P(L=65), P(L=20)]) == 2
+    for bad in (P(L=2), P(L=129), P(N=-1), P(N=21), P(n_clones=0), P(weight_mode=7), P(selection=9)):
+        assert pg.workspace_bytes([bad]) == 0, bad
+
+
+def test_init_rejects_bad_arguments_without_device(lib):
+    h = ctypes.c_void_p()
+    good = pg.make_params([P()])
+    n = lib.pop_workspace_bytes(good, 1)
+    # too small a workspace, misaligned workspace, null workspace, invalid params
+    assert lib.pop_init(ctypes.byref(h), good, 1, ctypes.c_void_p(1 << 20), n - 256, None) == pg.POP_ERR_ARG
+    assert lib.pop_init(ctypes.byref(h), good, 1, ctypes.c_void_p((1 << 20) + 8), n, None) == pg.POP_ERR_ARG
+    assert lib.pop_init(ctypes.byref(h), good, 1, None, n, None) == pg.POP_ERR_ARG
+    bad = pg.make_params([P(N=99)])
+    assert lib.pop_init(ctypes.byref(h), bad, 1, ctypes.c_void_p(1 << 20), n, None) == pg.POP_ERR_ARG
+    assert h.value is None
+    assert lib.pop_evolve(None, 0.1, None) == pg.POP_ERR_ARG
+    assert lib.pop_resample(None) == pg.POP_ERR_ARG
+    lib.pop_free(None)
+
+
+def test_strerror(lib):
+    for code in (0, -1, -2, -3, -4, -5):
+        assert lib.pop_strerror(code)
+    assert pg.strerror(-3).startswith("interval activity")

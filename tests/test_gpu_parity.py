@@ -1,0 +1,218 @@
+"""GPU path (through the C ABI) against the CPU oracle on identical Philox streams.
+
+Bit-exact: lattices, cumulative activities K, interval activities dK and [eq]
+ancestors, every interval.  psi_hat within 1e-12 relative (the psi terms use CUDA's
+FP64 exp/expm1/log1p against glibc's; every other quantity is an integer).
+Cases span several 1024-slot tiles with ragged tails, both lattice widths
+(L <= 64 and 64 < L <= 128), both signs of s, s = 0, empty and full rings, one
+clone, and a batch of uneven populations.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+PSI_RTOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def pg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_05095_gb300 import build
+    build.build()
+    import paper_1711_05095_gb300 as pg
+    return pg
+
+
+def oracle_pops(pops):
+    return [oracle.Population(q["L"], q["N"], q["n_clones"], q["seed"]) for q in pops]
+
+
+def assert_state_equal(gpu, orc, W, what):
+    words = oracle.sites_to_words(orc.sites, W)
+    assert np.array_equal(gpu["lattice"], words), what + ": lattice"
+    assert np.array_equal(gpu["K"], orc.K), what + ": K"
+
+
+def run_parity(pg, pops, s, dt, M):
+    batch = pg.PopulationBatch(pops)
+    orcs = oracle_pops(pops)
+    W = batch.W
+    for p, o in enumerate(orcs):
+        assert_state_equal(batch.copy_state(p), o, W, "init pop %d" % p)
+    for beta in range(1, M + 1):
+        batch.evolve(dt, s)
+        for p, o in enumerate(orcs):
+            o.evolve(dt)
+            g = batch.copy_state(p)
+            assert_state_equal(g, o, W, "evolve beta=%d pop %d" % (beta, p))
+            assert np.array_equal(g["dK"], o.dK), "dK beta=%d pop %d" % (beta, p)
+        batch.resample()
+        for p, o in enumerate(orcs):
+            o.resample(s[p])
+            g = batch.copy_state(p)
+            assert np.array_equal(g["anc"], o.anc), "anc beta=%d pop %d" % (beta, p)
+            assert_state_equal(g, o, W, "resample beta=%d pop %d" % (beta, p))
+    psi, kh, t_obs = batch.estimate_psi()
+    ev = batch.events()
+    for p, o in enumerate(orcs):
+        ps, ks = o.estimates()
+        np.testing.assert_allclose(psi[p], ps, rtol=PSI_RTOL, atol=0.0)
+        np.testing.assert_allclose(kh[p], ks, rtol=1e-15, atol=0.0)
+        assert int(ev[p]) == o.events
+    return batch, orcs
+
+
+@pytest.mark.parametrize("L,N,nc,s", [
+    (20, 10, 1000, 0.05),      # one tile, ragged
+    (20, 10, 2500, -0.3),      # three tiles, negative bias
+    (50, 25, 3072, 0.3),       # exact tiles
+    (64, 31, 1500, 0.8),       # widest one-word ring
+    (65, 30, 1100, 0.2),       # narrowest two-word ring
+    (100, 50, 2049, -0.05),
+    (128, 64, 4100, 0.01),     # widest ring
+    (3, 1, 777, 0.4),          # smallest ring
+    (37, 5, 1, 0.5),           # one clone
+    (20, 10, 1234, 0.0),       # no bias: identity ancestry
+    (12, 0, 300, 0.3),         # empty ring: no hops
+    (12, 12, 300, -0.3),       # full ring: no hops
+    (40, 20, 3000, 2.5),       # strong bias: many deletions
+])
+def test_parity_single(pg, L, N, nc, s):
+    pops = [dict(L=L, N=N, n_clones=nc, seed=1234 + L)]
+    batch, orcs = run_parity(pg, pops, [s], 0.1 if L < 100 else 0.05, 6)
+    if s == 0.0:
+        g = batch.copy_state(0)
+        assert np.array_equal(g["anc"], np.arange(nc))
+        assert batch.estimate_psi()[0][0] == 0.0
+
+
+def test_parity_uneven_batch(pg):
+    rng = np.random.default_rng(5)
+    pops, s = [], []
+    for i, L in enumerate([32, 64, 100, 128, 20, 77]):
+        pops.append(dict(L=L, N=L // 2 - i, n_clones=int(rng.integers(900, 3000)), seed=99 + i))
+        s.append(float(rng.uniform(-10, 30)) / L**2)
+    run_parity(pg, pops, s, 0.1, 5)
+
+
+def test_parity_long_dt(pg):
+    # many hops per interval (dt = 2 at L = 50: ~50 hops per clone)
+    run_parity(pg, [dict(L=50, N=25, n_clones=1500, seed=3)], [0.02], 2.0, 3)
+
+
+def test_run_equals_steps(pg):
+    pops = [dict(L=50, N=25, n_clones=2000, seed=7), dict(L=100, N=40, n_clones=1300, seed=8)]
+    s = [0.01, -0.004]
+    a = pg.PopulationBatch(pops)
+    b = pg.PopulationBatch(pops)
+    n = 70  # two captured graphs of 32 intervals plus 6 direct intervals
+    a.run(0.1, s, n)
+    for _ in range(n):
+        b.evolve(0.1, s)
+        b.resample()
+    for p in range(2):
+        ga, gb = a.copy_state(p), b.copy_state(p)
+        for key in ("lattice", "K", "anc", "dK"):
+            assert np.array_equal(ga[key], gb[key]), key
+    pa, ka, ta = a.estimate_psi()
+    pb, kb, tb = b.estimate_psi()
+    # same device arithmetic; only t_obs differs in rounding (n*dt against a sum of dt)
+    np.testing.assert_allclose(pa * ta, pb * tb, rtol=1e-15)
+    np.testing.assert_allclose(pa, pb, rtol=1e-14)
+    np.testing.assert_allclose(ka, kb, rtol=1e-14)
+    np.testing.assert_allclose(ta, tb, rtol=1e-13)
+    np.testing.assert_array_equal(a.events(), b.events())
+
+
+def test_full_size_s_sweep_sampled(pg):
+    # the 64-population s-sweep at full size (2^20 clones) in the bench's launch
+    # configuration (pop_run); three sampled populations checked bit for bit
+    w = workloads.s_sweep()
+    M = 4
+    batch = pg.PopulationBatch(w["pops"])
+    batch.run(w["dt"], w["s"], M)
+    psi, _, _ = batch.estimate_psi()
+    for p in (0, 31, 63):
+        q = w["pops"][p]
+        o = oracle.Population(q["L"], q["N"], q["n_clones"], q["seed"])
+        for _ in range(M):
+            o.evolve(w["dt"])
+            o.resample(w["s"][p])
+        g = batch.copy_state(p)
+        assert np.array_equal(g["anc"], o.anc)
+        assert_state_equal(g, o, batch.W, "s-sweep pop %d" % p)
+        np.testing.assert_allclose(psi[p], o.estimates()[0], rtol=PSI_RTOL)
+    # properties at every population: N conserved, ancestors monotone and in range
+    for p in range(0, 64, 9):
+        g = batch.copy_state(p)
+        counts = sum(np.vectorize(lambda v: bin(int(v)).count("1"))(g["lattice"][:, q])
+                     for q in range(batch.W))
+        assert np.all(counts == w["pops"][p]["N"])
+        assert np.all(np.diff(g["anc"]) >= 0)
+        assert g["anc"].min() >= 0 and g["anc"].max() < w["pops"][p]["n_clones"]
+
+
+def test_full_size_large_population_one_interval(pg):
+    # one population at the largest size (L = 128, N_c = 2^20), one interval
+    q = dict(L=128, N=64, n_clones=2**20, seed=2000)
+    s = 15.0 / 128**2
+    batch = pg.PopulationBatch([q])
+    batch.evolve(0.05, [s])
+    batch.resample()
+    o = oracle.Population(q["L"], q["N"], q["n_clones"], q["seed"])
+    o.evolve(0.05)
+    o.resample(s)
+    g = batch.copy_state(0)
+    assert np.array_equal(g["anc"], o.anc)
+    assert np.array_equal(g["dK"], o.dK)
+    assert_state_equal(g, o, batch.W, "large population")
+    np.testing.assert_allclose(batch.estimate_psi()[0][0], o.estimates()[0], rtol=PSI_RTOL)
+
+
+def test_set_state_from_host(pg):
+    q = dict(L=70, N=33, n_clones=1500, seed=42)
+    words = workloads.random_subsets(q["L"], q["N"], q["n_clones"], seed=9)
+    K0 = np.arange(q["n_clones"], dtype=np.int32)
+    batch = pg.PopulationBatch([q])
+    batch.set_state(0, words, K0)
+    g = batch.copy_state(0)
+    assert np.array_equal(g["lattice"], words) and np.array_equal(g["K"], K0)
+    sites = np.zeros((q["n_clones"], q["L"]), dtype=np.uint8)
+    for i in range(q["L"]):
+        sites[:, i] = (words[:, i // 64] >> np.uint64(i % 64)) & np.uint64(1)
+    out, K, dK = oracle.evolve_sites(q["L"], sites, 0.1, beta=1, seed=q["seed"], K=K0)
+    batch.evolve(0.1, [0.1])
+    g = batch.copy_state(0)
+    assert np.array_equal(g["lattice"], oracle.sites_to_words(out, batch.W))
+    assert np.array_equal(g["K"], K) and np.array_equal(g["dK"], dK)
+    with pytest.raises(pg.PopError):
+        bad = words.copy()
+        bad[0, 0] ^= np.uint64(1)   # wrong particle number
+        pg.PopulationBatch([q]).set_state(0, bad)
+
+
+def test_call_order_and_bias_errors(pg):
+    batch = pg.PopulationBatch([dict(L=20, N=10, n_clones=100, seed=1)])
+    with pytest.raises(pg.PopError) as e:
+        batch.resample()
+    assert e.value.status == pg.POP_ERR_STATE
+    with pytest.raises(pg.PopError) as e:
+        batch.estimate_psi()
+    assert e.value.status == pg.POP_ERR_STATE
+    batch.evolve(0.1, [0.2])
+    with pytest.raises(pg.PopError) as e:
+        batch.evolve(0.1, [0.2])
+    assert e.value.status == pg.POP_ERR_STATE
+    batch.resample()
+    with pytest.raises(pg.PopError) as e:
+        batch.evolve(0.1, [0.3])
+    assert e.value.status == pg.POP_ERR_STATE
+    with pytest.raises(pg.PopError) as e:
+        batch.evolve(-0.1, [0.2])
+    assert e.value.status == pg.POP_ERR_ARG
