@@ -29,9 +29,10 @@
  *      The slot j is the clone's position in the population, after resampling.
  *      One evolve draw serves two BKL steps: step e of the interval uses draw
  *      q = e/2, words (w0, w1) when e is even and (w2, w3) when e is odd.
- *   R2 exponential variate: u = (2*wa + 1) / 2^33 from the step's first word wa;
- *      E = -ln(u) by the FP32 logarithm defined in neg_ln_u() below (written from
- *      ln(m 2^n) = n ln 2 + 2 atanh((m-1)/(m+1)); no library log).
+ *   R2 exponential variate: u = (2*wa + 1) / 2^33 from the step's first word wa,
+ *      with 2*wa+1 truncated to 24 significant bits; E = -ln(u) by the FP32
+ *      logarithm defined in orc_neg_ln_u() below (ln(m 2^n) = n ln 2 + ln c +
+ *      ln(1 + r) with c from a 64-entry table; no library log at run time).
  *   R3 time arithmetic in FP32: tau = E * (1/r) with 1/r rounded to float,
  *      t_new = t + tau; the interval ends when t_new >= (float)dt (no hop).
  *   R4 bond choice: k = floor(wb * r / 2^32) with wb the step's second word (a
@@ -109,46 +110,51 @@ static uint64_t mul_hi_64(uint64_t a, uint64_t b) {
 
 /* ---------------------------------------------------------------------------
  * Reading R2: E = -ln(u), u = (2w+1)/2^33, in FP32.
- * v = 2w+1 is rounded once to float (round-to-nearest-even), v = m 2^e with m in
- * [1,2), folded to m in (sqrt(1/2), sqrt(2)].  Then
- *   ln u = (e - 33) ln 2 + ln m,   ln m = 2 atanh(f),  f = (m-1)/(m+1),
- *   2 atanh(f) = f (2 + 2/3 z + 2/5 z^2 + 2/7 z^3 + 2/9 z^4 + ...),  z = f^2,
- * truncated after the z^4 term (|f| <= 0.1716, so the first dropped term is
- * below 1e-9 relative).  ln 2 is split into a 15-bit head (exact products with
- * |e-33| <= 33) and a float tail.
+ * v = 2w+1 (33 bits, odd) is truncated to its 24 leading bits: v' = t 2^(p-23)
+ * with t in [2^23, 2^24) and p the position of the leading one, so
+ * v' = m 2^p with m = t / 2^23 in [1, 2) (exact in float).  Then
+ *   ln u' = (p - 33) ln 2 + ln m,
+ *   ln m = ln c_i + ln(1 + r),   c_i = 1 + (i + 1/2)/64,  i = top 6 fraction bits of m,
+ *   r = m / c_i - 1 (|r| <= 1/128),  ln(1 + r) ~ r (1 - r/2 + r^2/3)
+ * (the first dropped term is below 1e-9).  The table holds float(1/c_i) and
+ * float(ln c_i), each rounded once from FP64.  ln 2 is split into a 15-bit head
+ * (exact products with the small integer 33 - p) and a float tail.
  * ------------------------------------------------------------------------- */
-static const float ORC_SQRT2 = 0x1.6a09e6p+0f;
 static const float ORC_LN2_HI = 0x1.62e4p-1f;
 static const float ORC_LN2_LO = 0x1.7f7d1cp-20f;
-static const float ORC_C3 = 0x1.555556p-1f; /* 2/3 */
-static const float ORC_C5 = 0x1.99999ap-2f; /* 2/5 */
-static const float ORC_C7 = 0x1.24924ap-2f; /* 2/7 */
-static const float ORC_C9 = 0x1.c71c72p-3f; /* 2/9 */
+static const float ORC_THIRD = 0x1.555556p-2f; /* 1/3 */
+
+static float orc_tab_inv_c[64];
+static float orc_tab_ln_c[64];
+static int orc_tab_ready = 0;
+
+static void orc_log_table(void) {
+  for (int i = 0; i < 64; ++i) {
+    double c = 1.0 + ((double)i + 0.5) / 64.0;
+    orc_tab_inv_c[i] = (float)(1.0 / c);
+    orc_tab_ln_c[i] = (float)log(c);
+  }
+  orc_tab_ready = 1;
+}
 
 float orc_neg_ln_u(uint32_t w) {
+  if (!orc_tab_ready) orc_log_table();
   uint64_t v = 2u * (uint64_t)w + 1u;
-  float vf = (float)v;
-  uint32_t bits;
-  memcpy(&bits, &vf, sizeof bits);
-  int e = (int)((bits >> 23) & 0xffu) - 127;
-  uint32_t mbits = (bits & 0x007fffffu) | 0x3f800000u;
+  int p = 0;
+  while ((v >> (p + 1)) != 0u) ++p;
+  uint32_t t = (p >= 23) ? (uint32_t)(v >> (p - 23)) : (uint32_t)(v << (23 - p));
+  uint32_t mbits = 0x3f800000u | (t & 0x007fffffu);
   float m;
   memcpy(&m, &mbits, sizeof m);
-  if (m > ORC_SQRT2) {
-    m = m * 0.5f;
-    e += 1;
-  }
-  float f = (m - 1.0f) / (m + 1.0f);
-  float z = f * f;
-  float p = fmaf(ORC_C9, z, ORC_C7);
-  p = fmaf(p, z, ORC_C5);
-  p = fmaf(p, z, ORC_C3);
-  p = fmaf(p, z, 2.0f);
-  float ln_m = f * p;
-  float n = (float)(e - 33);
-  float ln_u = fmaf(n, ORC_LN2_LO, ln_m);
-  ln_u = fmaf(n, ORC_LN2_HI, ln_u);
-  return -ln_u;
+  int i = (int)((t >> 17) & 63u);
+  float r = fmaf(m, orc_tab_inv_c[i], -1.0f);
+  float q = fmaf(r, ORC_THIRD, -0.5f);
+  q = fmaf(q, r, 1.0f);
+  float ln_m = orc_tab_ln_c[i] + q * r;
+  float n = (float)(33 - p);
+  float E = fmaf(n, ORC_LN2_LO, -ln_m);
+  E = fmaf(n, ORC_LN2_HI, E);
+  return E;
 }
 
 /* ---------------------------------------------------------------------------
