@@ -2,12 +2,12 @@
 //
 // A handle owns only host state; every device buffer is carved out of the
 // caller's workspace.  Layout of the workspace (each region 256-byte aligned):
-//   PopDesc[P]  PopState[P]  tile_pop[ntiles]  wtab[P][4096] u64  inv_rate[P][129] f32
-//   hist[P][4096] u32  tile_status[2][ntiles] u64  ticket[2]  beta  ksum[P]
-//   X, Y lattices [nslots][W] u64   KX, KY, dK, anc [nslots] i32   S [nslots] u64
+//   PopDesc[P]  PopState[P]  tile_pop[ntiles]  wtab[P][4096] u64  qtab, qm1tab[P][4096] f64
+//   inv_rate[P][129] f32  logtab[64] f32x2  hist[P][4096] u32  tile_sum[ntiles] u64  beta  ksum[P]
+//   X, Y lattices [nslots][W] u64   KX, KY, dK, anc [nslots] i32
 // where every population starts on a 1024-slot tile and nslots is the padded total.
 //
-// One interval = k_evolve, k_scan, k_gather on the caller's stream.  pop_run captures
+// One interval = k_evolve, k_weights, k_gather on the caller's stream.  pop_run captures
 // kGraphIntervals intervals into a CUDA graph once (on a private capture stream) and
 // replays it on the caller's stream; the kernels read the interval number and every
 // other changing quantity from device memory, so replays need no new arguments.
@@ -27,10 +27,10 @@ namespace {
 constexpr int kGraphIntervals = 32;
 
 struct Layout {
-  int32_t P = 0, W = 0, ntiles = 0;
+  int32_t P = 0, W = 0, ntiles = 0, nunits = 0;
   int64_t nslots = 0;
-  size_t o_pops, o_st, o_tile_pop, o_wtab, o_inv, o_hist, o_status, o_ticket, o_beta,
-      o_ksum, o_X, o_Y, o_KX, o_KY, o_dK, o_anc, o_S, total;
+  size_t o_pops, o_st, o_tile_pop, o_wtab, o_qtab, o_qm1tab, o_inv, o_logtab, o_hist, o_tile_sum, o_beta,
+      o_ksum, o_X, o_Y, o_KX, o_KY, o_dK, o_anc, total;
 };
 
 size_t align256(size_t x) { return (x + 255u) & ~(size_t)255u; }
@@ -62,6 +62,7 @@ bool make_layout(const pop_params* params, int32_t n_pops, Layout* lay) {
   l.W = (maxL + 63) / 64;
   l.ntiles = (int32_t)ntiles;
   l.nslots = ntiles * kTile;
+  l.nunits = (int32_t)(l.nslots / kUnit);
   const size_t P = (size_t)n_pops, ns = (size_t)l.nslots, nt = (size_t)l.ntiles;
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };
@@ -69,10 +70,12 @@ bool make_layout(const pop_params* params, int32_t n_pops, Layout* lay) {
   l.o_st = take(P * sizeof(PopState));
   l.o_tile_pop = take(nt * sizeof(int32_t));
   l.o_wtab = take(P * kKcap * sizeof(unsigned long long));
+  l.o_qtab = take(P * kKcap * sizeof(double));
+  l.o_qm1tab = take(P * kKcap * sizeof(double));
   l.o_inv = take(P * kInvStride * sizeof(float));
+  l.o_logtab = take(64 * sizeof(float2));
   l.o_hist = take(P * kKcap * sizeof(unsigned int));
-  l.o_status = take(2 * nt * sizeof(unsigned long long));
-  l.o_ticket = take(2 * sizeof(unsigned int));
+  l.o_tile_sum = take(nt * sizeof(unsigned long long));
   l.o_beta = take(sizeof(unsigned int));
   l.o_ksum = take(P * sizeof(long long));
   l.o_X = take(ns * (size_t)l.W * sizeof(unsigned long long));
@@ -81,7 +84,6 @@ bool make_layout(const pop_params* params, int32_t n_pops, Layout* lay) {
   l.o_KY = take(ns * sizeof(int32_t));
   l.o_dK = take(ns * sizeof(int32_t));
   l.o_anc = take(ns * sizeof(int32_t));
-  l.o_S = take(ns * sizeof(unsigned long long));
   l.total = o;
   *lay = l;
   return true;
@@ -108,6 +110,8 @@ struct pop_batch {
   float graph_dt = 0.0f;
   unsigned char* ws = nullptr;
   Batch B{};
+  int evolve_grid = 0;
+  size_t evolve_smem = 0;
   bool s_fixed = false;
   std::vector<double> s;
   Phase phase = kReady;
@@ -135,20 +139,31 @@ int fix_biases(pop_t* h, const double* s) {
     return POP_OK;
   }
   // Fixed-point weights (64-bit): F = 61 - ceil(log2 N_c), so N_c weights of at most
-  // 2^F sum to at most 2^61; wtab[k] = nearest integer to 2^F exp(-|s| k).
-  std::vector<unsigned long long> wtab((size_t)h->lay.P * kKcap);
+  // 2^F sum to at most 2^61; wtab[k] = nearest integer to 2^F exp(-|s| k).  The psi
+  // term uses exp(-|s| k) and expm1(-|s| k) in FP64 (qtab, qm1tab).
+  const size_t n = (size_t)h->lay.P * kKcap;
+  std::vector<unsigned long long> wtab(n);
+  std::vector<double> qtab(n), qm1tab(n);
   for (int32_t p = 0; p < h->lay.P; ++p) {
     const int F = 61 - ceil_log2(h->params[p].n_clones);
     const double a = std::fabs(s[p]);
-    for (int k = 0; k < kKcap; ++k)
-      wtab[(size_t)p * kKcap + k] =
-          (unsigned long long)std::nearbyint(std::ldexp(std::exp(-a * (double)k), F));
+    for (int k = 0; k < kKcap; ++k) {
+      const double x = -a * (double)k;
+      const double q = std::exp(x);
+      wtab[(size_t)p * kKcap + k] = (unsigned long long)std::nearbyint(std::ldexp(q, F));
+      qtab[(size_t)p * kKcap + k] = q;
+      qm1tab[(size_t)p * kKcap + k] = std::expm1(x);
+    }
     h->desc[p].s = s[p];
     h->desc[p].abs_s = a;
+    h->desc[p].s_neg = s[p] < 0.0 ? 1 : 0;
   }
-  POP_CUDA(cudaMemcpyAsync(h->ws + h->lay.o_wtab, wtab.data(),
-                           wtab.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice,
-                           h->stream));
+  POP_CUDA(cudaMemcpyAsync(h->ws + h->lay.o_wtab, wtab.data(), n * sizeof(unsigned long long),
+                           cudaMemcpyHostToDevice, h->stream));
+  POP_CUDA(cudaMemcpyAsync(h->ws + h->lay.o_qtab, qtab.data(), n * sizeof(double),
+                           cudaMemcpyHostToDevice, h->stream));
+  POP_CUDA(cudaMemcpyAsync(h->ws + h->lay.o_qm1tab, qm1tab.data(), n * sizeof(double),
+                           cudaMemcpyHostToDevice, h->stream));
   POP_CUDA(cudaMemcpyAsync(h->ws + h->lay.o_pops, h->desc.data(),
                            h->desc.size() * sizeof(PopDesc), cudaMemcpyHostToDevice, h->stream));
   POP_CUDA(cudaStreamSynchronize(h->stream));
@@ -160,18 +175,35 @@ int fix_biases(pop_t* h, const double* s) {
 bool valid_dt(double dt) { return std::isfinite(dt) && dt > 0.0 && dt < 1e30; }
 
 int launch_evolve(pop_t* h, cudaStream_t st, float dt_f) {
-  const unsigned grid = (unsigned)(h->lay.nslots / kThreads);
-  if (h->lay.W == 1) k_evolve<1><<<grid, kThreads, 0, st>>>(h->B, dt_f);
-  else k_evolve<2><<<grid, kThreads, 0, st>>>(h->B, dt_f);
+  const unsigned grid = (unsigned)h->evolve_grid;
+  if (h->lay.W == 1) k_evolve<1><<<grid, kThreads, h->evolve_smem, st>>>(h->B, dt_f);
+  else k_evolve<2><<<grid, kThreads, h->evolve_smem, st>>>(h->B, dt_f);
   return cuda_status(cudaGetLastError());
 }
 
 int launch_resample(pop_t* h, cudaStream_t st) {
-  k_scan<<<(unsigned)h->lay.ntiles, kThreads, 0, st>>>(h->B);
-  const unsigned grid = (unsigned)(h->lay.nslots / kThreads);
+  const unsigned grid = (unsigned)h->lay.ntiles;
+  k_weights<<<grid, kThreads, 0, st>>>(h->B);
   if (h->lay.W == 1) k_gather<1><<<grid, kThreads, 0, st>>>(h->B);
   else k_gather<2><<<grid, kThreads, 0, st>>>(h->B);
   return cuda_status(cudaGetLastError());
+}
+
+// Persistent evolve grid: as many blocks as fit on the device at once, each
+// owning an equal share of the 256-slot units.
+template <int W>
+int size_evolve_grid(pop_t* h) {
+  const size_t smem = sizeof(EvolveSmem<W>);
+  POP_CUDA(cudaFuncSetAttribute(k_evolve<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+  int per_sm = 0, sms = 0;
+  POP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_evolve<W>, kThreads, smem));
+  POP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+  if (per_sm < 1) per_sm = 1;
+  const long long want = (long long)per_sm * sms;
+  h->evolve_grid = (int)(want < h->lay.nunits ? want : h->lay.nunits);
+  h->evolve_smem = smem;
+  return POP_OK;
 }
 
 int check_device_errors(pop_t* h, std::vector<PopState>* out) {
@@ -236,6 +268,8 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
     d.off = (int64_t)tile * kTile;
     d.s = 0.0;
     d.abs_s = 0.0;
+    d.s_neg = 0;
+    d.pad = 0;
     for (int32_t t = 0; t < d.ntiles; ++t) tile_pop[(size_t)tile + t] = p;
     tile += d.ntiles;
   }
@@ -243,6 +277,12 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
   std::vector<float> inv((size_t)n_pops * kInvStride, 0.0f);
   for (int32_t p = 0; p < n_pops; ++p)
     for (int r = 1; r <= params[p].L; ++r) inv[(size_t)p * kInvStride + r] = 1.0f / (float)r;
+  // waiting-time logarithm: c_i = 1 + (i + 1/2)/64, (float(1/c_i), float(ln c_i))
+  std::vector<float2> logtab(64);
+  for (int i = 0; i < 64; ++i) {
+    const double c = 1.0 + ((double)i + 0.5) / 64.0;
+    logtab[i] = make_float2((float)(1.0 / c), (float)std::log(c));
+  }
   std::vector<PopState> st((size_t)n_pops);
   for (PopState& q : st) {
     std::memset(&q, 0, sizeof q);
@@ -261,6 +301,8 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
                       cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
       cudaMemcpyAsync(ws + lay.o_inv, inv.data(), inv.size() * sizeof(float),
                       cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(ws + lay.o_logtab, logtab.data(), logtab.size() * sizeof(float2),
+                      cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
       cudaMemcpyAsync(ws + lay.o_beta, &beta0, sizeof beta0, cudaMemcpyHostToDevice,
                       h->stream) != cudaSuccess)
     return fail(POP_ERR_CUDA);
@@ -270,10 +312,12 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
   B.st = (PopState*)(ws + lay.o_st);
   B.tile_pop = (const int32_t*)(ws + lay.o_tile_pop);
   B.wtab = (const unsigned long long*)(ws + lay.o_wtab);
+  B.qtab = (const double*)(ws + lay.o_qtab);
+  B.qm1tab = (const double*)(ws + lay.o_qm1tab);
   B.inv_rate = (const float*)(ws + lay.o_inv);
+  B.logtab = (const float2*)(ws + lay.o_logtab);
   B.hist = (unsigned int*)(ws + lay.o_hist);
-  B.tile_status = (unsigned long long*)(ws + lay.o_status);
-  B.ticket = (unsigned int*)(ws + lay.o_ticket);
+  B.tile_sum = (unsigned long long*)(ws + lay.o_tile_sum);
   B.beta = (unsigned int*)(ws + lay.o_beta);
   B.ksum = (long long*)(ws + lay.o_ksum);
   B.X = (unsigned long long*)(ws + lay.o_X);
@@ -282,9 +326,11 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
   B.KY = (int32_t*)(ws + lay.o_KY);
   B.dK = (int32_t*)(ws + lay.o_dK);
   B.anc = (int32_t*)(ws + lay.o_anc);
-  B.S = (unsigned long long*)(ws + lay.o_S);
   B.ntiles = lay.ntiles;
+  B.nunits = lay.nunits;
   B.nslots = lay.nslots;
+  if ((lay.W == 1 ? size_evolve_grid<1>(h) : size_evolve_grid<2>(h)) != POP_OK)
+    return fail(POP_ERR_CUDA);
 
   const unsigned grid = (unsigned)(lay.nslots / kThreads);
   if (lay.W == 1) k_init<1><<<grid, kThreads, 0, h->stream>>>(B);

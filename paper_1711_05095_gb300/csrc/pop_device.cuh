@@ -1,18 +1,23 @@
 // Device code of the SSEP cloning library (sm_103a).
 //
 // One interval of the cloning algorithm (arXiv:1711.05095, Sec. 2.3) is three
-// kernels over a batch of populations laid out back to back in "slots":
+// kernels over a batch of populations laid out back to back in "slots" (every
+// population starts on a 1024-slot tile):
 //   k_evolve   dynamical stage (Sec. 4: BKL continuous-time Monte Carlo of the SSEP,
-//              Sec. 3.1 rates), one clone per thread, lattice in registers as a
-//              bitmask; epilogue: per-population min/max of the interval activity.
-//   k_scan     weights exp(-s dK) in 64-bit fixed point, exact single-pass prefix
-//              sum per population (decoupled look-back), histogram of the activity;
-//              the last tile of a population adds the psi term of eq. (psihat).
-//   k_gather   [eq] selection (Sec. 4.1, eq. alpha-Ups) inverted per old clone in
-//              exact integers, then a warp-cooperative coalesced pull copy of the
-//              lattices and carried activities (eq. khat).
+//              Sec. 3.1 rates).  A persistent grid; each block owns an equal range of
+//              256-slot units, stages the clones in shared memory and advances them in
+//              rounds of one BKL step per running clone, compacting the running clones
+//              after each round so that every lane does useful work.  Epilogue: the
+//              per-population min/max of the interval activity.
+//   k_weights  fixed-point weights exp(-s dK) (64-bit), their per-tile sums and the
+//              histogram of the interval activity.
+//   k_gather   per tile: the exclusive prefix sums of the weights (tile sums, then a
+//              block scan), [eq] selection (Sec. 4.1, eq. alpha-Ups) inverted per old
+//              clone in exact integers, and a pull copy of lattices and carried
+//              activities (eq. khat) staged through shared memory.  The first tile of
+//              each population adds the psi term of eq. (psihat).
 // All arithmetic that decides an integer result (waiting times, bond choice,
-// weights, ancestors) is specified bit for bit; see pop_api.cu for the contract.
+// weights, ancestors) is specified bit for bit; pop_api.cu states the contract.
 #pragma once
 
 #include <cstdint>
@@ -27,21 +32,20 @@ constexpr uint32_t kTagResample = 3u;
 
 constexpr int kThreads = 256;             // threads per block of every kernel
 constexpr int kWarps = kThreads / 32;
-constexpr int kTile = 1024;               // slots per scan tile; populations start on a tile
-constexpr int kItems = kTile / kThreads;  // slots per scan thread
+constexpr int kTile = 1024;               // slots per tile; populations start on a tile
+constexpr int kItems = kTile / kThreads;  // slots per thread in the tile kernels
+constexpr int kUnit = 256;                // slots per evolve work unit (one population)
+constexpr int kChunkUnits = 7;            // at most this many units staged in shared memory
+constexpr int kChunk = kUnit * kChunkUnits;
 constexpr int kKcap = 4096;               // fixed-point weight table size
 constexpr int kHistSmem = 512;            // activity bins kept in shared memory
-constexpr int kMaxL = 128;                // one-clone-per-thread lattices: W <= 2 words
+constexpr int kMap = 2048;                // new slots of one tile mapped in shared memory
+constexpr int kMaxL = 128;                // one clone per lane: W <= 2 words
 constexpr int kInvStride = kMaxL + 1;     // per-population 1/r table stride
-
-constexpr unsigned long long kStatusAgg = 1ull << 62;  // tile aggregate published
-constexpr unsigned long long kStatusPre = 2ull << 62;  // tile inclusive prefix published
-constexpr unsigned long long kValueMask = (1ull << 62) - 1ull;
-constexpr uint32_t kSpinLimit = 1u << 22;
-constexpr uint32_t kStepLimit = 1u << 24;  // BKL steps per clone per interval
+constexpr uint32_t kStepLimit = 1u << 24; // BKL steps per clone per interval
+constexpr int kFinish = kThreads / 2;     // fewer running clones: finish them one per thread
 
 constexpr int32_t kErrRange = -3;
-constexpr int32_t kErrTimeout = -4;
 
 // Constant per run.
 struct PopDesc {
@@ -50,16 +54,17 @@ struct PopDesc {
   int64_t off;       // first slot of the population (a multiple of kTile)
   uint64_t seed;     // Philox key
   int32_t first_tile, ntiles;
+  int32_t s_neg;     // s < 0: the reference activity is the maximum
+  int32_t pad;
   double s;          // bias
   double abs_s;
 };
 
 // Mutable per population.
 struct PopState {
-  int32_t dk_min, dk_max;      // interval activity range (evolve epilogue; reset by k_scan)
-  uint32_t done;               // scan tiles finished this interval
-  uint32_t U;                  // [eq] offset word of this interval
-  unsigned long long T;        // total fixed-point weight of this interval
+  int32_t dk_min, dk_max;      // interval activity range (k_evolve; reset by k_gather)
+  int32_t kref;                // reference activity of this interval (k_weights)
+  uint32_t U;                  // [eq] offset word of this interval (k_weights)
   double psi_acc;              // sum of psi terms (eq. psihat numerator)
   unsigned long long events;   // executed hops since init
   int32_t err;                 // sticky kernel-side error
@@ -71,20 +76,22 @@ struct Batch {
   PopState* st;
   const int32_t* tile_pop;              // tile -> population
   const unsigned long long* wtab;       // [P][kKcap] fixed-point weights
+  const double* qtab;                   // [P][kKcap] exp(-|s| k)
+  const double* qm1tab;                 // [P][kKcap] expm1(-|s| k)
   const float* inv_rate;                // [P][kInvStride] float(1/r)
-  unsigned int* hist;                   // [P][kKcap] activity histogram (kept zero between intervals)
-  unsigned long long* tile_status;      // [2][ntiles] look-back words, by interval parity
-  unsigned int* ticket;                 // [2] scan tile tickets, by interval parity
+  const float2* logtab;                 // [64] (1/c_i, ln c_i) of the waiting-time log
+  unsigned int* hist;                   // [P][kKcap] activity histogram (zero between intervals)
+  unsigned long long* tile_sum;         // [ntiles] weight sum of each tile
   unsigned int* beta;                   // interval being evolved (1-based)
   unsigned long long* X;                // evolved lattices  [slots][W]
   unsigned long long* Y;                // population lattices between intervals [slots][W]
   int32_t* KX;                          // evolved cumulative activity
   int32_t* KY;                          // population cumulative activity
   int32_t* dK;                          // activity of the last interval
-  unsigned long long* S;                // exclusive prefix sums of the weights
   int32_t* anc;                         // ancestors of the last cloning stage
   long long* ksum;                      // [P] sum of K (estimates)
   int32_t ntiles;
+  int32_t nunits;
   int64_t nslots;
 };
 
@@ -110,34 +117,30 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 }
 
 // ---------------------------------------------------------------------------
-// E = -ln(u), u = (2w+1)/2^33, as a fixed sequence of IEEE-754 float operations:
-// v = 2w+1 rounded once to float, v = m 2^e with m folded into (sqrt(1/2), sqrt(2)],
-// ln u = (e-33) ln2 + 2 atanh(f), f = (m-1)/(m+1), and 2 atanh(f) by its odd series
-// f (2 + 2/3 z + 2/5 z^2 + 2/7 z^3 + 2/9 z^4), z = f^2 (|f| <= 0.1716).  ln 2 is a
-// 15-bit head (exact products for |e-33| <= 33) plus a float tail.  Every step is
-// an explicitly rounded intrinsic, so no contraction can change the bits.
+// E = -ln(u), u = (2w+1)/2^33, in FP32 with a fixed sequence of operations:
+// v = 2w+1 truncated to its 24 leading bits, v' = m 2^p with m in [1, 2) and p the
+// position of the leading one; ln u' = (p-33) ln 2 + ln c_i + ln(1+r), where
+// c_i = 1 + (i + 1/2)/64 for the top 6 fraction bits i of m, r = m/c_i - 1
+// (|r| <= 1/128) and ln(1+r) ~ r (1 - r/2 + r^2/3).  tab[i] = (float(1/c_i),
+// float(ln c_i)).  ln 2 is a 15-bit head (exact products with 33-p) plus a float
+// tail.  Every float step is an explicitly rounded intrinsic, so no contraction
+// can change the bits; the integer work avoids 64-bit conversions, which run on
+// the narrow FP64 pipe of this part.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float neg_ln_u(uint32_t w) {
+__device__ __forceinline__ float neg_ln_u(uint32_t w, const float2* tab) {
   const unsigned long long v = 2ull * (unsigned long long)w + 1ull;
-  const float vf = __ull2float_rn(v);
-  const uint32_t bits = __float_as_uint(vf);
-  int e = (int)((bits >> 23) & 0xffu) - 127;
-  float m = __uint_as_float((bits & 0x007fffffu) | 0x3f800000u);
-  if (m > 0x1.6a09e6p+0f) {
-    m = __fmul_rn(m, 0.5f);
-    e += 1;
-  }
-  const float f = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
-  const float z = __fmul_rn(f, f);
-  float p = __fmaf_rn(0x1.c71c72p-3f, z, 0x1.24924ap-2f);
-  p = __fmaf_rn(p, z, 0x1.99999ap-2f);
-  p = __fmaf_rn(p, z, 0x1.555556p-1f);
-  p = __fmaf_rn(p, z, 2.0f);
-  const float ln_m = __fmul_rn(f, p);
-  const float n = (float)(e - 33);
-  float ln_u = __fmaf_rn(n, 0x1.7f7d1cp-20f, ln_m);
-  ln_u = __fmaf_rn(n, 0x1.62e4p-1f, ln_u);
-  return -ln_u;
+  const int p = 63 - __clzll((long long)v);  // 0..32
+  const uint32_t t = (p >= 23) ? (uint32_t)(v >> (p - 23)) : ((uint32_t)v << (23 - p));
+  const float m = __uint_as_float(0x3f800000u | (t & 0x007fffffu));
+  const float2 cl = tab[(t >> 17) & 63u];
+  const float r = __fmaf_rn(m, cl.x, -1.0f);
+  float q = __fmaf_rn(r, 0x1.555556p-2f, -0.5f);
+  q = __fmaf_rn(q, r, 1.0f);
+  const float ln_m = __fadd_rn(cl.y, __fmul_rn(q, r));
+  // float(33 - p) exactly: 1.5*2^23 + n has n in its low mantissa bits
+  const float n = __fsub_rn(__int_as_float(0x4B400000 + (33 - p)), 12582912.0f);
+  const float E = __fmaf_rn(n, 0x1.7f7d1cp-20f, -ln_m);
+  return __fmaf_rn(n, 0x1.62e4p-1f, E);
 }
 
 // ---------------------------------------------------------------------------
@@ -171,8 +174,18 @@ __device__ __forceinline__ int popc_lat(const unsigned long long (&a)[W]) {
   else return __popcll(a[0]) + __popcll(a[1]);
 }
 
-// Position of the k-th (0-based) set bit of a, k < popc(a): binary descent on
-// population counts of halves.
+// Position of the k-th (0-based) set bit of a, k < popc(a).
+#ifdef POP_KTH_FNS
+__device__ __forceinline__ int kth_set_bit64(unsigned long long a, uint32_t k) {
+  const uint32_t lo = (uint32_t)a;
+  const uint32_t c0 = (uint32_t)__popc(lo);
+  const bool in_lo = k < c0;
+  const uint32_t word = in_lo ? lo : (uint32_t)(a >> 32);
+  const uint32_t kk = in_lo ? k : k - c0;
+  return (int)__fns(word, 0u, (int)kk + 1) + (in_lo ? 0 : 32);
+}
+#else
+// binary descent on population counts of halves
 __device__ __forceinline__ int kth_set_bit64(unsigned long long a, uint32_t k) {
   uint32_t x = (uint32_t)a;
   int pos = 0;
@@ -190,6 +203,7 @@ __device__ __forceinline__ int kth_set_bit64(unsigned long long a, uint32_t k) {
   if (k >= c) { pos += 1; }
   return pos;
 }
+#endif
 
 template <int W>
 __device__ __forceinline__ int kth_bond(const unsigned long long (&a)[W], uint32_t k) {
@@ -270,7 +284,7 @@ __device__ __forceinline__ double warp_sum_f64(double v) {
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_init(Batch B) {
   const int64_t slot = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-  const int p = B.tile_pop[(blockIdx.x * kThreads) / kTile];
+  const int p = B.tile_pop[slot / kTile];
   const PopDesc d = B.pops[p];
   const int64_t j = slot - d.off;
   unsigned long long x[W];
@@ -296,255 +310,306 @@ __global__ void __launch_bounds__(kThreads) k_init(Batch B) {
   B.dK[slot] = 0;
 }
 
-// ---------------------------------------------------------------------------
-// Dynamical stage (Sec. 4 BKL; Sec. 3.1 rates 1 per possible hop).
-// Per step e of the interval: r = active bonds (escape rate); if r = 0 stop.
-// Draw q = e/2 of (q, beta, j, evolve) gives (wa, wb) = words (0,1) or (2,3).
-// tau = E(wa) * float(1/r); t_new = t + tau; stop if t_new >= dt (the residual
-// waiting time is dropped, which the exponential law's memorylessness allows);
-// else hop across the floor(wb r / 2^32)-th active bond.
-// All lanes of a warp that are still running are at the same step e, so the
-// draw on even steps is taken uniformly by the warp.
-// ---------------------------------------------------------------------------
+// Shared-memory state of k_evolve: one chunk of up to kChunk clones.
 template <int W>
-__global__ void __launch_bounds__(kThreads) k_evolve(Batch B, float dt_f) {
-  __shared__ float s_inv[kInvStride];
-  __shared__ int s_min[kWarps], s_max[kWarps];
-  __shared__ unsigned int s_ev[kWarps];
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int64_t slot = (int64_t)blockIdx.x * kThreads + tid;
-  const int p = B.tile_pop[(blockIdx.x * kThreads) / kTile];
-  const PopDesc d = B.pops[p];
-  for (int r = tid; r <= d.L; r += kThreads) s_inv[r] = B.inv_rate[p * kInvStride + r];
-  __syncthreads();
-  const int64_t j = slot - d.off;
-  const bool valid = j < d.nc;
-  const uint32_t beta = *B.beta;
-  int hops = 0;
-  if (valid) {
-    unsigned long long x[W];
-    load_lat<W>(B.Y, slot, x);
-    const int L = d.L;
-    const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
-    float t = 0.0f;
-    uint32_t e = 0u, wc = 0u, wd = 0u;
-    for (;;) {
-      if (e >= kStepLimit) {  // guard: the interval must end; report instead of spinning
-        B.st[p].err = kErrRange;
-        break;
+struct EvolveSmem {
+  unsigned long long x[kChunk][W];  // lattices
+  float t[kChunk];                  // time elapsed in the interval
+  int32_t hops[kChunk];             // activity of the interval so far
+  uint16_t act[2][kChunk];          // running clones of the current / next round
+  float inv[kChunkUnits][kInvStride];
+  float2 logtab[64];
+  uint2 u_key[kChunkUnits];         // Philox key of the unit's population
+  int32_t u_j0[kChunkUnits];        // population-local index of the unit's first slot
+  int32_t u_pop[kChunkUnits], u_L[kChunkUnits], u_valid[kChunkUnits];
+  int32_t u_min[kChunkUnits], u_max[kChunkUnits];
+  unsigned int u_ev[kChunkUnits];
+  int count[2];
+  int take;                         // next unclaimed entry of the current round's list
+};
+
+// One BKL step (Sec. 4 BKL; Sec. 3.1 rates 1 per possible hop) with the step's two
+// words (wa, wb): r = active bonds (escape rate; r = 0 ends the interval);
+// tau = E(wa) * float(1/r); t_new = t + tau; t_new >= dt ends the interval (the
+// residual waiting time is dropped, as the exponential law's memorylessness
+// allows); otherwise hop across the floor(wb r / 2^32)-th active bond.
+// Returns true if the clone hopped (and is still running).
+template <int W>
+__device__ __forceinline__ bool bkl_step(unsigned long long (&x)[W], float& t, int L,
+                                         const float* inv, const float2* tab, uint32_t wa,
+                                         uint32_t wb, float dt_f) {
+  unsigned long long a[W];
+  active_bonds<W>(x, L, a);
+  const int r = popc_lat<W>(a);
+  if (r == 0) return false;
+  const float t_new = __fadd_rn(t, __fmul_rn(neg_ln_u(wa, tab), inv[r]));
+  if (t_new >= dt_f) return false;
+  t = t_new;
+  hop<W>(x, kth_bond<W>(a, __umulhi(wb, (uint32_t)r)), L);
+  return true;
+}
+
+// Two steps of clone c of the chunk, e and e+1 (e even), from one Philox draw
+// q = e/2 of (q, beta, j, evolve): words (0,1) for step e, (2,3) for step e+1.
+// The state stays in registers for both steps.  Returns true if still running.
+template <int W>
+__device__ __forceinline__ bool bkl_pair(EvolveSmem<W>& S, int c, uint32_t e, uint32_t beta,
+                                         float dt_f) {
+  const int uu = c / kUnit;
+  const int L = S.u_L[uu];
+  const float* inv = S.inv[uu];
+  unsigned long long x[W];
+#pragma unroll
+  for (int q = 0; q < W; ++q) x[q] = S.x[c][q];
+  float t = S.t[c];
+  int h = S.hops[c];
+  bool run = false;
+  {
+    unsigned long long a[W];
+    active_bonds<W>(x, L, a);
+    if (popc_lat<W>(a) != 0) {
+      const uint2 key = S.u_key[uu];
+      const uint32_t j = (uint32_t)(S.u_j0[uu] + (c % kUnit));
+      const uint4 q = philox4x32_10(make_uint4(e >> 1, beta, j, kTagEvolve), key.x, key.y);
+      if (bkl_step<W>(x, t, L, inv, S.logtab, q.x, q.y, dt_f)) {
+        ++h;
+        if (bkl_step<W>(x, t, L, inv, S.logtab, q.z, q.w, dt_f)) {
+          ++h;
+          run = true;
+        }
       }
-      unsigned long long a[W];
-      active_bonds<W>(x, L, a);
-      const int r = popc_lat<W>(a);
-      if (r == 0) break;
-      uint32_t wa, wb;
-      if ((e & 1u) == 0u) {
-        const uint4 q = philox4x32_10(make_uint4(e >> 1, beta, (uint32_t)j, kTagEvolve), k0, k1);
-        wa = q.x; wb = q.y; wc = q.z; wd = q.w;
-      } else {
-        wa = wc; wb = wd;
-      }
-      ++e;
-      const float E = neg_ln_u(wa);
-      const float t_new = __fadd_rn(t, __fmul_rn(E, s_inv[r]));
-      if (t_new >= dt_f) break;
-      t = t_new;
-      const uint32_t k = __umulhi(wb, (uint32_t)r);
-      hop<W>(x, kth_bond<W>(a, k), L);
-      ++hops;
-    }
-    store_lat<W>(B.X, slot, x);
-    B.KX[slot] = B.KY[slot] + hops;
-    B.dK[slot] = hops;
-  }
-  const int mn = __reduce_min_sync(0xffffffffu, valid ? hops : INT_MAX);
-  const int mx = __reduce_max_sync(0xffffffffu, valid ? hops : INT_MIN);
-  const unsigned int ev = __reduce_add_sync(0xffffffffu, (unsigned int)hops);
-  if (lane == 0) { s_min[wid] = mn; s_max[wid] = mx; s_ev[wid] = ev; }
-  __syncthreads();
-  if (tid == 0) {
-    int bmn = s_min[0], bmx = s_max[0];
-    unsigned long long bev = s_ev[0];
-    for (int w = 1; w < kWarps; ++w) {
-      bmn = min(bmn, s_min[w]);
-      bmx = max(bmx, s_max[w]);
-      bev += s_ev[w];
-    }
-    if (bmn != INT_MAX) {
-      atomicMin(&B.st[p].dk_min, bmn);
-      atomicMax(&B.st[p].dk_max, bmx);
-      atomicAdd(&B.st[p].events, bev);
     }
   }
+#pragma unroll
+  for (int q = 0; q < W; ++q) S.x[c][q] = x[q];
+  S.hops[c] = h;
+  if (run) S.t[c] = t;
+  return run;
 }
 
 // ---------------------------------------------------------------------------
-// Weights and exact prefix sums.  F = 61 - ceil(log2 N_c), so the total T <= 2^61
-// and a look-back word holds a 62-bit value plus a 2-bit status.  One tile of
-// kTile slots per block; tiles are taken in ticket order, so every predecessor a
-// tile waits on is already running.
+// Dynamical stage.  Rounds of two BKL steps: every running clone of a round is at
+// the same (even) step, so each round takes one draw per clone; the next round's
+// list of running clones is built with warp-aggregated shared-memory appends.
+// When few clones are left they finish one per thread without further rounds.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_scan(Batch B) {
-  __shared__ unsigned int s_hist[kHistSmem];
-  __shared__ unsigned long long s_warp[kWarps];
-  __shared__ unsigned long long s_agg, s_excl;
-  __shared__ int s_tile, s_last;
+template <int W>
+__global__ void __launch_bounds__(kThreads, 5) k_evolve(Batch B, float dt_f) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  EvolveSmem<W>& S = *reinterpret_cast<EvolveSmem<W>*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t beta = *B.beta;
-  const int par = (int)(beta & 1u);
-  if (tid == 0) s_tile = (int)atomicAdd(&B.ticket[par], 1u);
-  for (int i = tid; i < kHistSmem; i += kThreads) s_hist[i] = 0u;
+  if (tid < 64) S.logtab[tid] = B.logtab[tid];
+  const int u_begin = (int)((long long)blockIdx.x * B.nunits / gridDim.x);
+  const int u_end = (int)((long long)(blockIdx.x + 1) * B.nunits / gridDim.x);
+  const int nchunks = (u_end - u_begin + kChunkUnits - 1) / kChunkUnits;
+  for (int ch = 0; ch < nchunks; ++ch) {
+    const int uc = u_begin + (int)((long long)ch * (u_end - u_begin) / nchunks);
+    const int nu = u_begin + (int)((long long)(ch + 1) * (u_end - u_begin) / nchunks) - uc;
+    const int64_t chunk_slot0 = (int64_t)uc * kUnit;
+    if (tid < nu) {
+      const int64_t slot0 = chunk_slot0 + (int64_t)tid * kUnit;
+      const int p = B.tile_pop[slot0 / kTile];
+      const PopDesc d = B.pops[p];
+      const int64_t j0 = slot0 - d.off;
+      S.u_pop[tid] = p;
+      S.u_L[tid] = d.L;
+      S.u_j0[tid] = (int32_t)j0;
+      S.u_key[tid] = make_uint2((uint32_t)d.seed, (uint32_t)(d.seed >> 32));
+      S.u_valid[tid] = (int)max((int64_t)0, min((int64_t)kUnit, d.nc - j0));
+      S.u_min[tid] = INT_MAX;
+      S.u_max[tid] = INT_MIN;
+      S.u_ev[tid] = 0u;
+    }
+    if (tid < 2) S.count[tid] = 0;
+    if (tid == 0) S.take = 0;
+    // this thread's cumulative activities, needed at write-back
+    int32_t ky[kChunkUnits];
+#pragma unroll
+    for (int m = 0; m < kChunkUnits; ++m)
+      if (m < nu) ky[m] = B.KY[chunk_slot0 + m * kUnit + tid];
+    __syncthreads();
+    for (int i = tid; i < nu * kInvStride; i += kThreads) {
+      const int uu = i / kInvStride, r = i % kInvStride;
+      S.inv[uu][r] = (r <= S.u_L[uu]) ? B.inv_rate[(size_t)S.u_pop[uu] * kInvStride + r] : 0.0f;
+    }
+#pragma unroll
+    for (int m = 0; m < kChunkUnits; ++m) {
+      if (m < nu) {
+        const int i = m * kUnit + tid;
+        if (tid < S.u_valid[m]) {
+          unsigned long long x[W];
+          load_lat<W>(B.Y, chunk_slot0 + i, x);
+#pragma unroll
+          for (int q = 0; q < W; ++q) S.x[i][q] = x[q];
+        }
+        S.t[i] = 0.0f;
+        S.hops[i] = 0;
+      }
+    }
+    __syncthreads();
+
+    int n = nu * kUnit;  // round 0 visits every slot of the chunk
+    int cur = 0;
+    for (uint32_t e = 0;; e += 2u) {
+      const int nxt = cur ^ 1;
+#ifdef POP_DYN_ROUNDS
+      for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&S.take, 32);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= n) break;
+#else
+      for (int base = wid * 32; base < n; base += kThreads) {
+#endif
+        const int idx = base + lane;
+        bool run = false;
+        int c = 0;
+        if (idx < n) {
+          c = (e == 0u) ? idx : (int)S.act[cur][idx];
+          if (e > 0u || (c % kUnit) < S.u_valid[c / kUnit]) run = bkl_pair<W>(S, c, e, beta, dt_f);
+        }
+        const unsigned int m = __ballot_sync(0xffffffffu, run);
+        if (m != 0u) {
+          const int leader = __ffs(m) - 1;
+          int pos = 0;
+          if (lane == leader) pos = atomicAdd(&S.count[nxt], __popc(m));
+          pos = __shfl_sync(0xffffffffu, pos, leader);
+          if (run) S.act[nxt][pos + __popc(m & ((1u << lane) - 1u))] = (uint16_t)c;
+        }
+      }
+      __syncthreads();
+      n = S.count[nxt];
+      if (tid == 0) {
+        S.count[cur] = 0;
+        S.take = 0;
+      }
+      __syncthreads();
+      cur = nxt;
+      if (n == 0) break;
+      if (n < kFinish) {
+        // few clones left: each runs to the end of the interval on its own thread,
+        // continuing its own step count (so its draws are the same)
+        if (tid < n) {
+          const int c = (int)S.act[cur][tid];
+          uint32_t f = e + 2u;
+          while (bkl_pair<W>(S, c, f, beta, dt_f)) {
+            f += 2u;
+            if (f >= kStepLimit) { B.st[S.u_pop[0]].err = kErrRange; break; }
+          }
+        }
+        __syncthreads();
+        break;
+      }
+      if (e + 2u >= kStepLimit) {  // guard: an interval must end; report, never spin
+        if (tid == 0) B.st[S.u_pop[0]].err = kErrRange;
+        break;
+      }
+    }
+
+    // write back (coalesced) and reduce the activity per unit
+#pragma unroll
+    for (int m = 0; m < kChunkUnits; ++m) {
+      if (m < nu) {
+        const int i = m * kUnit + tid;
+        const bool valid = tid < S.u_valid[m];
+        const int64_t slot = chunk_slot0 + i;
+        const int h = S.hops[i];
+        if (valid) {
+          unsigned long long x[W];
+#pragma unroll
+          for (int q = 0; q < W; ++q) x[q] = S.x[i][q];
+          store_lat<W>(B.X, slot, x);
+          B.KX[slot] = ky[m] + h;
+          B.dK[slot] = h;
+        }
+        const int mn = __reduce_min_sync(0xffffffffu, valid ? h : INT_MAX);
+        const int mx = __reduce_max_sync(0xffffffffu, valid ? h : INT_MIN);
+        const unsigned int ev = __reduce_add_sync(0xffffffffu, valid ? (unsigned int)h : 0u);
+        if (lane == 0) {
+          atomicMin(&S.u_min[m], mn);
+          atomicMax(&S.u_max[m], mx);
+          atomicAdd(&S.u_ev[m], ev);
+        }
+      }
+    }
+    __syncthreads();
+    if (tid < nu && S.u_min[tid] != INT_MAX) {
+      PopState* st = B.st + S.u_pop[tid];
+      atomicMin(&st->dk_min, S.u_min[tid]);
+      atomicMax(&st->dk_max, S.u_max[tid]);
+      atomicAdd(&st->events, (unsigned long long)S.u_ev[tid]);
+    }
+    __syncthreads();
+  }
+}
+
+// Block-wide sum of one 64-bit value per thread (result valid in every thread).
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v,
+                                                            unsigned long long* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_sum_u64(v);
+  if (lane == 0) scratch[wid] = v;
   __syncthreads();
-  const int tile = s_tile;
+  unsigned long long t = 0ull;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) t += scratch[w];
+  __syncthreads();
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// Weights: F = 61 - ceil(log2 N_c); w = wtab[|dK - k_ref|] with k_ref the min (s >= 0)
+// or max (s < 0) activity, so every weight is at most 2^F and the total at most 2^61.
+// Per tile: the weight sum and the histogram of |dK - k_ref|.  The first tile of a
+// population also records k_ref and the [eq] offset word U of the interval.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_weights(Batch B) {
+  __shared__ unsigned int s_hist[kHistSmem];
+  __shared__ unsigned long long s_red[kWarps];
+  const int tid = threadIdx.x;
+  const int tile = blockIdx.x;
   const int p = B.tile_pop[tile];
   const PopDesc d = B.pops[p];
   PopState* st = B.st + p;
   const int64_t base = (int64_t)tile * kTile;
   const int64_t j0 = base - d.off + (int64_t)tid * kItems;
-  const int dk_min = st->dk_min, dk_max = st->dk_max;
-  const int kref = (d.s >= 0.0) ? dk_min : dk_max;
   const int4 dk4 = reinterpret_cast<const int4*>(B.dK + base)[tid];
+  for (int i = tid; i < kHistSmem; i += kThreads) s_hist[i] = 0u;
+  const int dk_min = st->dk_min, dk_max = st->dk_max;
+  const int kref = d.s_neg ? dk_max : dk_min;
+  __syncthreads();
   const int dkv[kItems] = {dk4.x, dk4.y, dk4.z, dk4.w};
-  unsigned long long w[kItems];
-  unsigned long long tsum = 0ull;
-  bool range_err = false;
   const unsigned long long* wt = B.wtab + (size_t)p * kKcap;
+  unsigned long long sum = 0ull;
+  bool range_err = false;
 #pragma unroll
   for (int i = 0; i < kItems; ++i) {
-    w[i] = 0ull;
     if (j0 + i < d.nc) {
       const int k = abs(dkv[i] - kref);
       if (k >= kKcap) {
         range_err = true;
       } else {
-        w[i] = __ldg(wt + k);
+        sum += __ldg(wt + k);
         if (k < kHistSmem) atomicAdd(&s_hist[k], 1u);
         else atomicAdd(&B.hist[(size_t)p * kKcap + k], 1u);
       }
     }
-    tsum += w[i];
   }
   if (range_err) st->err = kErrRange;
-
-  // block-wide exclusive scan of the per-thread sums
-  unsigned long long x = tsum;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) s_warp[wid] = x;
-  __syncthreads();
-  if (wid == 0) {
-    const unsigned long long v = (lane < kWarps) ? s_warp[lane] : 0ull;
-    unsigned long long vi = v;
-#pragma unroll
-    for (int o = 1; o < kWarps; o <<= 1) {
-      const unsigned long long y = __shfl_up_sync(0xffffffffu, vi, o);
-      if (lane >= o) vi += y;
-    }
-    if (lane < kWarps) s_warp[lane] = vi - v;
-    if (lane == kWarps - 1) s_agg = vi;
-  }
-  __syncthreads();
-  const unsigned long long thread_excl = x - tsum + s_warp[wid];
-  const unsigned long long agg = s_agg;
-
-  // decoupled look-back across the tiles of this population
-  unsigned long long* status = B.tile_status + (size_t)par * B.ntiles;
-  if (wid == 0) {
-    unsigned long long excl = 0ull;
-    if (tile == d.first_tile) {
-      if (lane == 0) st_release(&status[tile], kStatusPre | agg);
-    } else {
-      if (lane == 0) st_release(&status[tile], kStatusAgg | agg);
-      int look = tile - 1;
-      bool timed_out = false;
-      for (;;) {
-        const int t = look - lane;
-        const bool in = t >= d.first_tile;
-        unsigned long long v = 0ull;
-        if (in) {
-          uint32_t spins = 0;
-          do {
-            v = ld_acquire(&status[t]);
-          } while ((v >> 62) == 0ull && ++spins < kSpinLimit);
-          if ((v >> 62) == 0ull) timed_out = true;
-        }
-        const unsigned int pre = __ballot_sync(0xffffffffu, in && (v >> 62) == 2ull);
-        if (pre != 0u) {
-          const int first = __ffs(pre) - 1;
-          excl += warp_sum_u64((in && lane <= first) ? (v & kValueMask) : 0ull);
-          break;
-        }
-        excl += warp_sum_u64(in ? (v & kValueMask) : 0ull);
-        look -= 32;
-        if (look < d.first_tile || __any_sync(0xffffffffu, timed_out)) break;
-      }
-      if (__any_sync(0xffffffffu, timed_out) && lane == 0) st->err = kErrTimeout;
-      if (lane == 0) st_release(&status[tile], kStatusPre | (excl + agg));
-    }
-    if (lane == 0) s_excl = excl;
-  }
-  __syncthreads();
-
-  // exclusive prefix sums of this thread's slots
-  unsigned long long run = s_excl + thread_excl;
-  unsigned long long sv[kItems];
-#pragma unroll
-  for (int i = 0; i < kItems; ++i) { sv[i] = run; run += w[i]; }
-  ulonglong2* sdst = reinterpret_cast<ulonglong2*>(B.S + base + (int64_t)tid * kItems);
-  sdst[0] = make_ulonglong2(sv[0], sv[1]);
-  sdst[1] = make_ulonglong2(sv[2], sv[3]);
-
-  // histogram to global memory
+  const unsigned long long total = block_sum_u64(sum, s_red);
   const int nb = min(dk_max - dk_min + 1, kHistSmem);
   for (int b = tid; b < nb; b += kThreads) {
     const unsigned int c = s_hist[b];
     if (c) atomicAdd(&B.hist[(size_t)p * kKcap + b], c);
   }
-  __threadfence();
-  __syncthreads();
   if (tid == 0) {
-    const unsigned int prev = atomicAdd(&st->done, 1u);
-    s_last = (prev == (unsigned int)(d.ntiles - 1));
-    // this tile's look-back word for the next interval of the same parity
-    B.tile_status[(size_t)(par ^ 1) * B.ntiles + tile] = 0ull;
-  }
-  __syncthreads();
-  if (!s_last || wid != 0) return;
-
-  // Last tile of the population: psi term of eq. (psihat) from the histogram,
-  //   term = -s k_ref + ln( (1/N_c) sum_k n_k exp(-|s| k) ),
-  // taken as log1p of the expm1 sum when the mean is above 1/2.
-  __threadfence();
-  const unsigned long long T =
-      ld_acquire(&status[d.first_tile + d.ntiles - 1]) & kValueMask;
-  const int R = min(dk_max - dk_min + 1, kKcap);
-  double a = 0.0, q = 0.0;
-  unsigned int* h = B.hist + (size_t)p * kKcap;
-  for (int b = lane; b < R; b += 32) {
-    const unsigned int c = __ldcg(h + b);
-    if (c) {
-      const double xk = -d.abs_s * (double)b;
-      a += (double)c * expm1(xk);
-      q += (double)c * exp(xk);
-      h[b] = 0u;
+    B.tile_sum[tile] = total;
+    if (tile == d.first_tile) {
+      st->kref = kref;
+      st->U = philox4x32_10(make_uint4(0u, *B.beta, 0u, kTagResample), (uint32_t)d.seed,
+                            (uint32_t)(d.seed >> 32)).x;
     }
-  }
-  a = warp_sum_f64(a);
-  q = warp_sum_f64(q);
-  if (lane == 0) {
-    const double ncd = (double)d.nc;
-    const double mean_q = q / ncd;
-    const double ln_mean = (mean_q > 0.5) ? log1p(a / ncd) : log(mean_q);
-    st->psi_acc += -d.s * (double)kref + ln_mean;
-    st->T = T;
-    st->U = philox4x32_10(make_uint4(0u, beta, 0u, kTagResample),
-                          (uint32_t)d.seed, (uint32_t)(d.seed >> 32)).x;
-    st->done = 0u;
-    st->dk_min = INT_MAX;
-    st->dk_max = INT_MIN;
   }
 }
 
@@ -557,82 +622,172 @@ __device__ __forceinline__ bool lt128(const U128& a, const U128& b) {
   return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
 }
 
-// First new slot whose [eq] point falls at or beyond the prefix sum S:
+// First new slot whose [eq] point lies at or beyond the prefix sum S:
 //   j_lo(S) = min{ j : (2^33 j + c) T >= S 2^33 N_c },  c = 2U + 1,
 // i.e. alpha_j = floor((2^33 j + c) T / (2^33 N_c)) >= S (eq. alpha-Ups with
-// d = c/2^33).  A float estimate is corrected with exact 128-bit comparisons.
+// d = c / 2^33).  A float estimate of S N_c / T (from the top 24 bits of S and T)
+// starts the search; exact 128-bit comparisons settle it.
 __device__ __forceinline__ uint32_t j_lo(unsigned long long S, unsigned long long T,
-                                         unsigned long long c, uint32_t nc, float nc_over_T) {
+                                         unsigned long long c, uint32_t nc, int sh,
+                                         float ratio) {
   if (S == 0ull) return 0u;
   if (S >= T) return nc;
   const U128 R = mul128(S, (unsigned long long)nc << 33);
-  const float est = __fmaf_rn(__ull2float_rn(S), nc_over_T, -__ull2float_rn(c) * 0x1p-33f);
-  long long j = (long long)ceilf(est);
-  j = j < 0 ? 0 : (j > (long long)nc ? (long long)nc : j);
-  while (j < (long long)nc && lt128(mul128(((unsigned long long)j << 33) + c, T), R)) ++j;
-  while (j > 0 && !lt128(mul128(((unsigned long long)(j - 1) << 33) + c, T), R)) --j;
+  const float est = __fmul_rn(__uint2float_rn((uint32_t)(S >> sh)), ratio);
+  unsigned long long j = (unsigned long long)min((float)nc, floorf(est));
+  while (j < nc && lt128(mul128((j << 33) + c, T), R)) ++j;
+  while (j > 0 && !lt128(mul128(((j - 1ull) << 33) + c, T), R)) --j;
   return (uint32_t)j;
 }
 
 // ---------------------------------------------------------------------------
-// Cloning stage: old clone k owns new slots [j_lo(S_k), j_lo(S_{k+1})).  Each warp
-// owns 32 consecutive old clones, hence one contiguous run of new slots; lanes
-// walk that run 32 at a time (coalesced stores), find their source lane by a
-// binary search over the warp's j_lo values and take the clone by shuffles.
-// The last block also advances the interval counter.
+// Cloning stage for one tile of old clones.  The tile's exclusive prefix comes from
+// the tile sums; a block scan gives S_k for its clones; old clone k owns the new
+// slots [j_lo(S_k), j_lo(S_{k+1})).  The old clones are staged in shared memory, a
+// map from new slot to old clone is scattered there, and every new slot of the
+// tile's range is written once, coalesced.  The first tile of each population adds
+// the psi term; the last block advances the interval counter (no block of this
+// kernel reads it).
 // ---------------------------------------------------------------------------
 template <int W>
-__global__ void __launch_bounds__(kThreads) k_gather(Batch B) {
-  const int tid = threadIdx.x, lane = tid & 31;
-  const int64_t slot = (int64_t)blockIdx.x * kThreads + tid;
-  const int p = B.tile_pop[(blockIdx.x * kThreads) / kTile];
+__global__ void __launch_bounds__(kThreads, 6) k_gather(Batch B) {
+  __shared__ unsigned long long s_x[kTile][W];
+  __shared__ int32_t s_K[kTile];
+  __shared__ uint32_t s_jlo[kTile + 1];
+  __shared__ uint16_t s_src[kMap];
+  __shared__ unsigned long long s_red[kWarps];
+  __shared__ unsigned long long s_wsum[kWarps];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int tile = blockIdx.x;
+  const int p = B.tile_pop[tile];
   const PopDesc d = B.pops[p];
-  const PopState* st = B.st + p;
-  const unsigned long long T = st->T;
-  const unsigned long long c = 2ull * (unsigned long long)st->U + 1ull;
+  PopState* st = B.st + p;
+  const int lt = tile - d.first_tile;
   const uint32_t nc = (uint32_t)d.nc;
-  const float nc_over_T = __fdiv_rn((float)nc, __ull2float_rn(T));
-  const int64_t k = slot - d.off;
-  const bool valid = k < d.nc;
-  uint32_t jlo = nc;
-  unsigned long long x[W];
-  int32_t Kv = 0;
+  const int64_t base = (int64_t)tile * kTile;
+  const int64_t j0 = base - d.off + (int64_t)tid * kItems;
+
+  // independent loads first: activities and the old clones of this tile
+  const int4 dk4 = reinterpret_cast<const int4*>(B.dK + base)[tid];
 #pragma unroll
-  for (int q = 0; q < W; ++q) x[q] = 0ull;
-  if (valid) {
-    jlo = j_lo(B.S[slot], T, c, nc, nc_over_T);
-    load_lat<W>(B.X, slot, x);
-    Kv = B.KX[slot];
-  }
-  uint32_t jhi = __shfl_down_sync(0xffffffffu, jlo, 1);
-  if (lane == 31) jhi = (k + 1 < d.nc) ? j_lo(B.S[slot + 1], T, c, nc, nc_over_T) : nc;
-  const uint32_t J0 = __shfl_sync(0xffffffffu, jlo, 0);
-  const uint32_t J1 = __shfl_sync(0xffffffffu, jhi, 31);
-  const int64_t k_first = slot - lane - d.off;
-  for (uint32_t base = J0; base < J1; base += 32u) {
-    const uint32_t jj = base + (uint32_t)lane;
-    int src = 0;
+  for (int m = 0; m < kItems; ++m) {
+    const int i = m * kThreads + tid;
+    if (base - d.off + i < d.nc) {
+      unsigned long long x[W];
+      load_lat<W>(B.X, base + i, x);
 #pragma unroll
-    for (int step = 16; step >= 1; step >>= 1) {
-      const uint32_t v = __shfl_sync(0xffffffffu, jlo, src + step);
-      if (v <= jj) src += step;
-    }
-    unsigned long long xs[W];
-#pragma unroll
-    for (int q = 0; q < W; ++q) xs[q] = __shfl_sync(0xffffffffu, x[q], src);
-    const int32_t Ks = __shfl_sync(0xffffffffu, Kv, src);
-    if (jj < J1) {
-      const int64_t dst = d.off + (int64_t)jj;
-      store_lat<W>(B.Y, dst, xs);
-      B.KY[dst] = Ks;
-      B.anc[dst] = (int32_t)(k_first + src);
+      for (int q = 0; q < W; ++q) s_x[i][q] = x[q];
+      s_K[i] = B.KX[base + i];
     }
   }
-  if (blockIdx.x == gridDim.x - 1 && tid == 0) {
-    const unsigned int b = *B.beta;
-    B.ticket[(b + 1u) & 1u] = 0u;
-    *B.beta = b + 1u;
+  const int kref = st->kref;
+  const unsigned long long c = 2ull * (unsigned long long)st->U + 1ull;
+
+  // population total T and this tile's exclusive prefix
+  unsigned long long tT = 0ull, tE = 0ull;
+  for (int i = tid; i < d.ntiles; i += kThreads) {
+    const unsigned long long v = B.tile_sum[d.first_tile + i];
+    tT += v;
+    if (i < lt) tE += v;
   }
+
+  // weights of this tile's clones and their scan within each warp
+  const int dkv[kItems] = {dk4.x, dk4.y, dk4.z, dk4.w};
+  const unsigned long long* wt = B.wtab + (size_t)p * kKcap;
+  unsigned long long w[kItems];
+  unsigned long long tsum = 0ull;
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    w[i] = 0ull;
+    if (j0 + i < d.nc) {
+      const int k = abs(dkv[i] - kref);
+      if (k < kKcap) w[i] = __ldg(wt + k);
+    }
+    tsum += w[i];
+  }
+  unsigned long long xs = tsum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, xs, o);
+    if (lane >= o) xs += y;
+  }
+  if (lane == 31) s_wsum[wid] = xs;
+  const unsigned long long T = block_sum_u64(tT, s_red);
+  const unsigned long long excl = block_sum_u64(tE, s_red);
+
+  const int sh = max(0, 64 - __clzll((long long)T) - 24);
+  const float ratio = __fdiv_rn((float)nc, __uint2float_rn((uint32_t)(T >> sh)));
+  unsigned long long run = excl + xs - tsum;
+  for (int q = 0; q < wid; ++q) run += s_wsum[q];
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    s_jlo[tid * kItems + i] = j_lo(run, T, c, nc, sh, ratio);
+    run += w[i];
+  }
+  if (tid == kThreads - 1) s_jlo[kTile] = j_lo(run, T, c, nc, sh, ratio);
+  __syncthreads();
+
+  const uint32_t J0 = s_jlo[0], J1 = s_jlo[kTile];
+  const bool mapped = (J1 - J0) <= (uint32_t)kMap;
+  if (mapped) {
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+      const int k = tid * kItems + i;
+      for (uint32_t jj = s_jlo[k]; jj < s_jlo[k + 1]; ++jj) s_src[jj - J0] = (uint16_t)k;
+    }
+    __syncthreads();
+  }
+  for (uint32_t jj = J0 + (uint32_t)tid; jj < J1; jj += kThreads) {
+    int k;
+    if (mapped) {
+      k = s_src[jj - J0];
+    } else {  // one old clone with very many copies: search the sorted j_lo
+      int lo = 0, hi = kTile - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_jlo[mid] <= jj) lo = mid; else hi = mid - 1;
+      }
+      k = lo;
+    }
+    unsigned long long x[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) x[q] = s_x[k][q];
+    const int64_t dst = d.off + (int64_t)jj;
+    store_lat<W>(B.Y, dst, x);
+    B.KY[dst] = s_K[k];
+    B.anc[dst] = lt * kTile + k;
+  }
+
+  // psi term of eq. (psihat) for this interval, once per population:
+  //   term = -s k_ref + ln( (1/N_c) sum_k n_k exp(-|s| k) ),
+  // with the log taken as log1p of the expm1 sum when the mean is above 1/2.
+  if (lt == 0 && wid == 0) {
+    const int dk_min = st->dk_min, dk_max = st->dk_max;
+    const int R = min(dk_max - dk_min + 1, kKcap);
+    unsigned int* h = B.hist + (size_t)p * kKcap;
+    const double* qt = B.qtab + (size_t)p * kKcap;
+    const double* qm = B.qm1tab + (size_t)p * kKcap;
+    double a = 0.0, q = 0.0;
+    for (int b = lane; b < R; b += 32) {
+      const unsigned int cnt = h[b];
+      if (cnt) {
+        a = fma((double)cnt, qm[b], a);
+        q = fma((double)cnt, qt[b], q);
+        h[b] = 0u;
+      }
+    }
+    a = warp_sum_f64(a);
+    q = warp_sum_f64(q);
+    if (lane == 0) {
+      const double ncd = (double)d.nc;
+      const double mean_q = q / ncd;
+      const double ln_mean = (mean_q > 0.5) ? log1p(a / ncd) : log(mean_q);
+      st->psi_acc += -d.s * (double)kref + ln_mean;
+      st->dk_min = INT_MAX;
+      st->dk_max = INT_MIN;
+    }
+  }
+  if (blockIdx.x == gridDim.x - 1 && tid == 0) *B.beta += 1u;
 }
 
 // Sum of the carried activities of each population (for k_hat, eq. khat).
@@ -640,7 +795,7 @@ __global__ void __launch_bounds__(kThreads) k_ksum(Batch B) {
   __shared__ long long s_part[kWarps];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int64_t slot = (int64_t)blockIdx.x * kThreads + tid;
-  const int p = B.tile_pop[(blockIdx.x * kThreads) / kTile];
+  const int p = B.tile_pop[slot / kTile];
   const PopDesc d = B.pops[p];
   long long v = (slot - d.off < d.nc) ? (long long)B.KY[slot] : 0ll;
 #pragma unroll
