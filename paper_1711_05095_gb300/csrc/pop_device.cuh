@@ -43,7 +43,6 @@ constexpr int kMap = 2048;                // new slots of one tile mapped in sha
 constexpr int kMaxL = 128;                // one clone per lane: W <= 2 words
 constexpr int kInvStride = kMaxL + 1;     // per-population 1/r table stride
 constexpr uint32_t kStepLimit = 1u << 24; // BKL steps per clone per interval
-constexpr int kFinish = kThreads / 2;     // fewer running clones: finish them one per thread
 
 constexpr int32_t kErrRange = -3;
 
@@ -313,10 +312,8 @@ __global__ void __launch_bounds__(kThreads) k_init(Batch B) {
 // Shared-memory state of k_evolve: one chunk of up to kChunk clones.
 template <int W>
 struct EvolveSmem {
-  unsigned long long x[kChunk][W];  // lattices
-  float t[kChunk];                  // time elapsed in the interval
-  int32_t hops[kChunk];             // activity of the interval so far
-  uint16_t act[2][kChunk];          // running clones of the current / next round
+  unsigned long long x[kChunk][W];  // lattices (in, then out)
+  int32_t hops[kChunk];             // activity of the interval
   float inv[kChunkUnits][kInvStride];
   float2 logtab[64];
   uint2 u_key[kChunkUnits];         // Philox key of the unit's population
@@ -324,8 +321,7 @@ struct EvolveSmem {
   int32_t u_pop[kChunkUnits], u_L[kChunkUnits], u_valid[kChunkUnits];
   int32_t u_min[kChunkUnits], u_max[kChunkUnits];
   unsigned int u_ev[kChunkUnits];
-  int count[2];
-  int take;                         // next unclaimed entry of the current round's list
+  int take;                         // next unclaimed clone of the chunk
 };
 
 // One BKL step (Sec. 4 BKL; Sec. 3.1 rates 1 per possible hop) with the step's two
@@ -349,55 +345,19 @@ __device__ __forceinline__ bool bkl_step(unsigned long long (&x)[W], float& t, i
   return true;
 }
 
-// Two steps of clone c of the chunk, e and e+1 (e even), from one Philox draw
-// q = e/2 of (q, beta, j, evolve): words (0,1) for step e, (2,3) for step e+1.
-// The state stays in registers for both steps.  Returns true if still running.
-template <int W>
-__device__ __forceinline__ bool bkl_pair(EvolveSmem<W>& S, int c, uint32_t e, uint32_t beta,
-                                         float dt_f) {
-  const int uu = c / kUnit;
-  const int L = S.u_L[uu];
-  const float* inv = S.inv[uu];
-  unsigned long long x[W];
-#pragma unroll
-  for (int q = 0; q < W; ++q) x[q] = S.x[c][q];
-  float t = S.t[c];
-  int h = S.hops[c];
-  bool run = false;
-  {
-    unsigned long long a[W];
-    active_bonds<W>(x, L, a);
-    if (popc_lat<W>(a) != 0) {
-      const uint2 key = S.u_key[uu];
-      const uint32_t j = (uint32_t)(S.u_j0[uu] + (c % kUnit));
-      const uint4 q = philox4x32_10(make_uint4(e >> 1, beta, j, kTagEvolve), key.x, key.y);
-      if (bkl_step<W>(x, t, L, inv, S.logtab, q.x, q.y, dt_f)) {
-        ++h;
-        if (bkl_step<W>(x, t, L, inv, S.logtab, q.z, q.w, dt_f)) {
-          ++h;
-          run = true;
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < W; ++q) S.x[c][q] = x[q];
-  S.hops[c] = h;
-  if (run) S.t[c] = t;
-  return run;
-}
-
 // ---------------------------------------------------------------------------
-// Dynamical stage.  Rounds of two BKL steps: every running clone of a round is at
-// the same (even) step, so each round takes one draw per clone; the next round's
-// list of running clones is built with warp-aggregated shared-memory appends.
-// When few clones are left they finish one per thread without further rounds.
+// Dynamical stage.  A persistent grid; each block stages an equal share of the
+// clones in shared memory.  Every lane holds one clone in registers and advances
+// it two BKL steps per iteration from one Philox draw (draw q of the clone serves
+// its steps 2q and 2q+1); a lane whose clone has ended takes the next clone of
+// the block from a shared-memory counter, so lanes stay busy until the block's
+// clones run out and no block-wide barrier is needed during the interval.
 // ---------------------------------------------------------------------------
 template <int W>
-__global__ void __launch_bounds__(kThreads, 5) k_evolve(Batch B, float dt_f) {
+__global__ void __launch_bounds__(kThreads, 6) k_evolve(Batch B, float dt_f) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   EvolveSmem<W>& S = *reinterpret_cast<EvolveSmem<W>*>(smem_raw);
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31;
   const uint32_t beta = *B.beta;
   if (tid < 64) S.logtab[tid] = B.logtab[tid];
   const int u_begin = (int)((long long)blockIdx.x * B.nunits / gridDim.x);
@@ -421,7 +381,6 @@ __global__ void __launch_bounds__(kThreads, 5) k_evolve(Batch B, float dt_f) {
       S.u_max[tid] = INT_MIN;
       S.u_ev[tid] = 0u;
     }
-    if (tid < 2) S.count[tid] = 0;
     if (tid == 0) S.take = 0;
     // this thread's cumulative activities, needed at write-back
     int32_t ky[kChunkUnits];
@@ -443,69 +402,80 @@ __global__ void __launch_bounds__(kThreads, 5) k_evolve(Batch B, float dt_f) {
 #pragma unroll
           for (int q = 0; q < W; ++q) S.x[i][q] = x[q];
         }
-        S.t[i] = 0.0f;
         S.hops[i] = 0;
       }
     }
     __syncthreads();
 
-    int n = nu * kUnit;  // round 0 visits every slot of the chunk
-    int cur = 0;
-    for (uint32_t e = 0;; e += 2u) {
-      const int nxt = cur ^ 1;
-#ifdef POP_DYN_ROUNDS
-      for (;;) {
+    const int n = nu * kUnit;
+    int c = -1;  // the lane's clone (chunk index), -1 when it has none
+    unsigned long long x[W];
+    float t = 0.0f;
+    int h = 0, L = 3;
+    uint32_t q = 0u, j = 0u;
+    uint2 key = make_uint2(0u, 0u);
+    const float* inv = S.inv[0];
+#pragma unroll
+    for (int w = 0; w < W; ++w) x[w] = 0ull;
+    for (;;) {
+      // one read of the counter per warp keeps every branch below warp-uniform
+      int taken = 0;
+      if (lane == 0) taken = *(volatile int*)&S.take;
+      taken = __shfl_sync(0xffffffffu, taken, 0);
+      const bool need = c < 0;
+      const unsigned int m = __ballot_sync(0xffffffffu, need);
+      if (m != 0u && taken < n) {
+        const int leader = __ffs(m) - 1;
         int base = 0;
-        if (lane == 0) base = atomicAdd(&S.take, 32);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= n) break;
-#else
-      for (int base = wid * 32; base < n; base += kThreads) {
-#endif
-        const int idx = base + lane;
-        bool run = false;
-        int c = 0;
-        if (idx < n) {
-          c = (e == 0u) ? idx : (int)S.act[cur][idx];
-          if (e > 0u || (c % kUnit) < S.u_valid[c / kUnit]) run = bkl_pair<W>(S, c, e, beta, dt_f);
-        }
-        const unsigned int m = __ballot_sync(0xffffffffu, run);
-        if (m != 0u) {
-          const int leader = __ffs(m) - 1;
-          int pos = 0;
-          if (lane == leader) pos = atomicAdd(&S.count[nxt], __popc(m));
-          pos = __shfl_sync(0xffffffffu, pos, leader);
-          if (run) S.act[nxt][pos + __popc(m & ((1u << lane) - 1u))] = (uint16_t)c;
-        }
-      }
-      __syncthreads();
-      n = S.count[nxt];
-      if (tid == 0) {
-        S.count[cur] = 0;
-        S.take = 0;
-      }
-      __syncthreads();
-      cur = nxt;
-      if (n == 0) break;
-      if (n < kFinish) {
-        // few clones left: each runs to the end of the interval on its own thread,
-        // continuing its own step count (so its draws are the same)
-        if (tid < n) {
-          const int c = (int)S.act[cur][tid];
-          uint32_t f = e + 2u;
-          while (bkl_pair<W>(S, c, f, beta, dt_f)) {
-            f += 2u;
-            if (f >= kStepLimit) { B.st[S.u_pop[0]].err = kErrRange; break; }
+        if (lane == leader) base = atomicAdd(&S.take, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (need) {
+          const int idx = base + __popc(m & ((1u << lane) - 1u));
+          if (idx < n) {
+            const int uu = idx / kUnit;
+            if ((idx % kUnit) < S.u_valid[uu]) {
+              c = idx;
+#pragma unroll
+              for (int w = 0; w < W; ++w) x[w] = S.x[c][w];
+              t = 0.0f;
+              h = 0;
+              q = 0u;
+              L = S.u_L[uu];
+              key = S.u_key[uu];
+              j = (uint32_t)(S.u_j0[uu] + (idx % kUnit));
+              inv = S.inv[uu];
+            }
           }
         }
-        __syncthreads();
-        break;
       }
-      if (e + 2u >= kStepLimit) {  // guard: an interval must end; report, never spin
-        if (tid == 0) B.st[S.u_pop[0]].err = kErrRange;
-        break;
+      if (__ballot_sync(0xffffffffu, c >= 0) == 0u) {
+        if (lane == 0) taken = *(volatile int*)&S.take;
+        if (__shfl_sync(0xffffffffu, taken, 0) >= n) break;
+      }
+      if (c >= 0) {
+        const uint4 d4 = philox4x32_10(make_uint4(q, beta, j, kTagEvolve), key.x, key.y);
+        bool run = false;
+        if (bkl_step<W>(x, t, L, inv, S.logtab, d4.x, d4.y, dt_f)) {
+          ++h;
+          if (bkl_step<W>(x, t, L, inv, S.logtab, d4.z, d4.w, dt_f)) {
+            ++h;
+            run = true;
+          }
+        }
+        ++q;
+        if (run && q >= kStepLimit / 2u) {  // guard: an interval must end; report, never spin
+          B.st[S.u_pop[c / kUnit]].err = kErrRange;
+          run = false;
+        }
+        if (!run) {
+#pragma unroll
+          for (int w = 0; w < W; ++w) S.x[c][w] = x[w];
+          S.hops[c] = h;
+          c = -1;
+        }
       }
     }
+    __syncthreads();
 
     // write back (coalesced) and reduce the activity per unit
 #pragma unroll
@@ -514,18 +484,18 @@ __global__ void __launch_bounds__(kThreads, 5) k_evolve(Batch B, float dt_f) {
         const int i = m * kUnit + tid;
         const bool valid = tid < S.u_valid[m];
         const int64_t slot = chunk_slot0 + i;
-        const int h = S.hops[i];
+        const int hh = S.hops[i];
         if (valid) {
-          unsigned long long x[W];
+          unsigned long long xo[W];
 #pragma unroll
-          for (int q = 0; q < W; ++q) x[q] = S.x[i][q];
-          store_lat<W>(B.X, slot, x);
-          B.KX[slot] = ky[m] + h;
-          B.dK[slot] = h;
+          for (int w = 0; w < W; ++w) xo[w] = S.x[i][w];
+          store_lat<W>(B.X, slot, xo);
+          B.KX[slot] = ky[m] + hh;
+          B.dK[slot] = hh;
         }
-        const int mn = __reduce_min_sync(0xffffffffu, valid ? h : INT_MAX);
-        const int mx = __reduce_max_sync(0xffffffffu, valid ? h : INT_MIN);
-        const unsigned int ev = __reduce_add_sync(0xffffffffu, valid ? (unsigned int)h : 0u);
+        const int mn = __reduce_min_sync(0xffffffffu, valid ? hh : INT_MAX);
+        const int mx = __reduce_max_sync(0xffffffffu, valid ? hh : INT_MIN);
+        const unsigned int ev = __reduce_add_sync(0xffffffffu, valid ? (unsigned int)hh : 0u);
         if (lane == 0) {
           atomicMin(&S.u_min[m], mn);
           atomicMax(&S.u_max[m], mx);
@@ -558,6 +528,20 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
   return t;
 }
 
+// |a - b| as an unsigned magnitude (no overflow for any pair of ints), so that an
+// out-of-range activity is rejected by the table-size check instead of indexing.
+__device__ __forceinline__ unsigned int abs_diff(int a, int b) {
+  const long long d = (long long)a - (long long)b;
+  const unsigned long long m = d < 0 ? (unsigned long long)(-d) : (unsigned long long)d;
+  return m > 0xffffffffull ? 0xffffffffu : (unsigned int)m;
+}
+
+// Number of histogram bins in use, clamped to [0, cap].
+__device__ __forceinline__ int hist_bins(int dk_min, int dk_max, int cap) {
+  const long long n = (long long)dk_max - (long long)dk_min + 1;
+  return n < 0 ? 0 : (n > cap ? cap : (int)n);
+}
+
 // ---------------------------------------------------------------------------
 // Weights: F = 61 - ceil(log2 N_c); w = wtab[|dK - k_ref|] with k_ref the min (s >= 0)
 // or max (s < 0) activity, so every weight is at most 2^F and the total at most 2^61.
@@ -586,19 +570,19 @@ __global__ void __launch_bounds__(kThreads) k_weights(Batch B) {
 #pragma unroll
   for (int i = 0; i < kItems; ++i) {
     if (j0 + i < d.nc) {
-      const int k = abs(dkv[i] - kref);
-      if (k >= kKcap) {
+      const unsigned int k = abs_diff(dkv[i], kref);
+      if (k >= (unsigned int)kKcap) {
         range_err = true;
       } else {
         sum += __ldg(wt + k);
-        if (k < kHistSmem) atomicAdd(&s_hist[k], 1u);
+        if (k < (unsigned int)kHistSmem) atomicAdd(&s_hist[k], 1u);
         else atomicAdd(&B.hist[(size_t)p * kKcap + k], 1u);
       }
     }
   }
   if (range_err) st->err = kErrRange;
   const unsigned long long total = block_sum_u64(sum, s_red);
-  const int nb = min(dk_max - dk_min + 1, kHistSmem);
+  const int nb = hist_bins(dk_min, dk_max, kHistSmem);
   for (int b = tid; b < nb; b += kThreads) {
     const unsigned int c = s_hist[b];
     if (c) atomicAdd(&B.hist[(size_t)p * kKcap + b], c);
@@ -700,8 +684,8 @@ __global__ void __launch_bounds__(kThreads, 6) k_gather(Batch B) {
   for (int i = 0; i < kItems; ++i) {
     w[i] = 0ull;
     if (j0 + i < d.nc) {
-      const int k = abs(dkv[i] - kref);
-      if (k < kKcap) w[i] = __ldg(wt + k);
+      const unsigned int k = abs_diff(dkv[i], kref);
+      if (k < (unsigned int)kKcap) w[i] = __ldg(wt + k);
     }
     tsum += w[i];
   }
@@ -763,7 +747,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_gather(Batch B) {
   // with the log taken as log1p of the expm1 sum when the mean is above 1/2.
   if (lt == 0 && wid == 0) {
     const int dk_min = st->dk_min, dk_max = st->dk_max;
-    const int R = min(dk_max - dk_min + 1, kKcap);
+    const int R = hist_bins(dk_min, dk_max, kKcap);
     unsigned int* h = B.hist + (size_t)p * kKcap;
     const double* qt = B.qtab + (size_t)p * kKcap;
     const double* qm = B.qm1tab + (size_t)p * kKcap;
