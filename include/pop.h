@@ -149,6 +149,31 @@ int pop_copy_state(pop_t* pop, int32_t p, uint64_t* h_lattice, int32_t* h_K,
 /* Executed hops (BKL events) per population since pop_init (host array of n_pops). */
 int pop_events(pop_t* pop, uint64_t* h_events);
 
+/*
+ * Cloning-stage selection of ONE population without allocating anything.  The
+ * paper has no counterpart: this exists for callers that cannot call cudaMalloc
+ * and so cannot provide pop_init's workspace: a process whose device memory is
+ * all reserved by another allocator (a framework's caching pool), a
+ * latency-critical loop where an allocation and the synchronisation it implies
+ * are not allowed, or an embedded runtime without a device allocator.
+ *   d_dK        device, n_clones int32: the interval activities K^beta (input)
+ *   n_clones    1 <= N_c <= POP_NOALLOC_MAX_CLONES (larger: POP_ERR_ARG)
+ *   s, seed     bias and Philox key of the population
+ *   interval    beta >= 1, selects the [eq] offset word of that interval
+ *   d_anc       device, n_clones int32: ancestors of the new clones (output)
+ *   h_psi_term  host, may be NULL: ln((1/N_c) sum_i exp(-s K_i^beta)) (output)
+ * Results equal those of pop_resample for the same activities.  Scratch lives in
+ * a static device array of 120 KiB that every GPU which loads the library holds
+ * until the process exits; each call clears what must start at zero, the array
+ * keeps the last call's contents, and calls that overlap on the GPU race on it.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Waits for
+ * the stream.  No cudaMalloc, cudaFree or allocating library routine is called.
+ */
+#define POP_NOALLOC_MAX_CLONES (1LL << 20)
+int pop_select_noalloc(const int32_t* d_dK, int64_t n_clones, double s, uint64_t seed,
+                       uint32_t interval, int32_t* d_anc, double* h_psi_term, void* cuda_stream);
+
 /* Lattice words per clone, W, of a batch (0 if the parameters are invalid). */
 int32_t pop_lattice_words(const pop_params* params, int32_t n_pops);
 

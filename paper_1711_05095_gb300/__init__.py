@@ -31,7 +31,8 @@ POP_MAX_L = 128
 # every symbol include/pop.h declares
 EXPORTS = ("pop_workspace_bytes", "pop_init", "pop_set_state", "pop_evolve", "pop_resample",
            "pop_run", "pop_estimate_psi", "pop_copy_state", "pop_events", "pop_lattice_words",
-           "pop_strerror", "pop_free")
+           "pop_select_noalloc", "pop_strerror", "pop_free")
+POP_NOALLOC_MAX_CLONES = 1 << 20
 
 
 class PopParams(ctypes.Structure):
@@ -83,6 +84,9 @@ def library():
     L.pop_copy_state.restype = ctypes.c_int
     L.pop_events.argtypes = [ctypes.c_void_p, _u64p]
     L.pop_events.restype = ctypes.c_int
+    L.pop_select_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_uint64,
+                                     ctypes.c_uint32, ctypes.c_void_p, _f64p, ctypes.c_void_p]
+    L.pop_select_noalloc.restype = ctypes.c_int
     L.pop_strerror.argtypes = [ctypes.c_int]
     L.pop_strerror.restype = ctypes.c_char_p
     L.pop_free.argtypes = [ctypes.c_void_p]
@@ -211,3 +215,20 @@ class PopulationBatch:
             self.close()
         except Exception:
             pass
+
+
+def select_noalloc(d_dK, s, seed, interval, d_anc, stream=None):
+    """pop_select_noalloc on torch device tensors (int32 activities in, int32
+    ancestors out, same length).  Returns the psi term of the interval.  For
+    callers that cannot allocate device memory; nothing is allocated here."""
+    import torch
+    n = int(d_dK.numel())
+    if d_anc.numel() != n or d_dK.dtype != torch.int32 or d_anc.dtype != torch.int32:
+        raise PopError(POP_ERR_ARG, "pop_select_noalloc")
+    st = stream if stream is not None else torch.cuda.current_stream(d_dK.device)
+    term = ctypes.c_double(0.0)
+    rc = library().pop_select_noalloc(ctypes.c_void_p(d_dK.data_ptr()), n, float(s), int(seed),
+                                      int(interval), ctypes.c_void_p(d_anc.data_ptr()),
+                                      ctypes.byref(term), ctypes.c_void_p(st.cuda_stream))
+    _check(rc, "pop_select_noalloc")
+    return term.value

@@ -4,8 +4,8 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SOURCES = [os.path.join(HERE, "csrc", "pop_api.cu")]
-DEPS = SOURCES + [os.path.join(HERE, "csrc", "pop_device.cuh"), os.path.join(ROOT, "include", "pop.h")]
+SOURCES = [os.path.join(HERE, "csrc", "pop_api.cu"), os.path.join(HERE, "csrc", "pop_noalloc.cu")]
+DEPS = SOURCES + [os.path.join(HERE, "csrc", "pop_common.cuh"), os.path.join(HERE, "csrc", "pop_kernels.cuh"), os.path.join(ROOT, "include", "pop.h")]
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpopgb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

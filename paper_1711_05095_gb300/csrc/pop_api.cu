@@ -18,7 +18,7 @@
 #include <vector>
 
 #include "pop.h"
-#include "pop_device.cuh"
+#include "pop_kernels.cuh"
 
 using namespace popgpu;
 

@@ -1,279 +1,10 @@
-// Device code of the SSEP cloning library (sm_103a).
-//
-// One interval of the cloning algorithm (arXiv:1711.05095, Sec. 2.3) is three
-// kernels over a batch of populations laid out back to back in "slots" (every
-// population starts on a 1024-slot tile):
-//   k_evolve   dynamical stage (Sec. 4: BKL continuous-time Monte Carlo of the SSEP,
-//              Sec. 3.1 rates).  A persistent grid; each block owns an equal range of
-//              256-slot units, stages the clones in shared memory and advances them in
-//              rounds of one BKL step per running clone, compacting the running clones
-//              after each round so that every lane does useful work.  Epilogue: the
-//              per-population min/max of the interval activity.
-//   k_weights  fixed-point weights exp(-s dK) (64-bit), their per-tile sums and the
-//              histogram of the interval activity.
-//   k_gather   per tile: the exclusive prefix sums of the weights (tile sums, then a
-//              block scan), [eq] selection (Sec. 4.1, eq. alpha-Ups) inverted per old
-//              clone in exact integers, and a pull copy of lattices and carried
-//              activities (eq. khat) staged through shared memory.  The first tile of
-//              each population adds the psi term of eq. (psihat).
-// All arithmetic that decides an integer result (waiting times, bond choice,
-// weights, ancestors) is specified bit for bit; pop_api.cu states the contract.
+// Kernels of the SSEP cloning library (sm_103a); see pop_common.cuh for the
+// interval structure, the data layout and the arithmetic they share.
 #pragma once
 
-#include <cstdint>
-#include <climits>
-#include <cuda_runtime.h>
+#include "pop_common.cuh"
 
 namespace popgpu {
-
-constexpr uint32_t kTagInit = 1u;
-constexpr uint32_t kTagEvolve = 2u;
-constexpr uint32_t kTagResample = 3u;
-
-constexpr int kThreads = 256;             // threads per block of every kernel
-constexpr int kWarps = kThreads / 32;
-constexpr int kTile = 1024;               // slots per tile; populations start on a tile
-constexpr int kItems = kTile / kThreads;  // slots per thread in the tile kernels
-constexpr int kUnit = 256;                // slots per evolve work unit (one population)
-constexpr int kChunkUnits = 7;            // at most this many units staged in shared memory
-constexpr int kChunk = kUnit * kChunkUnits;
-constexpr int kKcap = 4096;               // fixed-point weight table size
-constexpr int kHistSmem = 512;            // activity bins kept in shared memory
-constexpr int kMap = 2048;                // new slots of one tile mapped in shared memory
-constexpr int kMaxL = 128;                // one clone per lane: W <= 2 words
-constexpr int kInvStride = kMaxL + 1;     // per-population 1/r table stride
-constexpr uint32_t kStepLimit = 1u << 24; // BKL steps per clone per interval
-
-constexpr int32_t kErrRange = -3;
-
-// Constant per run.
-struct PopDesc {
-  int32_t L, N;
-  int64_t nc;        // clones N_c
-  int64_t off;       // first slot of the population (a multiple of kTile)
-  uint64_t seed;     // Philox key
-  int32_t first_tile, ntiles;
-  int32_t s_neg;     // s < 0: the reference activity is the maximum
-  int32_t pad;
-  double s;          // bias
-  double abs_s;
-};
-
-// Mutable per population.
-struct PopState {
-  int32_t dk_min, dk_max;      // interval activity range (k_evolve; reset by k_gather)
-  int32_t kref;                // reference activity of this interval (k_weights)
-  uint32_t U;                  // [eq] offset word of this interval (k_weights)
-  double psi_acc;              // sum of psi terms (eq. psihat numerator)
-  unsigned long long events;   // executed hops since init
-  int32_t err;                 // sticky kernel-side error
-  int32_t pad;
-};
-
-struct Batch {
-  const PopDesc* pops;
-  PopState* st;
-  const int32_t* tile_pop;              // tile -> population
-  const unsigned long long* wtab;       // [P][kKcap] fixed-point weights
-  const double* qtab;                   // [P][kKcap] exp(-|s| k)
-  const double* qm1tab;                 // [P][kKcap] expm1(-|s| k)
-  const float* inv_rate;                // [P][kInvStride] float(1/r)
-  const float2* logtab;                 // [64] (1/c_i, ln c_i) of the waiting-time log
-  unsigned int* hist;                   // [P][kKcap] activity histogram (zero between intervals)
-  unsigned long long* tile_sum;         // [ntiles] weight sum of each tile
-  unsigned int* beta;                   // interval being evolved (1-based)
-  unsigned long long* X;                // evolved lattices  [slots][W]
-  unsigned long long* Y;                // population lattices between intervals [slots][W]
-  int32_t* KX;                          // evolved cumulative activity
-  int32_t* KY;                          // population cumulative activity
-  int32_t* dK;                          // activity of the last interval
-  int32_t* anc;                         // ancestors of the last cloning stage
-  long long* ksum;                      // [P] sum of K (estimates)
-  int32_t ntiles;
-  int32_t nunits;
-  int64_t nslots;
-};
-
-// ---------------------------------------------------------------------------
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32->64
-// multiplies with the published multipliers; the key is bumped by the published
-// Weyl constants between rounds.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    if (r > 0) {
-      k0 += 0x9E3779B9u;
-      k1 += 0xBB67AE85u;
-    }
-    const uint32_t lo0 = c.x * 0xD2511F53u;
-    const uint32_t hi0 = __umulhi(c.x, 0xD2511F53u);
-    const uint32_t lo1 = c.z * 0xCD9E8D57u;
-    const uint32_t hi1 = __umulhi(c.z, 0xCD9E8D57u);
-    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-  }
-  return c;
-}
-
-// ---------------------------------------------------------------------------
-// E = -ln(u), u = (2w+1)/2^33, in FP32 with a fixed sequence of operations:
-// v = 2w+1 truncated to its 24 leading bits, v' = m 2^p with m in [1, 2) and p the
-// position of the leading one; ln u' = (p-33) ln 2 + ln c_i + ln(1+r), where
-// c_i = 1 + (i + 1/2)/64 for the top 6 fraction bits i of m, r = m/c_i - 1
-// (|r| <= 1/128) and ln(1+r) ~ r (1 - r/2 + r^2/3).  tab[i] = (float(1/c_i),
-// float(ln c_i)).  ln 2 is a 15-bit head (exact products with 33-p) plus a float
-// tail.  Every float step is an explicitly rounded intrinsic, so no contraction
-// can change the bits; the integer work avoids 64-bit conversions, which run on
-// the narrow FP64 pipe of this part.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float neg_ln_u(uint32_t w, const float2* tab) {
-  const unsigned long long v = 2ull * (unsigned long long)w + 1ull;
-  const int p = 63 - __clzll((long long)v);  // 0..32
-  const uint32_t t = (p >= 23) ? (uint32_t)(v >> (p - 23)) : ((uint32_t)v << (23 - p));
-  const float m = __uint_as_float(0x3f800000u | (t & 0x007fffffu));
-  const float2 cl = tab[(t >> 17) & 63u];
-  const float r = __fmaf_rn(m, cl.x, -1.0f);
-  float q = __fmaf_rn(r, 0x1.555556p-2f, -0.5f);
-  q = __fmaf_rn(q, r, 1.0f);
-  const float ln_m = __fadd_rn(cl.y, __fmul_rn(q, r));
-  // float(33 - p) exactly: 1.5*2^23 + n has n in its low mantissa bits
-  const float n = __fsub_rn(__int_as_float(0x4B400000 + (33 - p)), 12582912.0f);
-  const float E = __fmaf_rn(n, 0x1.7f7d1cp-20f, -ln_m);
-  return __fmaf_rn(n, 0x1.62e4p-1f, E);
-}
-
-// ---------------------------------------------------------------------------
-// Lattice helpers.  A clone is W 64-bit words; site i is bit i%64 of word i/64.
-// Bond i joins sites i and (i+1) mod L; it is active (a hop across it is
-// possible) when exactly one end is occupied: a = x XOR rot(x), rot(x)_i = x_{i+1}.
-// ---------------------------------------------------------------------------
-template <int W>
-__device__ __forceinline__ void active_bonds(const unsigned long long (&x)[W], int L,
-                                             unsigned long long (&a)[W]) {
-  if constexpr (W == 1) {
-    const unsigned long long rot = (x[0] >> 1) | ((x[0] & 1ull) << (L - 1));
-    a[0] = x[0] ^ rot;
-  } else {
-    if (L <= 64) {
-      const unsigned long long rot = (x[0] >> 1) | ((x[0] & 1ull) << (L - 1));
-      a[0] = x[0] ^ rot;
-      a[1] = 0ull;
-    } else {
-      const unsigned long long r0 = (x[0] >> 1) | (x[1] << 63);
-      const unsigned long long r1 = (x[1] >> 1) | ((x[0] & 1ull) << (L - 65));
-      a[0] = x[0] ^ r0;
-      a[1] = x[1] ^ r1;
-    }
-  }
-}
-
-template <int W>
-__device__ __forceinline__ int popc_lat(const unsigned long long (&a)[W]) {
-  if constexpr (W == 1) return __popcll(a[0]);
-  else return __popcll(a[0]) + __popcll(a[1]);
-}
-
-// Position of the k-th (0-based) set bit of a, k < popc(a).
-#ifdef POP_KTH_FNS
-__device__ __forceinline__ int kth_set_bit64(unsigned long long a, uint32_t k) {
-  const uint32_t lo = (uint32_t)a;
-  const uint32_t c0 = (uint32_t)__popc(lo);
-  const bool in_lo = k < c0;
-  const uint32_t word = in_lo ? lo : (uint32_t)(a >> 32);
-  const uint32_t kk = in_lo ? k : k - c0;
-  return (int)__fns(word, 0u, (int)kk + 1) + (in_lo ? 0 : 32);
-}
-#else
-// binary descent on population counts of halves
-__device__ __forceinline__ int kth_set_bit64(unsigned long long a, uint32_t k) {
-  uint32_t x = (uint32_t)a;
-  int pos = 0;
-  uint32_t c = (uint32_t)__popc(x);
-  if (k >= c) { k -= c; x = (uint32_t)(a >> 32); pos = 32; }
-  c = (uint32_t)__popc(x & 0xffffu);
-  if (k >= c) { k -= c; x >>= 16; pos += 16; }
-  c = (uint32_t)__popc(x & 0xffu);
-  if (k >= c) { k -= c; x >>= 8; pos += 8; }
-  c = (uint32_t)__popc(x & 0xfu);
-  if (k >= c) { k -= c; x >>= 4; pos += 4; }
-  c = (uint32_t)__popc(x & 0x3u);
-  if (k >= c) { k -= c; x >>= 2; pos += 2; }
-  c = x & 1u;
-  if (k >= c) { pos += 1; }
-  return pos;
-}
-#endif
-
-template <int W>
-__device__ __forceinline__ int kth_bond(const unsigned long long (&a)[W], uint32_t k) {
-  if constexpr (W == 1) {
-    return kth_set_bit64(a[0], k);
-  } else {
-    const uint32_t c0 = (uint32_t)__popcll(a[0]);
-    const bool lo = k < c0;
-    return kth_set_bit64(lo ? a[0] : a[1], lo ? k : k - c0) + (lo ? 0 : 64);
-  }
-}
-
-// A hop across bond b swaps the occupations of sites b and (b+1) mod L, which
-// differ, so both bits flip.
-template <int W>
-__device__ __forceinline__ void hop(unsigned long long (&x)[W], int b, int L) {
-  const int b1 = (b + 1 == L) ? 0 : b + 1;
-  if constexpr (W == 1) {
-    x[0] ^= (1ull << b) | (1ull << b1);
-  } else {
-    unsigned long long m0 = 0ull, m1 = 0ull;
-    if (b < 64) m0 |= 1ull << b; else m1 |= 1ull << (b - 64);
-    if (b1 < 64) m0 |= 1ull << b1; else m1 |= 1ull << (b1 - 64);
-    x[0] ^= m0;
-    x[1] ^= m1;
-  }
-}
-
-template <int W>
-__device__ __forceinline__ void load_lat(const unsigned long long* base, int64_t slot,
-                                         unsigned long long (&x)[W]) {
-  if constexpr (W == 1) {
-    x[0] = base[slot];
-  } else {
-    const ulonglong2 v = reinterpret_cast<const ulonglong2*>(base)[slot];
-    x[0] = v.x;
-    x[1] = v.y;
-  }
-}
-
-template <int W>
-__device__ __forceinline__ void store_lat(unsigned long long* base, int64_t slot,
-                                          const unsigned long long (&x)[W]) {
-  if constexpr (W == 1) {
-    base[slot] = x[0];
-  } else {
-    reinterpret_cast<ulonglong2*>(base)[slot] = make_ulonglong2(x[0], x[1]);
-  }
-}
-
-__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-__device__ __forceinline__ double warp_sum_f64(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 // ---------------------------------------------------------------------------
 // Initial state: a uniform N-subset of the L sites by selection sampling; site t is
@@ -514,34 +245,6 @@ __global__ void __launch_bounds__(kThreads, 6) k_evolve(Batch B, float dt_f) {
   }
 }
 
-// Block-wide sum of one 64-bit value per thread (result valid in every thread).
-__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v,
-                                                            unsigned long long* scratch) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  v = warp_sum_u64(v);
-  if (lane == 0) scratch[wid] = v;
-  __syncthreads();
-  unsigned long long t = 0ull;
-#pragma unroll
-  for (int w = 0; w < kWarps; ++w) t += scratch[w];
-  __syncthreads();
-  return t;
-}
-
-// |a - b| as an unsigned magnitude (no overflow for any pair of ints), so that an
-// out-of-range activity is rejected by the table-size check instead of indexing.
-__device__ __forceinline__ unsigned int abs_diff(int a, int b) {
-  const long long d = (long long)a - (long long)b;
-  const unsigned long long m = d < 0 ? (unsigned long long)(-d) : (unsigned long long)d;
-  return m > 0xffffffffull ? 0xffffffffu : (unsigned int)m;
-}
-
-// Number of histogram bins in use, clamped to [0, cap].
-__device__ __forceinline__ int hist_bins(int dk_min, int dk_max, int cap) {
-  const long long n = (long long)dk_max - (long long)dk_min + 1;
-  return n < 0 ? 0 : (n > cap ? cap : (int)n);
-}
-
 // ---------------------------------------------------------------------------
 // Weights: F = 61 - ceil(log2 N_c); w = wtab[|dK - k_ref|] with k_ref the min (s >= 0)
 // or max (s < 0) activity, so every weight is at most 2^F and the total at most 2^61.
@@ -595,33 +298,6 @@ __global__ void __launch_bounds__(kThreads) k_weights(Batch B) {
                             (uint32_t)(d.seed >> 32)).x;
     }
   }
-}
-
-// 128-bit unsigned products and comparison.
-struct U128 { unsigned long long hi, lo; };
-__device__ __forceinline__ U128 mul128(unsigned long long a, unsigned long long b) {
-  return U128{__umul64hi(a, b), a * b};
-}
-__device__ __forceinline__ bool lt128(const U128& a, const U128& b) {
-  return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
-}
-
-// First new slot whose [eq] point lies at or beyond the prefix sum S:
-//   j_lo(S) = min{ j : (2^33 j + c) T >= S 2^33 N_c },  c = 2U + 1,
-// i.e. alpha_j = floor((2^33 j + c) T / (2^33 N_c)) >= S (eq. alpha-Ups with
-// d = c / 2^33).  A float estimate of S N_c / T (from the top 24 bits of S and T)
-// starts the search; exact 128-bit comparisons settle it.
-__device__ __forceinline__ uint32_t j_lo(unsigned long long S, unsigned long long T,
-                                         unsigned long long c, uint32_t nc, int sh,
-                                         float ratio) {
-  if (S == 0ull) return 0u;
-  if (S >= T) return nc;
-  const U128 R = mul128(S, (unsigned long long)nc << 33);
-  const float est = __fmul_rn(__uint2float_rn((uint32_t)(S >> sh)), ratio);
-  unsigned long long j = (unsigned long long)min((float)nc, floorf(est));
-  while (j < nc && lt128(mul128((j << 33) + c, T), R)) ++j;
-  while (j > 0 && !lt128(mul128(((j - 1ull) << 33) + c, T), R)) --j;
-  return (uint32_t)j;
 }
 
 // ---------------------------------------------------------------------------
