@@ -36,17 +36,32 @@ UNIT = "events/s"
 # compiled code:
 #   Philox4x32-10 shared by two steps: (10 rounds x (2 widening products = 4 ops,
 #     2 three-input XORs = 4 ops) + 9 x 2 key additions) / 2              = 49
-#   -ln(u): 2w+1 (2), int->float (1), exponent/mantissa split (3), fold (2),
-#     m-1, m+1, divide (3), z (1), 4 fma, f*p (1), exponent to float (2), 2 fma = 21
+#   -ln(u): 2w+1 (2), leading one (1), 24-bit head (2), mantissa bits (2),
+#     table index (2), two table reads (2), r (1), cubic (3), add (1),
+#     exponent to float (2), two fma (2)                                      = 20
 #   time: 1/r lookup, multiply, add, compare                                   = 4
 #   active bonds and rate: rotate (4), xor (1), popc (1), r == 0 test (1)      = 7
 #   bond choice: multiply-high (1), k-th set bit of 64 bits (6 levels x 4)    = 25
 #   hop: b+1 mod L (3), two bit masks (3), xor (1)                              = 7
 #   loop bookkeeping (step and hop counters, exit test)                         = 3
-OPS_HOP = 49 + 21 + 4 + 7 + 25 + 7 + 3          # a step that hops: 116
-OPS_STOP = OPS_HOP - 25 - 7 - 1                 # the step that ends the interval: 83
+OPS_HOP = 49 + 20 + 4 + 7 + 25 + 7 + 3          # a step that hops: 115
+OPS_STOP = OPS_HOP - 25 - 7 - 1                 # the step that ends the interval: 82
 N_SM = 152
 ISSUE_OPS_PER_SM_CLK = 128                      # 4 schedulers x 32 lanes
+
+# DRAM bytes (read + write) of one k_evolve launch on this workload, from one
+# `ncu --set full` capture (profiles/interval_kernels_s_sweep.md), valid only for the
+# kernel sources it was taken on (hash of the two device headers).
+EVOLVE_TRAFFIC = {"bytes": 13571072, "sources": "6342b56d362b3699"}
+
+
+def kernel_sources_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("pop_common.cuh", "pop_kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_1711_05095_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def parse():
@@ -249,7 +264,7 @@ def main():
         host_lat.append((pinned, kz))
     W = pg.lattice_words(pops)
     h2d = sum(q["n_clones"] * (8 * W + 4) for q in pops)
-    d2h = P * (48 + 8)      # per-population state record and K sum read by pop_estimate_psi
+    d2h = P * (40 + 8)      # per-population state record and K sum read by pop_estimate_psi
 
     def e2e_step():
         b = pg.PopulationBatch(pops, device=dev, stream=stream, workspace=ws)
@@ -314,7 +329,9 @@ def main():
                    "parallelism": "replicas%d" % world},
         "gpu_launches": (3 * M + 2) * args.steps,
         "roofline": {"bound": "alu", "kernel": "k_evolve", "achieved": achieved, "peak": peak_gops,
-                     "unit": "Gop/s", "frac": achieved / peak_gops, "traffic": None,
+                     "unit": "Gop/s", "frac": achieved / peak_gops,
+                     "traffic": (EVOLVE_TRAFFIC["bytes"] if kernel_sources_digest() == EVOLVE_TRAFFIC["sources"]
+                                 else None),
                      "peak_kind": "issue rate 152 SM x 128 lanes x %.0f MHz (%s max clock)"
                                   % (sm_max, peak_kind),
                      "launch_ms": 1e3 * t_ev, "resample_ms": 1e3 * t_rs,
