@@ -216,16 +216,26 @@ __device__ __forceinline__ int kth_bond(const unsigned long long (&a)[W], uint32
 }
 
 // A hop across bond b swaps the occupations of sites b and (b+1) mod L, which
-// differ, so both bits flip.
+// differ, so both bits flip: bits b, b+1 (or b and 0 for the closing bond L-1).
 template <int W>
 __device__ __forceinline__ void hop(unsigned long long (&x)[W], int b, int L) {
-  const int b1 = (b + 1 == L) ? 0 : b + 1;
   if constexpr (W == 1) {
-    x[0] ^= (1ull << b) | (1ull << b1);
+    x[0] ^= (b + 1 == L) ? ((1ull << b) | 1ull) : (3ull << b);
   } else {
-    unsigned long long m0 = 0ull, m1 = 0ull;
-    if (b < 64) m0 |= 1ull << b; else m1 |= 1ull << (b - 64);
-    if (b1 < 64) m0 |= 1ull << b1; else m1 |= 1ull << (b1 - 64);
+    unsigned long long m0, m1;
+    if (b + 1 == L) {
+      m0 = 1ull | (b < 64 ? (1ull << b) : 0ull);
+      m1 = b >= 64 ? (1ull << (b - 64)) : 0ull;
+    } else if (b < 63) {
+      m0 = 3ull << b;
+      m1 = 0ull;
+    } else if (b == 63) {
+      m0 = 1ull << 63;
+      m1 = 1ull;
+    } else {
+      m0 = 0ull;
+      m1 = 3ull << (b - 64);
+    }
     x[0] ^= m0;
     x[1] ^= m1;
   }
@@ -328,6 +338,33 @@ __device__ __forceinline__ uint32_t j_lo(unsigned long long S, unsigned long lon
   while (j < nc && lt128(mul128((j << 33) + c, T), R)) ++j;
   while (j > 0 && !lt128(mul128(((j - 1ull) << 33) + c, T), R)) --j;
   return (uint32_t)j;
+}
+
+// j_lo of the prefix sums S0, S0 + w[0], ..., S0 + w[0] + ... + w[n-1] (n + 1
+// values): the first exactly as above, the rest by walking j forward, since
+// (2^33 (j+1) + c) T = (2^33 j + c) T + 2^33 T.
+template <int n>
+__device__ __forceinline__ void j_lo_run(unsigned long long S0, const unsigned long long (&w)[n],
+                                         unsigned long long T, unsigned long long c, uint32_t nc,
+                                         int sh, float ratio, uint32_t (&out)[n + 1]) {
+  unsigned long long j = j_lo(S0, T, c, nc, sh, ratio);
+  out[0] = (uint32_t)j;
+  U128 X = mul128((j << 33) + c, T);
+  const unsigned long long step_hi = T >> 31, step_lo = T << 33;  // 2^33 T
+  const unsigned long long nc33 = (unsigned long long)nc << 33;
+  unsigned long long S = S0;
+#pragma unroll
+  for (int i = 0; i < n; ++i) {
+    S += w[i];
+    const U128 R = mul128(S, nc33);
+    while (j < nc && lt128(X, R)) {
+      ++j;
+      const unsigned long long lo = X.lo + step_lo;
+      X.hi += step_hi + (lo < X.lo ? 1ull : 0ull);
+      X.lo = lo;
+    }
+    out[i + 1] = (uint32_t)j;
+  }
 }
 
 }  // namespace popgpu

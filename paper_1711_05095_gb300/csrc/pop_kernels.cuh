@@ -84,8 +84,11 @@ __device__ __forceinline__ bool bkl_step(unsigned long long (&x)[W], float& t, i
 // the block from a shared-memory counter, so lanes stay busy until the block's
 // clones run out and no block-wide barrier is needed during the interval.
 // ---------------------------------------------------------------------------
+#ifndef POP_EVOLVE_MIN_BLOCKS
+#define POP_EVOLVE_MIN_BLOCKS 5
+#endif
 template <int W>
-__global__ void __launch_bounds__(kThreads, 6) k_evolve(Batch B, float dt_f) {
+__global__ void __launch_bounds__(kThreads, POP_EVOLVE_MIN_BLOCKS) k_evolve(Batch B, float dt_f) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   EvolveSmem<W>& S = *reinterpret_cast<EvolveSmem<W>*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31;
@@ -379,12 +382,11 @@ __global__ void __launch_bounds__(kThreads, 6) k_gather(Batch B) {
   const float ratio = __fdiv_rn((float)nc, __uint2float_rn((uint32_t)(T >> sh)));
   unsigned long long run = excl + xs - tsum;
   for (int q = 0; q < wid; ++q) run += s_wsum[q];
+  uint32_t jl[kItems + 1];
+  j_lo_run<kItems>(run, w, T, c, nc, sh, ratio, jl);
 #pragma unroll
-  for (int i = 0; i < kItems; ++i) {
-    s_jlo[tid * kItems + i] = j_lo(run, T, c, nc, sh, ratio);
-    run += w[i];
-  }
-  if (tid == kThreads - 1) s_jlo[kTile] = j_lo(run, T, c, nc, sh, ratio);
+  for (int i = 0; i < kItems; ++i) s_jlo[tid * kItems + i] = jl[i];
+  if (tid == kThreads - 1) s_jlo[kTile] = jl[kItems];
   __syncthreads();
 
   const uint32_t J0 = s_jlo[0], J1 = s_jlo[kTile];
