@@ -61,12 +61,13 @@ extern "C" {
 #define POP_IID 1 /* independent alpha_j; not available yet */
 
 #define POP_KCAP 4096     /* size of the fixed-point weight table */
-#define POP_MAX_L 128     /* largest ring handled by the one-clone-per-thread evolve */
+#define POP_MAX_L 4096    /* largest ring; rings above 128 sites run one clone per warp */
 #define POP_MAX_CLONES (1LL << 30)
 
 /* One population of the batch. */
 typedef struct pop_params {
-  int32_t L;           /* ring length, 3 <= L <= POP_MAX_L */
+  int32_t L;           /* ring length, 3 <= L <= POP_MAX_L (a batch with any L > 128
+                          runs every population with the one-clone-per-warp evolve) */
   int32_t N;           /* particles, 0 <= N <= L */
   int64_t n_clones;    /* N_c, 1 <= N_c <= POP_MAX_CLONES */
   uint64_t seed;       /* Philox key of this population's streams */

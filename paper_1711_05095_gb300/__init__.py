@@ -26,7 +26,7 @@ POP_MODIFIED = 1
 POP_EQ = 0
 POP_IID = 1
 POP_KCAP = 4096
-POP_MAX_L = 128
+POP_MAX_L = 4096
 
 # every symbol include/pop.h declares
 EXPORTS = ("pop_workspace_bytes", "pop_init", "pop_set_state", "pop_evolve", "pop_resample",

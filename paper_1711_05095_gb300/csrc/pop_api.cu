@@ -177,7 +177,8 @@ bool valid_dt(double dt) { return std::isfinite(dt) && dt > 0.0 && dt < 1e30; }
 int launch_evolve(pop_t* h, cudaStream_t st, float dt_f) {
   const unsigned grid = (unsigned)h->evolve_grid;
   if (h->lay.W == 1) k_evolve<1><<<grid, kThreads, h->evolve_smem, st>>>(h->B, dt_f);
-  else k_evolve<2><<<grid, kThreads, h->evolve_smem, st>>>(h->B, dt_f);
+  else if (h->lay.W == 2) k_evolve<2><<<grid, kThreads, h->evolve_smem, st>>>(h->B, dt_f);
+  else k_evolve_wide<<<grid, kThreads, 0, st>>>(h->B, dt_f);
   return cuda_status(cudaGetLastError());
 }
 
@@ -185,7 +186,8 @@ int launch_resample(pop_t* h, cudaStream_t st) {
   const unsigned grid = (unsigned)h->lay.ntiles;
   k_weights<<<grid, kThreads, 0, st>>>(h->B);
   if (h->lay.W == 1) k_gather<1><<<grid, kThreads, 0, st>>>(h->B);
-  else k_gather<2><<<grid, kThreads, 0, st>>>(h->B);
+  else if (h->lay.W == 2) k_gather<2><<<grid, kThreads, 0, st>>>(h->B);
+  else k_gather<0><<<grid, kThreads, 0, st>>>(h->B);
   return cuda_status(cudaGetLastError());
 }
 
@@ -203,6 +205,19 @@ int size_evolve_grid(pop_t* h) {
   const long long want = (long long)per_sm * sms;
   h->evolve_grid = (int)(want < h->lay.nunits ? want : h->lay.nunits);
   h->evolve_smem = smem;
+  return POP_OK;
+}
+
+// Rings longer than 128 sites: one warp per clone, a grid-stride loop over slots.
+int size_evolve_grid_wide(pop_t* h) {
+  int per_sm = 0, sms = 0;
+  POP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_evolve_wide, kThreads, 0));
+  POP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+  if (per_sm < 1) per_sm = 1;
+  const long long want = (long long)per_sm * sms;
+  const long long need = (h->lay.nslots + kWarps - 1) / kWarps;
+  h->evolve_grid = (int)(want < need ? want : need);
+  h->evolve_smem = 0;
   return POP_OK;
 }
 
@@ -329,12 +344,15 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
   B.ntiles = lay.ntiles;
   B.nunits = lay.nunits;
   B.nslots = lay.nslots;
-  if ((lay.W == 1 ? size_evolve_grid<1>(h) : size_evolve_grid<2>(h)) != POP_OK)
-    return fail(POP_ERR_CUDA);
+  B.W = lay.W;
+  const int grc = lay.W == 1 ? size_evolve_grid<1>(h)
+                  : (lay.W == 2 ? size_evolve_grid<2>(h) : size_evolve_grid_wide(h));
+  if (grc != POP_OK) return fail(POP_ERR_CUDA);
 
   const unsigned grid = (unsigned)(lay.nslots / kThreads);
   if (lay.W == 1) k_init<1><<<grid, kThreads, 0, h->stream>>>(B);
-  else k_init<2><<<grid, kThreads, 0, h->stream>>>(B);
+  else if (lay.W == 2) k_init<2><<<grid, kThreads, 0, h->stream>>>(B);
+  else k_init<0><<<grid, kThreads, 0, h->stream>>>(B);
   if (cudaGetLastError() != cudaSuccess) return fail(POP_ERR_CUDA);
   // host tables above are stack vectors: wait until their copies have landed
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(POP_ERR_CUDA);

@@ -41,7 +41,8 @@ constexpr int kKcap = 4096;               // fixed-point weight table size
 constexpr int kHistSmem = 512;            // activity bins kept in shared memory
 constexpr int kMap = 2048;                // new slots of one tile mapped in shared memory
 constexpr int kMaxL = 128;                // one clone per lane: W <= 2 words
-constexpr int kInvStride = kMaxL + 1;     // per-population 1/r table stride
+constexpr int kMaxLWide = 4096;           // one clone per warp: 2 words per lane
+constexpr int kInvStride = kMaxLWide + 1; // per-population 1/r table stride
 constexpr uint32_t kStepLimit = 1u << 24; // BKL steps per clone per interval
 
 constexpr int32_t kErrRange = -3;
@@ -92,6 +93,8 @@ struct Batch {
   int32_t ntiles;
   int32_t nunits;
   int64_t nslots;
+  int32_t W;                            // lattice words per clone
+  int32_t pad;
 };
 
 // ---------------------------------------------------------------------------

@@ -17,25 +17,47 @@ __global__ void __launch_bounds__(kThreads) k_init(Batch B) {
   const int p = B.tile_pop[slot / kTile];
   const PopDesc d = B.pops[p];
   const int64_t j = slot - d.off;
-  unsigned long long x[W];
-#pragma unroll
-  for (int q = 0; q < W; ++q) x[q] = 0ull;
-  if (j < d.nc) {
+  if constexpr (W == 0) {
+    // wide lattices: words are written as soon as their 64 sites are decided
     const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
+    const bool valid = j < d.nc;
     int taken = 0;
-    for (int t = 0; t < d.L; ++t) {
-      const int need = d.N - taken;
-      if (need <= 0) break;
-      const uint4 r = philox4x32_10(make_uint4((uint32_t)t, 0u, (uint32_t)j, kTagInit), k0, k1);
-      const unsigned long long u = ((unsigned long long)r.y << 32) | r.x;
-      if (__umul64hi(u, (unsigned long long)(d.L - t)) < (unsigned long long)need) {
-        if (W == 1 || t < 64) x[0] |= 1ull << (t & 63);
-        else x[W - 1] |= 1ull << (t & 63);
-        ++taken;
+    unsigned long long word = 0ull;
+    for (int t = 0; t < 64 * B.W; ++t) {
+      if (valid && t < d.L && d.N - taken > 0) {
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)t, 0u, (uint32_t)j, kTagInit), k0, k1);
+        const unsigned long long u = ((unsigned long long)r.y << 32) | r.x;
+        if (__umul64hi(u, (unsigned long long)(d.L - t)) < (unsigned long long)(d.N - taken)) {
+          word |= 1ull << (t & 63);
+          ++taken;
+        }
+      }
+      if ((t & 63) == 63) {
+        B.Y[slot * B.W + (t >> 6)] = word;
+        word = 0ull;
       }
     }
+  } else {
+    unsigned long long x[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) x[q] = 0ull;
+    if (j < d.nc) {
+      const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
+      int taken = 0;
+      for (int t = 0; t < d.L; ++t) {
+        const int need = d.N - taken;
+        if (need <= 0) break;
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)t, 0u, (uint32_t)j, kTagInit), k0, k1);
+        const unsigned long long u = ((unsigned long long)r.y << 32) | r.x;
+        if (__umul64hi(u, (unsigned long long)(d.L - t)) < (unsigned long long)need) {
+          if (W == 1 || t < 64) x[0] |= 1ull << (t & 63);
+          else x[W - 1] |= 1ull << (t & 63);
+          ++taken;
+        }
+      }
+    }
+    store_lat<W>(B.Y, slot, x);
   }
-  store_lat<W>(B.Y, slot, x);
   B.KY[slot] = 0;
   B.dK[slot] = 0;
 }
@@ -45,7 +67,7 @@ template <int W>
 struct EvolveSmem {
   unsigned long long x[kChunk][W];  // lattices (in, then out)
   int32_t hops[kChunk];             // activity of the interval
-  float inv[kChunkUnits][kInvStride];
+  float inv[kChunkUnits][kMaxL + 1];
   float2 logtab[64];
   uint2 u_key[kChunkUnits];         // Philox key of the unit's population
   int32_t u_j0[kChunkUnits];        // population-local index of the unit's first slot
@@ -122,8 +144,8 @@ __global__ void __launch_bounds__(kThreads, POP_EVOLVE_MIN_BLOCKS) k_evolve(Batc
     for (int m = 0; m < kChunkUnits; ++m)
       if (m < nu) ky[m] = B.KY[chunk_slot0 + m * kUnit + tid];
     __syncthreads();
-    for (int i = tid; i < nu * kInvStride; i += kThreads) {
-      const int uu = i / kInvStride, r = i % kInvStride;
+    for (int i = tid; i < nu * (kMaxL + 1); i += kThreads) {
+      const int uu = i / (kMaxL + 1), r = i % (kMaxL + 1);
       S.inv[uu][r] = (r <= S.u_L[uu]) ? B.inv_rate[(size_t)S.u_pop[uu] * kInvStride + r] : 0.0f;
     }
 #pragma unroll
@@ -314,7 +336,8 @@ __global__ void __launch_bounds__(kThreads) k_weights(Batch B) {
 // ---------------------------------------------------------------------------
 template <int W>
 __global__ void __launch_bounds__(kThreads, 6) k_gather(Batch B) {
-  __shared__ unsigned long long s_x[kTile][W];
+  constexpr int WS = W > 0 ? W : 1;  // W == 0: wide lattices, copied without staging
+  __shared__ unsigned long long s_x[W > 0 ? kTile : 1][WS];
   __shared__ int32_t s_K[kTile];
   __shared__ uint32_t s_jlo[kTile + 1];
   __shared__ uint16_t s_src[kMap];
@@ -336,10 +359,12 @@ __global__ void __launch_bounds__(kThreads, 6) k_gather(Batch B) {
   for (int m = 0; m < kItems; ++m) {
     const int i = m * kThreads + tid;
     if (base - d.off + i < d.nc) {
-      unsigned long long x[W];
-      load_lat<W>(B.X, base + i, x);
+      if constexpr (W > 0) {
+        unsigned long long x[W];
+        load_lat<W>(B.X, base + i, x);
 #pragma unroll
-      for (int q = 0; q < W; ++q) s_x[i][q] = x[q];
+        for (int q = 0; q < W; ++q) s_x[i][q] = x[q];
+      }
       s_K[i] = B.KX[base + i];
     }
   }
@@ -399,25 +424,38 @@ __global__ void __launch_bounds__(kThreads, 6) k_gather(Batch B) {
     }
     __syncthreads();
   }
-  for (uint32_t jj = J0 + (uint32_t)tid; jj < J1; jj += kThreads) {
-    int k;
-    if (mapped) {
-      k = s_src[jj - J0];
-    } else {  // one old clone with very many copies: search the sorted j_lo
-      int lo = 0, hi = kTile - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_jlo[mid] <= jj) lo = mid; else hi = mid - 1;
-      }
-      k = lo;
+  auto source = [&](uint32_t jj) -> int {
+    if (mapped) return s_src[jj - J0];
+    int lo = 0, hi = kTile - 1;  // one old clone with very many copies: search j_lo
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_jlo[mid] <= jj) lo = mid; else hi = mid - 1;
     }
-    unsigned long long x[W];
+    return lo;
+  };
+  if constexpr (W > 0) {
+    for (uint32_t jj = J0 + (uint32_t)tid; jj < J1; jj += kThreads) {
+      const int k = source(jj);
+      unsigned long long x[W];
 #pragma unroll
-    for (int q = 0; q < W; ++q) x[q] = s_x[k][q];
-    const int64_t dst = d.off + (int64_t)jj;
-    store_lat<W>(B.Y, dst, x);
-    B.KY[dst] = s_K[k];
-    B.anc[dst] = lt * kTile + k;
+      for (int q = 0; q < W; ++q) x[q] = s_x[k][q];
+      const int64_t dst = d.off + (int64_t)jj;
+      store_lat<W>(B.Y, dst, x);
+      B.KY[dst] = s_K[k];
+      B.anc[dst] = lt * kTile + k;
+    }
+  } else {
+    // one warp per new clone; its lanes copy the lattice words (coalesced)
+    for (uint32_t jj = J0 + (uint32_t)wid; jj < J1; jj += kWarps) {
+      const int k = source(jj);
+      const int64_t dst = d.off + (int64_t)jj;
+      for (int q = lane; q < B.W; q += 32)
+        B.Y[dst * B.W + q] = B.X[(base + k) * B.W + q];
+      if (lane == 0) {
+        B.KY[dst] = s_K[k];
+        B.anc[dst] = lt * kTile + k;
+      }
+    }
   }
 
   // psi term of eq. (psihat) for this interval, once per population:
@@ -450,6 +488,109 @@ __global__ void __launch_bounds__(kThreads, 6) k_gather(Batch B) {
     }
   }
   if (blockIdx.x == gridDim.x - 1 && tid == 0) *B.beta += 1u;
+}
+
+// ---------------------------------------------------------------------------
+// Dynamical stage for rings longer than 128 sites: one warp per clone.  Lane l
+// holds sites [128 l, 128 l + 128) in two words.  Active bonds are x XOR rot(x),
+// where the site above a lane's top bit is bit 0 of the next lane and the site
+// above L-1 is site 0.  The escape rate is a warp sum, the k-th active bond is
+// found from an exclusive prefix of the lanes' counts, and the draw, the waiting
+// time and the bond index are the same on every lane (the same arithmetic as the
+// one-clone-per-lane kernel, so results are identical to the oracle's).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void wide_active(unsigned long long xl, unsigned long long xh, int L,
+                                            int lane, unsigned long long& al,
+                                            unsigned long long& ah) {
+  const unsigned long long nb = __shfl_sync(0xffffffffu, xl, (lane + 1) & 31) & 1ull;
+  const unsigned long long b0 = __shfl_sync(0xffffffffu, xl, 0) & 1ull;
+  const int last = (L - 1) >> 7, pos = (L - 1) & 127;
+  unsigned long long rl = (xl >> 1) | (xh << 63);
+  unsigned long long rh = (xh >> 1) | (nb << 63);
+  if (lane == last) {
+    if (pos < 64) rl |= b0 << pos; else rh |= b0 << (pos - 64);
+  }
+  if (lane > last) { rl = 0ull; rh = 0ull; }
+  al = xl ^ rl;
+  ah = xh ^ rh;
+}
+
+// One BKL step of the warp's clone; returns true if it hopped.
+__device__ __forceinline__ bool wide_step(unsigned long long& xl, unsigned long long& xh,
+                                          float& t, int L, int lane, const float* inv,
+                                          const float2* tab, uint32_t wa, uint32_t wb,
+                                          float dt_f) {
+  unsigned long long al, ah;
+  wide_active(xl, xh, L, lane, al, ah);
+  const int cl = __popcll(al) + __popcll(ah);
+  const int r = __reduce_add_sync(0xffffffffu, (unsigned int)cl);
+  if (r == 0) return false;
+  const float t_new = __fadd_rn(t, __fmul_rn(neg_ln_u(wa, tab), inv[r]));
+  if (t_new >= dt_f) return false;
+  t = t_new;
+  const uint32_t k = __umulhi(wb, (uint32_t)r);
+  int incl = cl;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int excl = incl - cl;
+  const unsigned int owner_mask = __ballot_sync(0xffffffffu, (uint32_t)excl <= k && k < (uint32_t)incl);
+  const int owner = __ffs(owner_mask) - 1;
+  int bpos = 0;
+  if (lane == owner) {
+    const uint32_t kk = k - (uint32_t)excl;
+    const uint32_t cl0 = (uint32_t)__popcll(al);
+    bpos = (kk < cl0) ? kth_set_bit64(al, kk) : 64 + kth_set_bit64(ah, kk - cl0);
+  }
+  const int b = (owner << 7) + __shfl_sync(0xffffffffu, bpos, owner);
+  const int b1 = (b + 1 == L) ? 0 : b + 1;
+  if ((b >> 7) == lane) { const int q = b & 127; if (q < 64) xl ^= 1ull << q; else xh ^= 1ull << (q - 64); }
+  if ((b1 >> 7) == lane) { const int q = b1 & 127; if (q < 64) xl ^= 1ull << q; else xh ^= 1ull << (q - 64); }
+  return true;
+}
+
+__global__ void __launch_bounds__(kThreads) k_evolve_wide(Batch B, float dt_f) {
+  __shared__ float2 s_tab[64];
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid < 64) s_tab[tid] = B.logtab[tid];
+  __syncthreads();
+  const uint32_t beta = *B.beta;
+  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+  for (int64_t slot = (int64_t)blockIdx.x * kWarps + (tid >> 5); slot < B.nslots; slot += nwarps) {
+    const int p = B.tile_pop[slot / kTile];
+    const PopDesc d = B.pops[p];
+    const int64_t j = slot - d.off;
+    if (j >= d.nc) continue;  // padding (warp-uniform)
+    const int W = B.W;
+    unsigned long long xl = (2 * lane < W) ? B.Y[slot * W + 2 * lane] : 0ull;
+    unsigned long long xh = (2 * lane + 1 < W) ? B.Y[slot * W + 2 * lane + 1] : 0ull;
+    const float* inv = B.inv_rate + (size_t)p * kInvStride;
+    const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
+    float t = 0.0f;
+    int h = 0;
+    for (uint32_t q = 0;; ++q) {
+      if (q >= kStepLimit / 2u) {  // guard: an interval must end; report, never spin
+        if (lane == 0) B.st[p].err = kErrRange;
+        break;
+      }
+      const uint4 d4 = philox4x32_10(make_uint4(q, beta, (uint32_t)j, kTagEvolve), k0, k1);
+      if (!wide_step(xl, xh, t, d.L, lane, inv, s_tab, d4.x, d4.y, dt_f)) break;
+      ++h;
+      if (!wide_step(xl, xh, t, d.L, lane, inv, s_tab, d4.z, d4.w, dt_f)) break;
+      ++h;
+    }
+    if (2 * lane < W) B.X[slot * W + 2 * lane] = xl;
+    if (2 * lane + 1 < W) B.X[slot * W + 2 * lane + 1] = xh;
+    if (lane == 0) {
+      B.KX[slot] = B.KY[slot] + h;
+      B.dK[slot] = h;
+      atomicMin(&B.st[p].dk_min, h);
+      atomicMax(&B.st[p].dk_max, h);
+      atomicAdd(&B.st[p].events, (unsigned long long)h);
+    }
+  }
 }
 
 // Sum of the carried activities of each population (for k_hat, eq. khat).

@@ -44,7 +44,8 @@ def test_workspace_bytes(lib):
     assert a > 0 and a % 256 == 0 and b > a
     assert pg.lattice_words([P(L=64)]) == 1
     assert pg.lattice_words([P(L=65), P(L=20)]) == 2
-    for bad in (P(L=2), P(L=129), P(N=-1), P(N=21), P(n_clones=0), P(weight_mode=7), P(selection=9)):
+    assert pg.lattice_words([P(L=4096, N=5)]) == 64
+    for bad in (P(L=2), P(L=4097), P(N=-1), P(N=21), P(n_clones=0), P(weight_mode=7), P(selection=9)):
         assert pg.workspace_bytes([bad]) == 0, bad
 
 

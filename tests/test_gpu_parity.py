@@ -216,3 +216,22 @@ def test_call_order_and_bias_errors(pg):
     with pytest.raises(pg.PopError) as e:
         batch.evolve(-0.1, [0.2])
     assert e.value.status == pg.POP_ERR_ARG
+
+
+@pytest.mark.parametrize("L,N,nc,s,dt", [
+    (129, 64, 1100, 0.01, 0.05),     # narrowest ring of the one-clone-per-warp evolve
+    (200, 37, 2100, -0.02, 0.05),
+    (256, 128, 1025, 0.003, 0.05),   # exactly two lanes of sites
+    (1000, 500, 700, 0.001, 0.01),
+    (4096, 2048, 300, 0.0001, 0.005),  # widest ring: all 32 lanes, closing bond in lane 31
+    (3000, 1, 500, 0.5, 0.2),        # one particle on a long ring
+])
+def test_parity_wide_rings(pg, L, N, nc, s, dt):
+    run_parity(pg, [dict(L=L, N=N, n_clones=nc, seed=77 + L)], [s], dt, 3)
+
+
+def test_parity_mixed_batch_wide(pg):
+    # one ring above 128 sites puts every population of the batch on the wide path
+    pops = [dict(L=50, N=25, n_clones=1500, seed=1), dict(L=300, N=150, n_clones=1100, seed=2),
+            dict(L=7, N=3, n_clones=900, seed=3)]
+    run_parity(pg, pops, [0.02, 0.004, -0.3], 0.05, 3)
