@@ -139,6 +139,32 @@ def dist_setup(args):
     return world, rank, local
 
 
+def rank_populations(pops, rank):
+    """Weak scaling: every rank runs the whole batch as an independent replica with
+    its own seeds (populations never span ranks, so no data-path collective)."""
+    return [dict(q, seed=q["seed"] + 100000 * rank) for q in pops]
+
+
+def reduce_over_ranks(dist, device, seconds, units):
+    """(max seconds over ranks, sum of units over ranks): value = units / seconds."""
+    if dist is None:
+        return float(seconds), float(units)
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    e = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(e.item())
+
+
+def seconds_to_se(sigma, batch_seconds, batch_runs, target=1e-3):
+    """Device seconds to bring the standard error of psi_hat over independent runs to
+    `target`: R = ceil((sigma / target)^2) runs at the measured time per run."""
+    import math
+    runs = max(2, int(math.ceil((sigma / target) ** 2)))
+    return runs, batch_seconds * runs / batch_runs
+
+
 def cpu_oracle_sample(w, pop_idx, M):
     """The oracle as it stands, single-threaded, on the listed populations for M
     intervals.  Returns (events, seconds)."""
@@ -201,8 +227,7 @@ def main():
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
 
-    # weak scaling: every rank runs its own 64-population batch with its own seeds
-    pops = [dict(q, seed=q["seed"] + 100000 * rank) for q in w["pops"]]
+    pops = rank_populations(w["pops"], rank)
     s, dt, M = w["s"], w["dt"], w["M"]
     P = len(pops)
     nbytes = pg.workspace_bytes(pops)
@@ -242,15 +267,7 @@ def main():
     barrier()
     wall = time.perf_counter() - t_wall0
     clocks = sampler.stop()
-    t_dev = sum(ms) / 1e3
-    if dist is not None:
-        t = torch.tensor([t_dev], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e = torch.tensor([ev_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(e, op=dist.ReduceOp.SUM)
-        t_dev, ev_all = float(t.item()), float(e.item())
-    else:
-        ev_all = float(ev_total)
+    t_dev, ev_all = reduce_over_ranks(dist, dev, sum(ms) / 1e3, ev_total)
     value = ev_all / t_dev
 
     # end to end through the C ABI with host buffers: initial configurations from
@@ -285,13 +302,8 @@ def main():
         t0 = time.perf_counter()
         e2e_ev += e2e_step()
         e2e_t += time.perf_counter() - t0
-    e2e_value = e2e_ev / e2e_t
-    if dist is not None:
-        t = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e = torch.tensor([e2e_ev], dtype=torch.float64, device=dev)
-        dist.all_reduce(e, op=dist.ReduceOp.SUM)
-        e2e_value = float(e.item()) / float(t.item())
+    e2e_t_all, e2e_ev_all = reduce_over_ranks(dist, dev, e2e_t, e2e_ev)
+    e2e_value = e2e_ev_all / e2e_t_all
 
     # dominant kernel: k_evolve, timed with CUDA events on the launching stream
     R = args.kernel_intervals
@@ -312,6 +324,26 @@ def main():
     t_ev = sum(a0.elapsed_time(a1) for a0, a1, _ in evs) / R / 1e3
     t_rs = sum(a1.elapsed_time(a2) for _, a1, a2 in evs) / R / 1e3
     clone_intervals = sum(q["n_clones"] for q in pops)
+
+    # seconds to SE(psi_hat) <= 1e-3 at lambda = 20 (s = 0.008): 64 independent seeds
+    # of the same population, one batch, full t_obs
+    se_w = workloads.seed_replicas(w["pops"][0], 20.0 / 50**2, 64, seed=500000 + 1000 * rank)
+    se_pops = se_w["pops"]
+    ws_se = torch.empty(pg.workspace_bytes(se_pops), dtype=torch.uint8, device=dev)
+    flush.zero_()
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    b = pg.PopulationBatch(se_pops, device=dev, stream=stream, workspace=ws_se)
+    b.run(dt, se_w["s"], M)
+    psi_se, _, _ = b.estimate_psi()
+    s1.record(stream)
+    s1.synchronize()
+    b.close()
+    se_batch_s = s0.elapsed_time(s1) / 1e3
+    sigma = float(np.std(psi_se, ddof=1))
+    se_runs, se_seconds = seconds_to_se(sigma, se_batch_s, len(se_pops))
+    del ws_se
     ops_per_launch = (OPS_HOP * ev_k + OPS_STOP * clone_intervals * R) / R
     peaks, peak_kind = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -337,6 +369,11 @@ def main():
                      "launch_ms": 1e3 * t_ev, "resample_ms": 1e3 * t_rs,
                      "ops_per_launch": ops_per_launch},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "seconds_to_se": {"value": se_seconds, "unit": "s", "target_se": 1e-3,
+                          "workload": "L=50 N=25 lambda=20 N_c=16384 dt=0.1 t_obs=%g" % w["t_obs"],
+                          "sigma_per_run": sigma, "runs_needed": se_runs,
+                          "batch_runs": len(se_pops), "batch_seconds": se_batch_s,
+                          "mean_psi": float(np.mean(psi_se)), "method": "plain cloning"},
         "clocks": clocks,
         "wall_s_timed": wall,
         "psi_check": {"lambda=-20": float(psi[0]), "lambda=40": float(psi[-1])},

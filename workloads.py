@@ -57,6 +57,13 @@ def uneven_batch(n_pops=256, dt=0.1, t_obs=500.0, seed=12345):
     return _w(pops, lam / Ls.astype(np.float64) ** 2, dt, t_obs)
 
 
+def seed_replicas(pop, s, n_runs, seed, dt=0.1, t_obs=1000.0):
+    """n_runs independent copies (own seeds) of one population at bias s: the
+    replicas whose spread gives the standard error of psi_hat."""
+    pops = [dict(pop, seed=seed + r) for r in range(n_runs)]
+    return _w(pops, [s] * n_runs, dt, t_obs)
+
+
 def random_subsets(L, N, n_clones, seed):
     """Host-side uniform N-subsets packed as uint64 words (n_clones, ceil(L/64)):
     initial configurations supplied from host memory (pop_set_state)."""
