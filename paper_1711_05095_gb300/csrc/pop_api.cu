@@ -205,6 +205,8 @@ int size_evolve_grid(pop_t* h) {
   const long long want = (long long)per_sm * sms;
   h->evolve_grid = (int)(want < h->lay.nunits ? want : h->lay.nunits);
   h->evolve_smem = smem;
+  h->B.unit_q = h->lay.nunits / h->evolve_grid;
+  h->B.unit_r = h->lay.nunits % h->evolve_grid;
   return POP_OK;
 }
 

@@ -94,6 +94,7 @@ struct Batch {
   int32_t nunits;
   int64_t nslots;
   int32_t W;                            // lattice words per clone
+  int32_t unit_q, unit_r;               // k_evolve: nunits = unit_q * grid + unit_r
   int32_t pad;
 };
 

@@ -116,12 +116,16 @@ __global__ void __launch_bounds__(kThreads, POP_EVOLVE_MIN_BLOCKS) k_evolve(Batc
   const int tid = threadIdx.x, lane = tid & 31;
   const uint32_t beta = *B.beta;
   if (tid < 64) S.logtab[tid] = B.logtab[tid];
-  const int u_begin = (int)((long long)blockIdx.x * B.nunits / gridDim.x);
-  const int u_end = (int)((long long)(blockIdx.x + 1) * B.nunits / gridDim.x);
-  const int nchunks = (u_end - u_begin + kChunkUnits - 1) / kChunkUnits;
+  // this block's units: an even split of B.nunits over the grid, B.unit_q units each
+  // and one more for the first B.unit_r blocks (no divisions on the device)
+  const int bx = (int)blockIdx.x;
+  const int u_begin = bx * B.unit_q + min(bx, B.unit_r);
+  const int len = B.unit_q + (bx < B.unit_r ? 1 : 0);
+  const int nchunks = (len + kChunkUnits - 1) / kChunkUnits;
+  const int cq = len / nchunks, cr = len - cq * nchunks;
   for (int ch = 0; ch < nchunks; ++ch) {
-    const int uc = u_begin + (int)((long long)ch * (u_end - u_begin) / nchunks);
-    const int nu = u_begin + (int)((long long)(ch + 1) * (u_end - u_begin) / nchunks) - uc;
+    const int uc = u_begin + ch * cq + min(ch, cr);
+    const int nu = cq + (ch < cr ? 1 : 0);
     const int64_t chunk_slot0 = (int64_t)uc * kUnit;
     if (tid < nu) {
       const int64_t slot0 = chunk_slot0 + (int64_t)tid * kUnit;
@@ -144,9 +148,9 @@ __global__ void __launch_bounds__(kThreads, POP_EVOLVE_MIN_BLOCKS) k_evolve(Batc
     for (int m = 0; m < kChunkUnits; ++m)
       if (m < nu) ky[m] = B.KY[chunk_slot0 + m * kUnit + tid];
     __syncthreads();
-    for (int i = tid; i < nu * (kMaxL + 1); i += kThreads) {
-      const int uu = i / (kMaxL + 1), r = i % (kMaxL + 1);
-      S.inv[uu][r] = (r <= S.u_L[uu]) ? B.inv_rate[(size_t)S.u_pop[uu] * kInvStride + r] : 0.0f;
+    for (int uu = 0; uu < nu; ++uu) {
+      const float* src = B.inv_rate + (size_t)S.u_pop[uu] * kInvStride;
+      for (int r = tid; r <= kMaxL; r += kThreads) S.inv[uu][r] = (r <= S.u_L[uu]) ? src[r] : 0.0f;
     }
 #pragma unroll
     for (int m = 0; m < kChunkUnits; ++m) {
