@@ -25,6 +25,7 @@ _i32p = ctypes.POINTER(ctypes.c_int32)
 _u32p = ctypes.POINTER(ctypes.c_uint32)
 _u64p = ctypes.POINTER(ctypes.c_uint64)
 _f64p = ctypes.POINTER(ctypes.c_double)
+_f32p = ctypes.POINTER(ctypes.c_float)
 
 KCAP = 4096
 
@@ -61,6 +62,22 @@ def lib():
                               ctypes.c_double, ctypes.c_double, ctypes.c_int64, _f64p, _f64p,
                               _u64p, _u8p, _i32p]
         L.orc_run.restype = ctypes.c_int
+        L.orc_run_ex.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                                 ctypes.c_double, ctypes.c_double, ctypes.c_int64, ctypes.c_int32,
+                                 ctypes.c_int32, _f64p, _f64p, _u64p, _u8p, _i32p]
+        L.orc_run_ex.restype = ctypes.c_int
+        _f32p = ctypes.POINTER(ctypes.c_float)
+        L.orc_evolve_modified.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_uint32, ctypes.c_uint64, _u8p, _i32p, _i32p, _f32p]
+        L.orc_evolve_modified.restype = ctypes.c_int
+        L.orc_weight_exp.argtypes = [ctypes.c_float, ctypes.c_int]
+        L.orc_weight_exp.restype = ctypes.c_uint64
+        L.orc_weights_modified.argtypes = [ctypes.c_double, ctypes.c_int64, _f32p, _u64p]
+        L.orc_weights_modified.restype = ctypes.c_int
+        L.orc_psi_term_modified.argtypes = [ctypes.c_double, ctypes.c_int64, _f32p]
+        L.orc_psi_term_modified.restype = ctypes.c_double
+        L.orc_ancestors_iid.argtypes = [ctypes.c_int64, _u64p, ctypes.c_uint32, ctypes.c_uint64, _i32p]
+        L.orc_ancestors_iid.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -83,10 +100,14 @@ def neg_ln_u(w):
 
 
 class Population:
-    """One population of clones, one byte per site (clone-major)."""
+    """One population of clones, one byte per site (clone-major).  modified: the
+    MODIFIED dynamics and weights (reading R13); iid: [iid] selection (R14)."""
 
-    def __init__(self, L, N, n_clones, seed):
+    def __init__(self, L, N, n_clones, seed, modified=False, iid=False):
         self.L, self.N, self.n_clones, self.seed = int(L), int(N), int(n_clones), int(seed)
+        self.modified, self.iid = bool(modified), bool(iid)
+        self.s = None
+        self.A = np.zeros(int(n_clones), dtype=np.float32)
         self.sites = np.zeros((self.n_clones, self.L), dtype=np.uint8)
         self.K = np.zeros(self.n_clones, dtype=np.int32)
         self.dK = np.zeros(self.n_clones, dtype=np.int32)
@@ -100,11 +121,17 @@ class Population:
         if rc != 0:
             raise ValueError("orc_init rejected its arguments (rc=%d)" % rc)
 
-    def evolve(self, dt):
-        """Dynamical stage of the next interval."""
+    def evolve(self, dt, s=None):
+        """Dynamical stage of the next interval (MODIFIED mode needs s)."""
         self.beta += 1
-        rc = lib().orc_evolve(self.L, self.n_clones, float(dt), self.beta, self.seed,
-                              _p(self.sites, _u8p), _p(self.K, _i32p), _p(self.dK, _i32p))
+        if self.modified:
+            self.s = float(s)
+            rc = lib().orc_evolve_modified(self.L, self.n_clones, float(dt), self.s, self.beta, self.seed,
+                                           _p(self.sites, _u8p), _p(self.K, _i32p), _p(self.dK, _i32p),
+                                           _p(self.A, _f32p))
+        else:
+            rc = lib().orc_evolve(self.L, self.n_clones, float(dt), self.beta, self.seed,
+                                  _p(self.sites, _u8p), _p(self.K, _i32p), _p(self.dK, _i32p))
         if rc != 0:
             raise ValueError("orc_evolve rc=%d" % rc)
         self.t_obs += float(dt)
@@ -112,10 +139,15 @@ class Population:
 
     def weights(self, s):
         w = np.zeros(self.n_clones, dtype=np.uint64)
-        rc = lib().orc_weights(float(s), self.n_clones, _p(self.dK, _i32p), _p(w, _u64p))
+        if self.modified:
+            rc = lib().orc_weights_modified(float(s), self.n_clones, _p(self.A, _f32p), _p(w, _u64p))
+        else:
+            rc = lib().orc_weights(float(s), self.n_clones, _p(self.dK, _i32p), _p(w, _u64p))
         return w, rc
 
     def psi_term(self, s):
+        if self.modified:
+            return lib().orc_psi_term_modified(float(s), self.n_clones, _p(self.A, _f32p))
         return lib().orc_psi_term(float(s), self.n_clones, _p(self.dK, _i32p))
 
     def resample(self, s):
@@ -124,7 +156,8 @@ class Population:
         self.psi_acc += term
         w, rc = self.weights(s)
         anc = np.zeros(self.n_clones, dtype=np.int32)
-        rc2 = lib().orc_ancestors(self.n_clones, _p(w, _u64p), self.beta, self.seed, _p(anc, _i32p))
+        sel = lib().orc_ancestors_iid if self.iid else lib().orc_ancestors
+        rc2 = sel(self.n_clones, _p(w, _u64p), self.beta, self.seed, _p(anc, _i32p))
         if rc2 != 0:
             raise ValueError("orc_ancestors rc=%d" % rc2)
         new_sites = np.zeros_like(self.sites)
@@ -190,7 +223,40 @@ def init_sites(L, N, n_clones, seed):
     return sites
 
 
-def run(L, N, n_clones, seed, s, dt, M, want_state=False):
+def weight_exp(x, F):
+    """floor(2^F exp(x)) for x <= 0 by the specified FP32 exponential (R13)."""
+    return int(lib().orc_weight_exp(ctypes.c_float(float(x)), int(F)))
+
+
+def ancestors_iid(w, beta, seed):
+    w = np.ascontiguousarray(np.asarray(w, dtype=np.uint64))
+    anc = np.zeros(w.size, dtype=np.int32)
+    rc = lib().orc_ancestors_iid(w.size, _p(w, _u64p), int(beta), int(seed), _p(anc, _i32p))
+    if rc != 0:
+        raise ValueError("orc_ancestors_iid rc=%d" % rc)
+    return anc
+
+
+def evolve_sites_modified(L, sites, dt, s, beta, seed):
+    """MODIFIED dynamics of given configurations; returns (sites, dK, A)."""
+    sites = np.ascontiguousarray(np.array(sites, dtype=np.uint8))
+    n = sites.shape[0]
+    K = np.zeros(n, dtype=np.int32)
+    dK = np.zeros(n, dtype=np.int32)
+    A = np.zeros(n, dtype=np.float32)
+    rc = lib().orc_evolve_modified(int(L), n, float(dt), float(s), int(beta), int(seed), _p(sites, _u8p),
+                                   _p(K, _i32p), _p(dK, _i32p), _p(A, _f32p))
+    if rc != 0:
+        raise ValueError("orc_evolve_modified rc=%d" % rc)
+    return sites, dK, A
+
+
+def psi_term_modified(s, A):
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.float32))
+    return float(lib().orc_psi_term_modified(float(s), A.size, _p(A, _f32p)))
+
+
+def run(L, N, n_clones, seed, s, dt, M, want_state=False, modified=False, iid=False):
     """Full run; returns dict(psi, k_hat, events[, sites, K])."""
     psi = ctypes.c_double(0.0)
     kh = ctypes.c_double(0.0)
@@ -201,8 +267,9 @@ def run(L, N, n_clones, seed, s, dt, M, want_state=False):
         sites = np.zeros((int(n_clones), int(L)), dtype=np.uint8)
         K = np.zeros(int(n_clones), dtype=np.int32)
         sp, kp = _p(sites, _u8p), _p(K, _i32p)
-    rc = lib().orc_run(int(L), int(N), int(n_clones), int(seed), float(s), float(dt), int(M),
-                       ctypes.byref(psi), ctypes.byref(kh), ctypes.byref(ev), sp, kp)
+    rc = lib().orc_run_ex(int(L), int(N), int(n_clones), int(seed), float(s), float(dt), int(M),
+                          int(bool(modified)), int(bool(iid)),
+                          ctypes.byref(psi), ctypes.byref(kh), ctypes.byref(ev), sp, kp)
     out = dict(psi=psi.value, k_hat=kh.value, events=int(ev.value), rc=rc)
     if want_state:
         out.update(sites=sites, K=K)

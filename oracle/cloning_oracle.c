@@ -49,6 +49,16 @@
  *      word; alpha_j = floor((2^33 j + 2U + 1) T / (2^33 N_c)) for j = 0..N_c-1;
  *      the ancestor is the 0-based k with S_k <= alpha_j < S_{k+1}, S the
  *      exclusive prefix sums of the weights (the printed index is off by one).
+ *   R13 MODIFIED dynamics (Sec. 3.2, eq. def-ups-ssep): every rate times e^-s, so
+ *      tau = E * float(e^s / r); the weight exponent A = integral of the unmodified
+ *      escape rate r over the interval, accumulated in FP32 as A <- fma(r, tau, A)
+ *      per hop and A <- fma(r, dt - t, A) for the last segment.  Upsilon =
+ *      exp(-c A) with c = float(1 - e^-s).  A_ref = min A (s >= 0) or max A (s < 0);
+ *      w = floor(2^F exp_spec(-c (A - A_ref))) with exp_spec the FP32 exponential
+ *      of orc_weight_exp() below; the psi term is -c A_ref + log1p((T - N_c 2^F)/(N_c 2^F))
+ *      from the exact integer total T of those weights.
+ *   R14 [iid] selection (Sec. 4.1): alpha_j = floor(U64_j T / 2^64), U64_j = w1 2^32 + w0
+ *      of draw (j, beta, 0, 4); the ancestor is the k with S_k <= alpha_j < S_{k+1}.
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared (see oracle/build.py).
  * Contraction must stay off: every float operation below is a separately rounded
@@ -62,6 +72,7 @@
 #define ORC_TAG_INIT 1u
 #define ORC_TAG_EVOLVE 2u
 #define ORC_TAG_RESAMPLE 3u
+#define ORC_TAG_IID 4u
 #define ORC_KCAP 4096
 
 #define ORC_OK 0
@@ -363,6 +374,162 @@ void orc_gather(int32_t L, int64_t n_clones, const int32_t* anc,
 }
 
 /* ---------------------------------------------------------------------------
+ * Reading R13: the MODIFIED dynamics of Sec. 3.2 for one interval.  Same streams
+ * and steps as orc_evolve; the waiting time uses the rate e^-s r, and A (the
+ * integral of the unmodified escape rate over the interval) is returned per clone.
+ * ------------------------------------------------------------------------- */
+int orc_evolve_modified(int32_t L, int64_t n_clones, double dt, double s, uint32_t beta,
+                        uint64_t seed, uint8_t* sites, int32_t* K, int32_t* dK, float* A) {
+  if (L < 3 || n_clones < 1 || !(dt > 0.0)) return ORC_ERR_ARG;
+  const float dt_f = (float)dt;
+  const double es = exp(s);
+  for (int64_t j = 0; j < n_clones; ++j) {
+    uint8_t* n = sites + j * (int64_t)L;
+    float t = 0.0f, a = 0.0f;
+    uint32_t e = 0;
+    int32_t hops = 0;
+    for (;;) {
+      int r = count_active(n, L);
+      if (r == 0) break;
+      uint32_t w[4];
+      philox_at(e / 2u, beta, (uint32_t)j, ORC_TAG_EVOLVE, seed, w);
+      uint32_t wa = (e % 2u == 0u) ? w[0] : w[2];
+      uint32_t wb = (e % 2u == 0u) ? w[1] : w[3];
+      ++e;
+      float E = orc_neg_ln_u(wa);
+      float inv_r = (float)(es / (double)r);
+      float tau = E * inv_r;
+      float t_new = t + tau;
+      if (t_new >= dt_f) {
+        a = fmaf((float)r, dt_f - t, a);
+        break;
+      }
+      a = fmaf((float)r, tau, a);
+      t = t_new;
+      uint64_t k = ((uint64_t)wb * (uint64_t)r) >> 32;
+      int b = -1;
+      uint64_t seen = 0;
+      for (int i = 0; i < L; ++i) {
+        if (n[i] != n[(i + 1) % L]) {
+          if (seen == k) { b = i; break; }
+          ++seen;
+        }
+      }
+      int b1 = (b + 1) % L;
+      uint8_t tmp = n[b];
+      n[b] = n[b1];
+      n[b1] = tmp;
+      ++hops;
+    }
+    dK[j] = hops;
+    K[j] += hops;
+    A[j] = a;
+  }
+  return ORC_OK;
+}
+
+/* 2^(i/64) for i = 0..63, rounded once from FP64 (reading R13). */
+static float orc_tab_exp2[64];
+static int orc_exp_ready = 0;
+static void orc_exp_table(void) {
+  for (int i = 0; i < 64; ++i) orc_tab_exp2[i] = (float)exp2((double)i / 64.0);
+  orc_exp_ready = 1;
+}
+
+static const float ORC_64_LOG2E = 0x1.715476p+6f;   /* 64 / ln 2 */
+static const float ORC_LN2_64_HI = 0x1.62p-7f;      /* ln2/64, 9-bit head */
+static const float ORC_LN2_64_LO = 0x1.c85fe0p-16f; /* ln2/64 - head */
+static const float ORC_SIXTH = 0x1.555556p-3f;      /* 1/6 */
+
+/* floor(2^F exp(x)) for x <= 0 (reading R13).  x = (k/64) ln 2 + r with
+ * k = floor(64 x / ln 2) and r = x - k ln2/64 formed exactly in two fma steps
+ * (k ln2/64 split into a 9-bit head, exact for |k| < 2^15, and a float tail);
+ * exp(x) = 2^n 2^(i/64) e^r with k = 64 n + i, 2^(i/64) from the table and
+ * e^r ~ 1 + r (1 + r (1/2 + r/6)) for 0 <= r < ln2/64 (first dropped term below
+ * 6e-10).  y = 2^(i/64) e^r is a float in [1, 2.02); the weight is its 24-bit
+ * mantissa shifted by (exponent of y) + n + F - 23. */
+uint64_t orc_weight_exp(float x, int F) {
+  if (!orc_exp_ready) orc_exp_table();
+  if (!(x >= -87.0f)) return 0;
+  int k = (int)floorf(x * ORC_64_LOG2E);
+  float r = fmaf(-(float)k, ORC_LN2_64_HI, x);
+  r = fmaf(-(float)k, ORC_LN2_64_LO, r);
+  float q = fmaf(r, ORC_SIXTH, 0.5f);
+  q = fmaf(q, r, 1.0f);
+  q = fmaf(q, r, 1.0f);
+  int i = ((k % 64) + 64) % 64;
+  int n = (k - i) / 64;
+  float y = orc_tab_exp2[i] * q;
+  uint32_t bits;
+  memcpy(&bits, &y, sizeof bits);
+  int ey = (int)((bits >> 23) & 0xffu) - 127;
+  uint64_t mant = (uint64_t)((bits & 0x007fffffu) | 0x00800000u);
+  int sa = ey + n + F - 23;
+  if (sa >= 0) return mant << sa;
+  if (sa <= -64) return 0;
+  return mant >> (-sa);
+}
+
+float orc_a_ref(double s, int64_t n_clones, const float* A) {
+  float ref = A[0];
+  for (int64_t j = 1; j < n_clones; ++j) {
+    if (s >= 0.0) { if (A[j] < ref) ref = A[j]; }
+    else          { if (A[j] > ref) ref = A[j]; }
+  }
+  return ref;
+}
+
+int orc_weights_modified(double s, int64_t n_clones, const float* A, uint64_t* w) {
+  if (n_clones < 1) return ORC_ERR_ARG;
+  const int F = orc_weight_scale(n_clones);
+  const float c = (float)(-expm1(-s));
+  const float ref = orc_a_ref(s, n_clones, A);
+  for (int64_t j = 0; j < n_clones; ++j) {
+    float x = (-c) * (A[j] - ref);
+    w[j] = orc_weight_exp(x, F);
+  }
+  return ORC_OK;
+}
+
+/* psi term of reading R13 from the exact total T of the quantised weights. */
+double orc_psi_term_modified(double s, int64_t n_clones, const float* A) {
+  const int F = orc_weight_scale(n_clones);
+  const float c = (float)(-expm1(-s));
+  const float ref = orc_a_ref(s, n_clones, A);
+  uint64_t T = 0;
+  for (int64_t j = 0; j < n_clones; ++j) T += orc_weight_exp((-c) * (A[j] - ref), F);
+  const double base = ldexp((double)n_clones, F);
+  const int64_t D = (int64_t)T - (int64_t)(((uint64_t)n_clones) << F);
+  return -(double)c * (double)ref + log1p((double)D / base);
+}
+
+/* Reading R14: [iid] clone selection. */
+int orc_ancestors_iid(int64_t n_clones, const uint64_t* w, uint32_t beta, uint64_t seed,
+                      int32_t* anc) {
+  if (n_clones < 1) return ORC_ERR_ARG;
+  uint64_t* S = (uint64_t*)malloc((size_t)(n_clones + 1) * sizeof(uint64_t));
+  if (!S) return ORC_ERR_ARG;
+  S[0] = 0;
+  for (int64_t k = 0; k < n_clones; ++k) S[k + 1] = S[k] + w[k];
+  const uint64_t T = S[n_clones];
+  if (T == 0) { free(S); return ORC_ERR_ARG; }
+  for (int64_t j = 0; j < n_clones; ++j) {
+    uint32_t r[4];
+    philox_at((uint32_t)j, beta, 0u, ORC_TAG_IID, seed, r);
+    uint64_t u = ((uint64_t)r[1] << 32) | r[0];
+    uint64_t alpha = mul_hi_64(u, T);
+    int64_t lo = 0, hi = n_clones - 1;
+    while (lo < hi) {
+      int64_t mid = lo + (hi - lo + 1) / 2;
+      if (S[mid] <= alpha) lo = mid; else hi = mid - 1;
+    }
+    anc[j] = (int32_t)lo;
+  }
+  free(S);
+  return ORC_OK;
+}
+
+/* ---------------------------------------------------------------------------
  * A full run of the cloning algorithm (Sec. 2.3): init, then M intervals of
  * (dynamical stage, cloning stage).  psi_hat = (1/t_obs) sum_beta term_beta
  * (eq. psihat, all M intervals); k_hat = (1/(N_c L t_obs)) sum_j K_j over the
@@ -370,9 +537,9 @@ void orc_gather(int32_t L, int64_t n_clones, const int32_t* anc,
  * events (optional) receives the number of hops executed by all clones.
  * If sites_out / K_out are given, the final population is written there.
  * ------------------------------------------------------------------------- */
-int orc_run(int32_t L, int32_t N, int64_t n_clones, uint64_t seed, double s, double dt,
-            int64_t M, double* psi_hat, double* k_hat, uint64_t* events,
-            uint8_t* sites_out, int32_t* K_out) {
+int orc_run_ex(int32_t L, int32_t N, int64_t n_clones, uint64_t seed, double s, double dt,
+               int64_t M, int32_t modified, int32_t iid, double* psi_hat, double* k_hat,
+               uint64_t* events, uint8_t* sites_out, int32_t* K_out) {
   if (L < 3 || N < 0 || N > L || n_clones < 1 || !(dt > 0.0) || M < 1) return ORC_ERR_ARG;
   size_t nbytes = (size_t)n_clones * (size_t)L;
   uint8_t* a = (uint8_t*)malloc(nbytes);
@@ -382,18 +549,28 @@ int orc_run(int32_t L, int32_t N, int64_t n_clones, uint64_t seed, double s, dou
   int32_t* dK = (int32_t*)malloc((size_t)n_clones * sizeof(int32_t));
   uint64_t* w = (uint64_t*)malloc((size_t)n_clones * sizeof(uint64_t));
   int32_t* anc = (int32_t*)malloc((size_t)n_clones * sizeof(int32_t));
+  float* A = (float*)malloc((size_t)n_clones * sizeof(float));
   int status = ORC_OK;
-  if (!a || !b || !Ka || !Kb || !dK || !w || !anc) { status = ORC_ERR_ARG; goto done; }
+  if (!a || !b || !Ka || !Kb || !dK || !w || !anc || !A) { status = ORC_ERR_ARG; goto done; }
   orc_init(L, N, n_clones, seed, a, Ka);
   double acc = 0.0;
   uint64_t ev = 0;
   for (int64_t beta = 1; beta <= M; ++beta) {
-    orc_evolve(L, n_clones, dt, (uint32_t)beta, seed, a, Ka, dK);
+    int st;
+    if (modified) {
+      orc_evolve_modified(L, n_clones, dt, s, (uint32_t)beta, seed, a, Ka, dK, A);
+      acc += orc_psi_term_modified(s, n_clones, A);
+      st = orc_weights_modified(s, n_clones, A, w);
+    } else {
+      orc_evolve(L, n_clones, dt, (uint32_t)beta, seed, a, Ka, dK);
+      acc += orc_psi_term(s, n_clones, dK);
+      st = orc_weights(s, n_clones, dK, w);
+    }
     for (int64_t j = 0; j < n_clones; ++j) ev += (uint64_t)dK[j];
-    acc += orc_psi_term(s, n_clones, dK);
-    int st = orc_weights(s, n_clones, dK, w);
     if (st != ORC_OK) status = st;
-    if (orc_ancestors(n_clones, w, (uint32_t)beta, seed, anc) != ORC_OK) {
+    st = iid ? orc_ancestors_iid(n_clones, w, (uint32_t)beta, seed, anc)
+             : orc_ancestors(n_clones, w, (uint32_t)beta, seed, anc);
+    if (st != ORC_OK) {
       status = ORC_ERR_RANGE;
       goto done;
     }
@@ -412,6 +589,12 @@ int orc_run(int32_t L, int32_t N, int64_t n_clones, uint64_t seed, double s, dou
     if (K_out) memcpy(K_out, Ka, (size_t)n_clones * sizeof(int32_t));
   }
 done:
-  free(a); free(b); free(Ka); free(Kb); free(dK); free(w); free(anc);
+  free(a); free(b); free(Ka); free(Kb); free(dK); free(w); free(anc); free(A);
   return status;
+}
+
+int orc_run(int32_t L, int32_t N, int64_t n_clones, uint64_t seed, double s, double dt,
+            int64_t M, double* psi_hat, double* k_hat, uint64_t* events,
+            uint8_t* sites_out, int32_t* K_out) {
+  return orc_run_ex(L, N, n_clones, seed, s, dt, M, 0, 0, psi_hat, k_hat, events, sites_out, K_out);
 }
