@@ -30,7 +30,8 @@
  *     population's 64-bit seed, counter (c0, c1, c2, c3) =
  *       initial state   (site t, 0,        clone slot j, 1)
  *       dynamical stage (draw q, interval, clone slot j, 2)  step e uses draw e/2
- *       cloning stage   (0,      interval, 0,            3)
+ *       cloning stage   (0,      interval, 0,            3)   [eq]
+ *                       (new clone j, interval, 0,      4)   [iid]
  *     Intervals are numbered from 1.  Results are reproducible bit for bit for a
  *     given batch, independent of the launch configuration.
  */
@@ -54,11 +55,14 @@ extern "C" {
 
 /* weight modes (eq. upsdef) */
 #define POP_PLAIN 0    /* unmodified SSEP rates, Upsilon = exp(-s dK) (eq. upsbdef, U = 0) */
-#define POP_MODIFIED 1 /* rates times e^-s, eq. (def-ups-ssep); not available yet */
+#define POP_MODIFIED 1 /* every rate times e^-s, Upsilon = exp(-(1-e^-s) int r dt)
+                          (Sec. 3.2, eq. def-ups-ssep); the integral is accumulated in
+                          FP32 and the weights use a specified FP32 exponential */
 
 /* clone selection (Sec. 4.1) */
 #define POP_EQ 0  /* equally spaced alpha_j, eq. (alpha-Ups) */
-#define POP_IID 1 /* independent alpha_j; not available yet */
+#define POP_IID 1 /* independent uniform alpha_j = floor(U64 T / 2^64), U64 from Philox
+                     counter (new clone j, interval, 0, 4) */
 
 #define POP_KCAP 4096     /* size of the fixed-point weight table */
 #define POP_MAX_L 4096    /* largest ring; rings above 128 sites run one clone per warp */
@@ -71,8 +75,8 @@ typedef struct pop_params {
   int32_t N;           /* particles, 0 <= N <= L */
   int64_t n_clones;    /* N_c, 1 <= N_c <= POP_MAX_CLONES */
   uint64_t seed;       /* Philox key of this population's streams */
-  int32_t weight_mode; /* POP_PLAIN */
-  int32_t selection;   /* POP_EQ */
+  int32_t weight_mode; /* POP_PLAIN or POP_MODIFIED */
+  int32_t selection;   /* POP_EQ or POP_IID */
 } pop_params;
 
 typedef struct pop_batch pop_t;

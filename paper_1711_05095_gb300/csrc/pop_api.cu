@@ -29,7 +29,7 @@ constexpr int kGraphIntervals = 32;
 struct Layout {
   int32_t P = 0, W = 0, ntiles = 0, nunits = 0;
   int64_t nslots = 0;
-  size_t o_pops, o_st, o_tile_pop, o_wtab, o_qtab, o_qm1tab, o_inv, o_logtab, o_hist, o_tile_sum, o_beta,
+  size_t o_pops, o_st, o_tile_pop, o_wtab, o_qtab, o_qm1tab, o_inv, o_logtab, o_exp2, o_A, o_S, o_hist, o_tile_sum, o_beta,
       o_ksum, o_X, o_Y, o_KX, o_KY, o_dK, o_anc, total;
 };
 
@@ -42,8 +42,8 @@ bool valid_params(const pop_params* params, int32_t n_pops) {
     if (q.L < 3 || q.L > POP_MAX_L) return false;
     if (q.N < 0 || q.N > q.L) return false;
     if (q.n_clones < 1 || q.n_clones > POP_MAX_CLONES) return false;
-    if (q.weight_mode != POP_PLAIN) return false;
-    if (q.selection != POP_EQ) return false;
+    if (q.weight_mode != POP_PLAIN && q.weight_mode != POP_MODIFIED) return false;
+    if (q.selection != POP_EQ && q.selection != POP_IID) return false;
   }
   return true;
 }
@@ -74,6 +74,7 @@ bool make_layout(const pop_params* params, int32_t n_pops, Layout* lay) {
   l.o_qm1tab = take(P * kKcap * sizeof(double));
   l.o_inv = take(P * kInvStride * sizeof(float));
   l.o_logtab = take(64 * sizeof(float2));
+  l.o_exp2 = take(64 * sizeof(float));
   l.o_hist = take(P * kKcap * sizeof(unsigned int));
   l.o_tile_sum = take(nt * sizeof(unsigned long long));
   l.o_beta = take(sizeof(unsigned int));
@@ -84,6 +85,8 @@ bool make_layout(const pop_params* params, int32_t n_pops, Layout* lay) {
   l.o_KY = take(ns * sizeof(int32_t));
   l.o_dK = take(ns * sizeof(int32_t));
   l.o_anc = take(ns * sizeof(int32_t));
+  l.o_A = take(ns * sizeof(float));
+  l.o_S = take(ns * sizeof(unsigned long long));
   l.total = o;
   *lay = l;
   return true;
@@ -110,6 +113,7 @@ struct pop_batch {
   float graph_dt = 0.0f;
   unsigned char* ws = nullptr;
   Batch B{};
+  bool any_mod = false;
   int evolve_grid = 0;
   size_t evolve_smem = 0;
   bool s_fixed = false;
@@ -157,6 +161,19 @@ int fix_biases(pop_t* h, const double* s) {
     h->desc[p].s = s[p];
     h->desc[p].abs_s = a;
     h->desc[p].s_neg = s[p] < 0.0 ? 1 : 0;
+    h->desc[p].c_f = (float)(-std::expm1(-s[p]));
+  }
+  // MODIFIED dynamics: every rate times e^-s, so the waiting-time factor is e^s / r
+  std::vector<float> inv_mod;
+  for (int32_t p = 0; p < h->lay.P; ++p) {
+    if (!h->desc[p].modified) continue;
+    inv_mod.assign(kInvStride, 0.0f);
+    const double es = std::exp(s[p]);
+    for (int r = 1; r <= h->params[p].L; ++r) inv_mod[r] = (float)(es / (double)r);
+    POP_CUDA(cudaMemcpyAsync(h->ws + h->lay.o_inv + (size_t)p * kInvStride * sizeof(float),
+                             inv_mod.data(), kInvStride * sizeof(float), cudaMemcpyHostToDevice,
+                             h->stream));
+    POP_CUDA(cudaStreamSynchronize(h->stream));
   }
   POP_CUDA(cudaMemcpyAsync(h->ws + h->lay.o_wtab, wtab.data(), n * sizeof(unsigned long long),
                            cudaMemcpyHostToDevice, h->stream));
@@ -176,9 +193,16 @@ bool valid_dt(double dt) { return std::isfinite(dt) && dt > 0.0 && dt < 1e30; }
 
 int launch_evolve(pop_t* h, cudaStream_t st, float dt_f) {
   const unsigned grid = (unsigned)h->evolve_grid;
-  if (h->lay.W == 1) k_evolve<1><<<grid, kThreads, h->evolve_smem, st>>>(h->B, dt_f);
-  else if (h->lay.W == 2) k_evolve<2><<<grid, kThreads, h->evolve_smem, st>>>(h->B, dt_f);
-  else k_evolve_wide<<<grid, kThreads, 0, st>>>(h->B, dt_f);
+  const size_t sm = h->evolve_smem;
+  if (h->any_mod) {
+    if (h->lay.W == 1) k_evolve<1, true><<<grid, kThreads, sm, st>>>(h->B, dt_f);
+    else if (h->lay.W == 2) k_evolve<2, true><<<grid, kThreads, sm, st>>>(h->B, dt_f);
+    else k_evolve_wide<true><<<grid, kThreads, 0, st>>>(h->B, dt_f);
+  } else {
+    if (h->lay.W == 1) k_evolve<1, false><<<grid, kThreads, sm, st>>>(h->B, dt_f);
+    else if (h->lay.W == 2) k_evolve<2, false><<<grid, kThreads, sm, st>>>(h->B, dt_f);
+    else k_evolve_wide<false><<<grid, kThreads, 0, st>>>(h->B, dt_f);
+  }
   return cuda_status(cudaGetLastError());
 }
 
@@ -188,18 +212,23 @@ int launch_resample(pop_t* h, cudaStream_t st) {
   if (h->lay.W == 1) k_gather<1><<<grid, kThreads, 0, st>>>(h->B);
   else if (h->lay.W == 2) k_gather<2><<<grid, kThreads, 0, st>>>(h->B);
   else k_gather<0><<<grid, kThreads, 0, st>>>(h->B);
+  if (h->B.any_iid) {
+    if (h->lay.W == 1) k_select_iid<1><<<grid, kThreads, 0, st>>>(h->B);
+    else if (h->lay.W == 2) k_select_iid<2><<<grid, kThreads, 0, st>>>(h->B);
+    else k_select_iid<0><<<grid, kThreads, 0, st>>>(h->B);
+  }
   return cuda_status(cudaGetLastError());
 }
 
 // Persistent evolve grid: as many blocks as fit on the device at once, each
 // owning an equal share of the 256-slot units.
-template <int W>
+template <int W, bool MOD>
 int size_evolve_grid(pop_t* h) {
   const size_t smem = sizeof(EvolveSmem<W>);
-  POP_CUDA(cudaFuncSetAttribute(k_evolve<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  POP_CUDA(cudaFuncSetAttribute(k_evolve<W, MOD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
   int per_sm = 0, sms = 0;
-  POP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_evolve<W>, kThreads, smem));
+  POP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_evolve<W, MOD>, kThreads, smem));
   POP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
   if (per_sm < 1) per_sm = 1;
   const long long want = (long long)per_sm * sms;
@@ -211,9 +240,10 @@ int size_evolve_grid(pop_t* h) {
 }
 
 // Rings longer than 128 sites: one warp per clone, a grid-stride loop over slots.
+template <bool MOD>
 int size_evolve_grid_wide(pop_t* h) {
   int per_sm = 0, sms = 0;
-  POP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_evolve_wide, kThreads, 0));
+  POP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_evolve_wide<MOD>, kThreads, 0));
   POP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
   if (per_sm < 1) per_sm = 1;
   const long long want = (long long)per_sm * sms;
@@ -286,7 +316,13 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
     d.s = 0.0;
     d.abs_s = 0.0;
     d.s_neg = 0;
+    d.modified = params[p].weight_mode == POP_MODIFIED ? 1 : 0;
+    d.iid = params[p].selection == POP_IID ? 1 : 0;
+    d.F = 61 - ceil_log2(params[p].n_clones);
+    d.c_f = 0.0f;
     d.pad = 0;
+    h->any_mod = h->any_mod || d.modified;
+    h->B.any_iid = h->B.any_iid || d.iid;
     for (int32_t t = 0; t < d.ntiles; ++t) tile_pop[(size_t)tile + t] = p;
     tile += d.ntiles;
   }
@@ -305,7 +341,12 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
     std::memset(&q, 0, sizeof q);
     q.dk_min = INT_MAX;
     q.dk_max = INT_MIN;
+    q.a_min = INT_MAX;
+    q.a_max = INT_MIN;
   }
+  // MODIFIED weight exponential: 2^(i/64)
+  std::vector<float> exp2tab(64);
+  for (int i = 0; i < 64; ++i) exp2tab[i] = (float)std::exp2((double)i / 64.0);
   const unsigned int beta0 = 1u;
 
   unsigned char* ws = h->ws;
@@ -320,6 +361,8 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
                       cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
       cudaMemcpyAsync(ws + lay.o_logtab, logtab.data(), logtab.size() * sizeof(float2),
                       cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(ws + lay.o_exp2, exp2tab.data(), exp2tab.size() * sizeof(float),
+                      cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
       cudaMemcpyAsync(ws + lay.o_beta, &beta0, sizeof beta0, cudaMemcpyHostToDevice,
                       h->stream) != cudaSuccess)
     return fail(POP_ERR_CUDA);
@@ -333,6 +376,9 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
   B.qm1tab = (const double*)(ws + lay.o_qm1tab);
   B.inv_rate = (const float*)(ws + lay.o_inv);
   B.logtab = (const float2*)(ws + lay.o_logtab);
+  B.exp2tab = (const float*)(ws + lay.o_exp2);
+  B.A = (float*)(ws + lay.o_A);
+  B.S = (unsigned long long*)(ws + lay.o_S);
   B.hist = (unsigned int*)(ws + lay.o_hist);
   B.tile_sum = (unsigned long long*)(ws + lay.o_tile_sum);
   B.beta = (unsigned int*)(ws + lay.o_beta);
@@ -347,8 +393,10 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
   B.nunits = lay.nunits;
   B.nslots = lay.nslots;
   B.W = lay.W;
-  const int grc = lay.W == 1 ? size_evolve_grid<1>(h)
-                  : (lay.W == 2 ? size_evolve_grid<2>(h) : size_evolve_grid_wide(h));
+  const bool mod = h->any_mod;
+  const int grc = lay.W == 1 ? (mod ? size_evolve_grid<1, true>(h) : size_evolve_grid<1, false>(h))
+                  : lay.W == 2 ? (mod ? size_evolve_grid<2, true>(h) : size_evolve_grid<2, false>(h))
+                               : (mod ? size_evolve_grid_wide<true>(h) : size_evolve_grid_wide<false>(h));
   if (grc != POP_OK) return fail(POP_ERR_CUDA);
 
   const unsigned grid = (unsigned)(lay.nslots / kThreads);

@@ -29,6 +29,7 @@ namespace popgpu {
 constexpr uint32_t kTagInit = 1u;
 constexpr uint32_t kTagEvolve = 2u;
 constexpr uint32_t kTagResample = 3u;
+constexpr uint32_t kTagIid = 4u;
 
 constexpr int kThreads = 256;             // threads per block of every kernel
 constexpr int kWarps = kThreads / 32;
@@ -55,6 +56,10 @@ struct PopDesc {
   uint64_t seed;     // Philox key
   int32_t first_tile, ntiles;
   int32_t s_neg;     // s < 0: the reference activity is the maximum
+  int32_t modified;  // MODIFIED dynamics and weights (Sec. 3.2, eq. def-ups-ssep)
+  int32_t iid;       // [iid] selection (Sec. 4.1)
+  int32_t F;         // fixed-point weight scale, 61 - ceil(log2 N_c)
+  float c_f;         // float(1 - e^-s), the MODIFIED weight coefficient
   int32_t pad;
   double s;          // bias
   double abs_s;
@@ -68,7 +73,11 @@ struct PopState {
   double psi_acc;              // sum of psi terms (eq. psihat numerator)
   unsigned long long events;   // executed hops since init
   int32_t err;                 // sticky kernel-side error
+  int32_t a_min, a_max;        // MODIFIED: range of the rate integral A (float bits, A >= 0)
+  float a_ref;                 // MODIFIED: reference A of this interval (k_weights)
+  uint32_t beta;               // interval being resampled (k_weights)
   int32_t pad;
+  unsigned long long T;        // total weight of this interval ([iid] selection)
 };
 
 struct Batch {
@@ -80,6 +89,9 @@ struct Batch {
   const double* qm1tab;                 // [P][kKcap] expm1(-|s| k)
   const float* inv_rate;                // [P][kInvStride] float(1/r)
   const float2* logtab;                 // [64] (1/c_i, ln c_i) of the waiting-time log
+  const float* exp2tab;                 // [64] 2^(i/64) of the MODIFIED weight exponential
+  float* A;                             // MODIFIED: rate integral of the last interval
+  unsigned long long* S;                // [iid]: exclusive prefix sums of the weights
   unsigned int* hist;                   // [P][kKcap] activity histogram (zero between intervals)
   unsigned long long* tile_sum;         // [ntiles] weight sum of each tile
   unsigned int* beta;                   // interval being evolved (1-based)
@@ -95,7 +107,7 @@ struct Batch {
   int64_t nslots;
   int32_t W;                            // lattice words per clone
   int32_t unit_q, unit_r;               // k_evolve: nunits = unit_q * grid + unit_r
-  int32_t pad;
+  int32_t any_iid;                      // some population selects [iid]: k_select_iid runs last
 };
 
 // ---------------------------------------------------------------------------
@@ -369,6 +381,52 @@ __device__ __forceinline__ void j_lo_run(unsigned long long S0, const unsigned l
     }
     out[i + 1] = (uint32_t)j;
   }
+}
+
+// ---------------------------------------------------------------------------
+// MODIFIED weights: floor(2^F exp(x)) for x <= 0 in FP32 with a fixed sequence of
+// rounded operations.  x = (k/64) ln 2 + r, k = floor(64 x / ln 2), r formed in
+// two fma steps with ln2/64 split into a 9-bit head (exact products for |k| < 2^15)
+// and a float tail; exp(x) = 2^n 2^(i/64) e^r (k = 64 n + i), 2^(i/64) from tab2,
+// e^r ~ 1 + r (1 + r (1/2 + r/6)).  The weight is the 24-bit mantissa of
+// y = 2^(i/64) e^r shifted by (exponent of y) + n + F - 23.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long weight_exp(float x, int F, const float* tab2) {
+  if (!(x >= -87.0f)) return 0ull;
+  const int k = (int)floorf(__fmul_rn(x, 0x1.715476p+6f));
+  const float kf = (float)k;
+  float r = __fmaf_rn(-kf, 0x1.62p-7f, x);
+  r = __fmaf_rn(-kf, 0x1.c85fe0p-16f, r);
+  float q = __fmaf_rn(r, 0x1.555556p-3f, 0.5f);
+  q = __fmaf_rn(q, r, 1.0f);
+  q = __fmaf_rn(q, r, 1.0f);
+  const int i = k & 63, n = k >> 6;
+  const float y = __fmul_rn(tab2[i], q);
+  const uint32_t bits = __float_as_uint(y);
+  const int ey = (int)((bits >> 23) & 0xffu) - 127;
+  const unsigned long long mant = (unsigned long long)((bits & 0x007fffffu) | 0x00800000u);
+  const int sa = ey + n + F - 23;
+  if (sa >= 0) return mant << sa;
+  if (sa <= -64) return 0ull;
+  return mant >> (-sa);
+}
+
+// The weight of one clone: plain (table of 2^F exp(-|s| k), k = |dK - k_ref|) or
+// MODIFIED (weight_exp of -c (A - A_ref)).  Returns false on a plain range error.
+__device__ __forceinline__ bool clone_weight(const PopDesc& d, int dk, int kref, float a,
+                                            float a_ref, const unsigned long long* wt,
+                                            const float* tab2, unsigned long long& w,
+                                            unsigned int& k_out) {
+  if (d.modified) {
+    w = weight_exp(__fmul_rn(-d.c_f, __fsub_rn(a, a_ref)), d.F, tab2);
+    k_out = 0u;
+    return true;
+  }
+  const unsigned int k = abs_diff(dk, kref);
+  k_out = k;
+  if (k >= (unsigned int)kKcap) { w = 0ull; return false; }
+  w = __ldg(wt + k);
+  return true;
 }
 
 }  // namespace popgpu

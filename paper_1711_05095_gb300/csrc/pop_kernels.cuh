@@ -67,12 +67,14 @@ template <int W>
 struct EvolveSmem {
   unsigned long long x[kChunk][W];  // lattices (in, then out)
   int32_t hops[kChunk];             // activity of the interval
+  float a[kChunk];                  // MODIFIED: integral of the escape rate over the interval
   float inv[kChunkUnits][kMaxL + 1];
   float2 logtab[64];
   uint2 u_key[kChunkUnits];         // Philox key of the unit's population
   int32_t u_j0[kChunkUnits];        // population-local index of the unit's first slot
   int32_t u_pop[kChunkUnits], u_L[kChunkUnits], u_valid[kChunkUnits];
   int32_t u_min[kChunkUnits], u_max[kChunkUnits];
+  int32_t u_amin[kChunkUnits], u_amax[kChunkUnits];
   unsigned int u_ev[kChunkUnits];
   int take;                         // next unclaimed clone of the chunk
 };
@@ -83,16 +85,24 @@ struct EvolveSmem {
 // residual waiting time is dropped, as the exponential law's memorylessness
 // allows); otherwise hop across the floor(wb r / 2^32)-th active bond.
 // Returns true if the clone hopped (and is still running).
-template <int W>
-__device__ __forceinline__ bool bkl_step(unsigned long long (&x)[W], float& t, int L,
+// MODIFIED dynamics (Sec. 3.2): inv holds float(e^s / r) and the integral of the
+// unmodified escape rate is accumulated, A <- fma(r, tau, A) per hop and
+// A <- fma(r, dt - t, A) for the last segment.
+template <int W, bool MOD>
+__device__ __forceinline__ bool bkl_step(unsigned long long (&x)[W], float& t, float& acc, int L,
                                          const float* inv, const float2* tab, uint32_t wa,
                                          uint32_t wb, float dt_f) {
   unsigned long long a[W];
   active_bonds<W>(x, L, a);
   const int r = popc_lat<W>(a);
   if (r == 0) return false;
-  const float t_new = __fadd_rn(t, __fmul_rn(neg_ln_u(wa, tab), inv[r]));
-  if (t_new >= dt_f) return false;
+  const float tau = __fmul_rn(neg_ln_u(wa, tab), inv[r]);
+  const float t_new = __fadd_rn(t, tau);
+  if (t_new >= dt_f) {
+    if (MOD) acc = __fmaf_rn((float)r, __fsub_rn(dt_f, t), acc);
+    return false;
+  }
+  if (MOD) acc = __fmaf_rn((float)r, tau, acc);
   t = t_new;
   hop<W>(x, kth_bond<W>(a, __umulhi(wb, (uint32_t)r)), L);
   return true;
@@ -109,7 +119,7 @@ __device__ __forceinline__ bool bkl_step(unsigned long long (&x)[W], float& t, i
 #ifndef POP_EVOLVE_MIN_BLOCKS
 #define POP_EVOLVE_MIN_BLOCKS 5
 #endif
-template <int W>
+template <int W, bool MOD>
 __global__ void __launch_bounds__(kThreads, POP_EVOLVE_MIN_BLOCKS) k_evolve(Batch B, float dt_f) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   EvolveSmem<W>& S = *reinterpret_cast<EvolveSmem<W>*>(smem_raw);
@@ -139,6 +149,8 @@ __global__ void __launch_bounds__(kThreads, POP_EVOLVE_MIN_BLOCKS) k_evolve(Batc
       S.u_valid[tid] = (int)max((int64_t)0, min((int64_t)kUnit, d.nc - j0));
       S.u_min[tid] = INT_MAX;
       S.u_max[tid] = INT_MIN;
+      S.u_amin[tid] = INT_MAX;
+      S.u_amax[tid] = INT_MIN;
       S.u_ev[tid] = 0u;
     }
     if (tid == 0) S.take = 0;
@@ -170,7 +182,7 @@ __global__ void __launch_bounds__(kThreads, POP_EVOLVE_MIN_BLOCKS) k_evolve(Batc
     const int n = nu * kUnit;
     int c = -1;  // the lane's clone (chunk index), -1 when it has none
     unsigned long long x[W];
-    float t = 0.0f;
+    float t = 0.0f, acc = 0.0f;
     int h = 0, L = 3;
     uint32_t q = 0u, j = 0u;
     uint2 key = make_uint2(0u, 0u);
@@ -198,6 +210,7 @@ __global__ void __launch_bounds__(kThreads, POP_EVOLVE_MIN_BLOCKS) k_evolve(Batc
 #pragma unroll
               for (int w = 0; w < W; ++w) x[w] = S.x[c][w];
               t = 0.0f;
+              acc = 0.0f;
               h = 0;
               q = 0u;
               L = S.u_L[uu];
@@ -215,9 +228,9 @@ __global__ void __launch_bounds__(kThreads, POP_EVOLVE_MIN_BLOCKS) k_evolve(Batc
       if (c >= 0) {
         const uint4 d4 = philox4x32_10(make_uint4(q, beta, j, kTagEvolve), key.x, key.y);
         bool run = false;
-        if (bkl_step<W>(x, t, L, inv, S.logtab, d4.x, d4.y, dt_f)) {
+        if (bkl_step<W, MOD>(x, t, acc, L, inv, S.logtab, d4.x, d4.y, dt_f)) {
           ++h;
-          if (bkl_step<W>(x, t, L, inv, S.logtab, d4.z, d4.w, dt_f)) {
+          if (bkl_step<W, MOD>(x, t, acc, L, inv, S.logtab, d4.z, d4.w, dt_f)) {
             ++h;
             run = true;
           }
@@ -231,6 +244,7 @@ __global__ void __launch_bounds__(kThreads, POP_EVOLVE_MIN_BLOCKS) k_evolve(Batc
 #pragma unroll
           for (int w = 0; w < W; ++w) S.x[c][w] = x[w];
           S.hops[c] = h;
+          if (MOD) S.a[c] = acc;
           c = -1;
         }
       }
@@ -252,6 +266,17 @@ __global__ void __launch_bounds__(kThreads, POP_EVOLVE_MIN_BLOCKS) k_evolve(Batc
           store_lat<W>(B.X, slot, xo);
           B.KX[slot] = ky[m] + hh;
           B.dK[slot] = hh;
+          if (MOD) B.A[slot] = S.a[i];
+        }
+        if (MOD) {
+          // A >= 0, so its float bits order like the values
+          const int ab = valid ? __float_as_int(S.a[i]) : 0;
+          const int amn = __reduce_min_sync(0xffffffffu, valid ? ab : INT_MAX);
+          const int amx = __reduce_max_sync(0xffffffffu, valid ? ab : INT_MIN);
+          if (lane == 0) {
+            atomicMin(&S.u_amin[m], amn);
+            atomicMax(&S.u_amax[m], amx);
+          }
         }
         const int mn = __reduce_min_sync(0xffffffffu, valid ? hh : INT_MAX);
         const int mx = __reduce_max_sync(0xffffffffu, valid ? hh : INT_MIN);
@@ -269,6 +294,10 @@ __global__ void __launch_bounds__(kThreads, POP_EVOLVE_MIN_BLOCKS) k_evolve(Batc
       atomicMin(&st->dk_min, S.u_min[tid]);
       atomicMax(&st->dk_max, S.u_max[tid]);
       atomicAdd(&st->events, (unsigned long long)S.u_ev[tid]);
+      if (MOD) {
+        atomicMin(&st->a_min, S.u_amin[tid]);
+        atomicMax(&st->a_max, S.u_amax[tid]);
+      }
     }
     __syncthreads();
   }
@@ -291,9 +320,16 @@ __global__ void __launch_bounds__(kThreads) k_weights(Batch B) {
   const int64_t base = (int64_t)tile * kTile;
   const int64_t j0 = base - d.off + (int64_t)tid * kItems;
   const int4 dk4 = reinterpret_cast<const int4*>(B.dK + base)[tid];
+  float av[kItems] = {0.0f, 0.0f, 0.0f, 0.0f};
+  if (d.modified) {
+    const float4 a4 = reinterpret_cast<const float4*>(B.A + base)[tid];
+    av[0] = a4.x; av[1] = a4.y; av[2] = a4.z; av[3] = a4.w;
+  }
   for (int i = tid; i < kHistSmem; i += kThreads) s_hist[i] = 0u;
   const int dk_min = st->dk_min, dk_max = st->dk_max;
   const int kref = d.s_neg ? dk_max : dk_min;
+  // MODIFIED reference: the smallest (s >= 0) or largest (s < 0) rate integral
+  const float a_ref = __int_as_float(d.s_neg ? st->a_max : st->a_min);
   __syncthreads();
   const int dkv[kItems] = {dk4.x, dk4.y, dk4.z, dk4.w};
   const unsigned long long* wt = B.wtab + (size_t)p * kKcap;
@@ -302,28 +338,36 @@ __global__ void __launch_bounds__(kThreads) k_weights(Batch B) {
 #pragma unroll
   for (int i = 0; i < kItems; ++i) {
     if (j0 + i < d.nc) {
-      const unsigned int k = abs_diff(dkv[i], kref);
-      if (k >= (unsigned int)kKcap) {
+      unsigned long long w;
+      unsigned int k;
+      if (!clone_weight(d, dkv[i], kref, av[i], a_ref, wt, B.exp2tab, w, k)) {
         range_err = true;
       } else {
-        sum += __ldg(wt + k);
-        if (k < (unsigned int)kHistSmem) atomicAdd(&s_hist[k], 1u);
-        else atomicAdd(&B.hist[(size_t)p * kKcap + k], 1u);
+        sum += w;
+        if (!d.modified) {
+          if (k < (unsigned int)kHistSmem) atomicAdd(&s_hist[k], 1u);
+          else atomicAdd(&B.hist[(size_t)p * kKcap + k], 1u);
+        }
       }
     }
   }
   if (range_err) st->err = kErrRange;
   const unsigned long long total = block_sum_u64(sum, s_red);
-  const int nb = hist_bins(dk_min, dk_max, kHistSmem);
-  for (int b = tid; b < nb; b += kThreads) {
-    const unsigned int c = s_hist[b];
-    if (c) atomicAdd(&B.hist[(size_t)p * kKcap + b], c);
+  if (!d.modified) {
+    const int nb = hist_bins(dk_min, dk_max, kHistSmem);
+    for (int b = tid; b < nb; b += kThreads) {
+      const unsigned int c = s_hist[b];
+      if (c) atomicAdd(&B.hist[(size_t)p * kKcap + b], c);
+    }
   }
   if (tid == 0) {
     B.tile_sum[tile] = total;
     if (tile == d.first_tile) {
+      const uint32_t beta = *B.beta;
       st->kref = kref;
-      st->U = philox4x32_10(make_uint4(0u, *B.beta, 0u, kTagResample), (uint32_t)d.seed,
+      st->a_ref = a_ref;
+      st->beta = beta;
+      st->U = philox4x32_10(make_uint4(0u, beta, 0u, kTagResample), (uint32_t)d.seed,
                             (uint32_t)(d.seed >> 32)).x;
     }
   }
@@ -372,7 +416,13 @@ __global__ void __launch_bounds__(kThreads, 6) k_gather(Batch B) {
       s_K[i] = B.KX[base + i];
     }
   }
+  float av[kItems] = {0.0f, 0.0f, 0.0f, 0.0f};
+  if (d.modified) {
+    const float4 a4 = reinterpret_cast<const float4*>(B.A + base)[tid];
+    av[0] = a4.x; av[1] = a4.y; av[2] = a4.z; av[3] = a4.w;
+  }
   const int kref = st->kref;
+  const float a_ref = st->a_ref;
   const unsigned long long c = 2ull * (unsigned long long)st->U + 1ull;
 
   // population total T and this tile's exclusive prefix
@@ -392,8 +442,8 @@ __global__ void __launch_bounds__(kThreads, 6) k_gather(Batch B) {
   for (int i = 0; i < kItems; ++i) {
     w[i] = 0ull;
     if (j0 + i < d.nc) {
-      const unsigned int k = abs_diff(dkv[i], kref);
-      if (k < (unsigned int)kKcap) w[i] = __ldg(wt + k);
+      unsigned int k;
+      clone_weight(d, dkv[i], kref, av[i], a_ref, wt, B.exp2tab, w[i], k);
     }
     tsum += w[i];
   }
@@ -411,6 +461,15 @@ __global__ void __launch_bounds__(kThreads, 6) k_gather(Batch B) {
   const float ratio = __fdiv_rn((float)nc, __uint2float_rn((uint32_t)(T >> sh)));
   unsigned long long run = excl + xs - tsum;
   for (int q = 0; q < wid; ++q) run += s_wsum[q];
+  if (d.iid) {
+    // [iid]: publish this tile's prefix sums; k_select_iid draws the points
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+      B.S[base + (int64_t)tid * kItems + i] = run;
+      run += w[i];
+    }
+    if (lt == 0 && tid == 0) st->T = T;
+  } else {
   uint32_t jl[kItems + 1];
   j_lo_run<kItems>(run, w, T, c, nc, sh, ratio, jl);
 #pragma unroll
@@ -461,11 +520,23 @@ __global__ void __launch_bounds__(kThreads, 6) k_gather(Batch B) {
       }
     }
   }
+  }  // [eq]
 
-  // psi term of eq. (psihat) for this interval, once per population:
-  //   term = -s k_ref + ln( (1/N_c) sum_k n_k exp(-|s| k) ),
-  // with the log taken as log1p of the expm1 sum when the mean is above 1/2.
-  if (lt == 0 && wid == 0) {
+  // psi term of eq. (psihat) for this interval, once per population.
+  // MODIFIED (reading of eq. def-ups-ssep): -c A_ref + log1p((T - N_c 2^F) / (N_c 2^F))
+  // from the exact total T of the quantised weights.
+  if (d.modified && lt == 0 && tid == 0) {
+    const double base_w = ldexp((double)d.nc, d.F);
+    const long long D = (long long)T - (long long)((unsigned long long)d.nc << d.F);
+    st->psi_acc += -(double)d.c_f * (double)a_ref + log1p((double)D / base_w);
+    st->dk_min = INT_MAX;
+    st->dk_max = INT_MIN;
+    st->a_min = INT_MAX;
+    st->a_max = INT_MIN;
+  }
+  // plain: term = -s k_ref + ln( (1/N_c) sum_k n_k exp(-|s| k) ) from the exact
+  // activity histogram, the log taken as log1p of the expm1 sum when the mean is > 1/2.
+  if (!d.modified && lt == 0 && wid == 0) {
     const int dk_min = st->dk_min, dk_max = st->dk_max;
     const int R = hist_bins(dk_min, dk_max, kKcap);
     unsigned int* h = B.hist + (size_t)p * kKcap;
@@ -489,6 +560,58 @@ __global__ void __launch_bounds__(kThreads, 6) k_gather(Batch B) {
       st->psi_acc += -d.s * (double)kref + ln_mean;
       st->dk_min = INT_MAX;
       st->dk_max = INT_MIN;
+      st->a_min = INT_MAX;
+      st->a_max = INT_MIN;
+    }
+  }
+  // the interval ends here unless [iid] selection still has to run
+  if (!B.any_iid && blockIdx.x == gridDim.x - 1 && tid == 0) *B.beta += 1u;
+}
+
+// ---------------------------------------------------------------------------
+// [iid] selection (Sec. 4.1): new clone j of the population pulls old clone k with
+// S_k <= alpha_j < S_{k+1}, alpha_j = floor(U64_j T / 2^64), U64_j from draw
+// (j, beta, 0, 4); a binary search over the population's prefix sums.  One block
+// per tile of new slots; populations with [eq] selection are skipped.  The last
+// block advances the interval counter.
+// ---------------------------------------------------------------------------
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_select_iid(Batch B) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int tile = blockIdx.x;
+  const int p = B.tile_pop[tile];
+  const PopDesc d = B.pops[p];
+  if (d.iid) {
+    const PopState* st = B.st + p;
+    const unsigned long long T = st->T;
+    const uint32_t beta = st->beta;
+    const int lt = tile - d.first_tile;
+    const unsigned long long* S = B.S + d.off;
+    const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
+    for (int i = (W > 0 ? tid : wid); i < kTile; i += (W > 0 ? kThreads : kWarps)) {
+      const int64_t j = (int64_t)lt * kTile + i;
+      if (j >= d.nc) break;
+      const uint4 r = philox4x32_10(make_uint4((uint32_t)j, beta, 0u, kTagIid), k0, k1);
+      const unsigned long long alpha = __umul64hi(((unsigned long long)r.y << 32) | r.x, T);
+      long long lo = 0, hi = d.nc - 1;  // the last k with S_k <= alpha
+      while (lo < hi) {
+        const long long mid = lo + (hi - lo + 1) / 2;
+        if (S[mid] <= alpha) lo = mid; else hi = mid - 1;
+      }
+      const int64_t src = d.off + lo, dst = d.off + j;
+      if constexpr (W > 0) {
+        unsigned long long x[W];
+        load_lat<W>(B.X, src, x);
+        store_lat<W>(B.Y, dst, x);
+        B.KY[dst] = B.KX[src];
+        B.anc[dst] = (int32_t)lo;
+      } else {
+        for (int q = lane; q < B.W; q += 32) B.Y[dst * B.W + q] = B.X[src * B.W + q];
+        if (lane == 0) {
+          B.KY[dst] = B.KX[src];
+          B.anc[dst] = (int32_t)lo;
+        }
+      }
     }
   }
   if (blockIdx.x == gridDim.x - 1 && tid == 0) *B.beta += 1u;
@@ -519,9 +642,11 @@ __device__ __forceinline__ void wide_active(unsigned long long xl, unsigned long
   ah = xh ^ rh;
 }
 
-// One BKL step of the warp's clone; returns true if it hopped.
+// One BKL step of the warp's clone; returns true if it hopped (MOD: accumulate
+// the rate integral as in bkl_step).
+template <bool MOD>
 __device__ __forceinline__ bool wide_step(unsigned long long& xl, unsigned long long& xh,
-                                          float& t, int L, int lane, const float* inv,
+                                          float& t, float& acc, int L, int lane, const float* inv,
                                           const float2* tab, uint32_t wa, uint32_t wb,
                                           float dt_f) {
   unsigned long long al, ah;
@@ -529,8 +654,13 @@ __device__ __forceinline__ bool wide_step(unsigned long long& xl, unsigned long 
   const int cl = __popcll(al) + __popcll(ah);
   const int r = __reduce_add_sync(0xffffffffu, (unsigned int)cl);
   if (r == 0) return false;
-  const float t_new = __fadd_rn(t, __fmul_rn(neg_ln_u(wa, tab), inv[r]));
-  if (t_new >= dt_f) return false;
+  const float tau = __fmul_rn(neg_ln_u(wa, tab), inv[r]);
+  const float t_new = __fadd_rn(t, tau);
+  if (t_new >= dt_f) {
+    if (MOD) acc = __fmaf_rn((float)r, __fsub_rn(dt_f, t), acc);
+    return false;
+  }
+  if (MOD) acc = __fmaf_rn((float)r, tau, acc);
   t = t_new;
   const uint32_t k = __umulhi(wb, (uint32_t)r);
   int incl = cl;
@@ -555,6 +685,7 @@ __device__ __forceinline__ bool wide_step(unsigned long long& xl, unsigned long 
   return true;
 }
 
+template <bool MOD>
 __global__ void __launch_bounds__(kThreads) k_evolve_wide(Batch B, float dt_f) {
   __shared__ float2 s_tab[64];
   const int tid = threadIdx.x, lane = tid & 31;
@@ -572,7 +703,7 @@ __global__ void __launch_bounds__(kThreads) k_evolve_wide(Batch B, float dt_f) {
     unsigned long long xh = (2 * lane + 1 < W) ? B.Y[slot * W + 2 * lane + 1] : 0ull;
     const float* inv = B.inv_rate + (size_t)p * kInvStride;
     const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
-    float t = 0.0f;
+    float t = 0.0f, acc = 0.0f;
     int h = 0;
     for (uint32_t q = 0;; ++q) {
       if (q >= kStepLimit / 2u) {  // guard: an interval must end; report, never spin
@@ -580,9 +711,9 @@ __global__ void __launch_bounds__(kThreads) k_evolve_wide(Batch B, float dt_f) {
         break;
       }
       const uint4 d4 = philox4x32_10(make_uint4(q, beta, (uint32_t)j, kTagEvolve), k0, k1);
-      if (!wide_step(xl, xh, t, d.L, lane, inv, s_tab, d4.x, d4.y, dt_f)) break;
+      if (!wide_step<MOD>(xl, xh, t, acc, d.L, lane, inv, s_tab, d4.x, d4.y, dt_f)) break;
       ++h;
-      if (!wide_step(xl, xh, t, d.L, lane, inv, s_tab, d4.z, d4.w, dt_f)) break;
+      if (!wide_step<MOD>(xl, xh, t, acc, d.L, lane, inv, s_tab, d4.z, d4.w, dt_f)) break;
       ++h;
     }
     if (2 * lane < W) B.X[slot * W + 2 * lane] = xl;
@@ -593,6 +724,11 @@ __global__ void __launch_bounds__(kThreads) k_evolve_wide(Batch B, float dt_f) {
       atomicMin(&B.st[p].dk_min, h);
       atomicMax(&B.st[p].dk_max, h);
       atomicAdd(&B.st[p].events, (unsigned long long)h);
+      if (MOD) {
+        B.A[slot] = acc;
+        atomicMin(&B.st[p].a_min, __float_as_int(acc));
+        atomicMax(&B.st[p].a_max, __float_as_int(acc));
+      }
     }
   }
 }

@@ -45,6 +45,7 @@ def test_workspace_bytes(lib):
     assert pg.lattice_words([P(L=64)]) == 1
     assert pg.lattice_words([P(L=65), P(L=20)]) == 2
     assert pg.lattice_words([P(L=4096, N=5)]) == 64
+    assert pg.workspace_bytes([P(weight_mode=1, selection=1)]) > 0
     for bad in (P(L=2), P(L=4097), P(N=-1), P(N=21), P(n_clones=0), P(weight_mode=7), P(selection=9)):
         assert pg.workspace_bytes([bad]) == 0, bad
 

@@ -30,7 +30,9 @@ def pg():
 
 
 def oracle_pops(pops):
-    return [oracle.Population(q["L"], q["N"], q["n_clones"], q["seed"]) for q in pops]
+    return [oracle.Population(q["L"], q["N"], q["n_clones"], q["seed"],
+                              modified=q.get("weight_mode", 0) == 1, iid=q.get("selection", 0) == 1)
+            for q in pops]
 
 
 def assert_state_equal(gpu, orc, W, what):
@@ -48,7 +50,7 @@ def run_parity(pg, pops, s, dt, M):
     for beta in range(1, M + 1):
         batch.evolve(dt, s)
         for p, o in enumerate(orcs):
-            o.evolve(dt)
+            o.evolve(dt, s[p])
             g = batch.copy_state(p)
             assert_state_equal(g, o, W, "evolve beta=%d pop %d" % (beta, p))
             assert np.array_equal(g["dK"], o.dK), "dK beta=%d pop %d" % (beta, p)
@@ -235,3 +237,30 @@ def test_parity_mixed_batch_wide(pg):
     pops = [dict(L=50, N=25, n_clones=1500, seed=1), dict(L=300, N=150, n_clones=1100, seed=2),
             dict(L=7, N=3, n_clones=900, seed=3)]
     run_parity(pg, pops, [0.02, 0.004, -0.3], 0.05, 3)
+
+
+MOD, IID = 1, 1
+
+
+@pytest.mark.parametrize("L,N,nc,s,mode,sel", [
+    (20, 10, 1500, 0.3, MOD, 0),
+    (50, 25, 2100, -0.2, MOD, 0),
+    (100, 40, 1100, 0.05, MOD, 0),       # two-word lattices
+    (300, 150, 600, 0.01, MOD, 0),       # one clone per warp
+    (37, 5, 1, 0.5, MOD, 0),             # one clone
+    (20, 10, 1500, 0.3, 0, IID),
+    (64, 31, 1300, -0.1, MOD, IID),
+    (200, 100, 800, 0.02, 0, IID),       # one clone per warp
+    (12, 0, 300, 0.3, MOD, 0),           # empty ring: A = 0, equal weights
+])
+def test_parity_modified_and_iid(pg, L, N, nc, s, mode, sel):
+    pops = [dict(L=L, N=N, n_clones=nc, seed=555 + L, weight_mode=mode, selection=sel)]
+    run_parity(pg, pops, [s], 0.1 if L < 100 else 0.05, 5)
+
+
+def test_parity_mixed_modes_batch(pg):
+    pops = [dict(L=30, N=15, n_clones=1200, seed=1),
+            dict(L=40, N=20, n_clones=2100, seed=2, weight_mode=MOD),
+            dict(L=50, N=25, n_clones=900, seed=3, selection=IID),
+            dict(L=60, N=20, n_clones=1500, seed=4, weight_mode=MOD, selection=IID)]
+    run_parity(pg, pops, [0.1, -0.05, 0.02, 0.3], 0.1, 4)
