@@ -151,6 +151,15 @@ int pop_estimate_psi(pop_t* pop, double* psi, double* k_hat, double* t_obs);
 int pop_copy_state(pop_t* pop, int32_t p, uint64_t* h_lattice, int32_t* h_K,
                    int32_t* h_anc, int32_t* h_dK);
 
+/*
+ * Population mean of |delta rho_n|^2 over the current configurations (eq. fourdens:
+ * delta rho_n = L^-1/2 sum_j exp(-2 pi i n X_j / L) over the occupied sites X_j;
+ * Sec. 3.3 uses n = 1 to follow the clustering transition).  Per clone in FP32 from
+ * float tables of cos and sin, the mean in FP64.  h_mean: host array of n_pops.
+ * n >= 0.  POP_ERR_STATE between pop_evolve and pop_resample.  Waits for the stream.
+ */
+int pop_density_mode(pop_t* pop, int32_t n, double* h_mean);
+
 /* Executed hops (BKL events) per population since pop_init (host array of n_pops). */
 int pop_events(pop_t* pop, uint64_t* h_events);
 

@@ -78,6 +78,8 @@ def lib():
         L.orc_psi_term_modified.restype = ctypes.c_double
         L.orc_ancestors_iid.argtypes = [ctypes.c_int64, _u64p, ctypes.c_uint32, ctypes.c_uint64, _i32p]
         L.orc_ancestors_iid.restype = ctypes.c_int
+        L.orc_density_mode.argtypes = [ctypes.c_int32, ctypes.c_int64, _u8p, ctypes.c_int32]
+        L.orc_density_mode.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -221,6 +223,12 @@ def init_sites(L, N, n_clones, seed):
     if rc != 0:
         raise ValueError("orc_init rc=%d" % rc)
     return sites
+
+
+def density_mode(sites, n):
+    """Population mean of |delta rho_n|^2 (eq. fourdens), FP32 per clone, FP64 mean."""
+    sites = np.ascontiguousarray(np.asarray(sites, dtype=np.uint8))
+    return float(lib().orc_density_mode(sites.shape[1], sites.shape[0], _p(sites, _u8p), int(n)))
 
 
 def weight_exp(x, F):

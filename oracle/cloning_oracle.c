@@ -530,6 +530,37 @@ int orc_ancestors_iid(int64_t n_clones, const uint64_t* w, uint32_t beta, uint64
 }
 
 /* ---------------------------------------------------------------------------
+ * Fourier density mode, eq. (fourdens): delta rho_n = L^-1/2 sum_j e^{-2 pi i n X_j / L}
+ * over the occupied sites X_j.  Reading: per clone in FP32, |delta rho_n|^2 =
+ * (C^2 + S^2) / L with C, S the sums (in increasing site order) of
+ * float(cos(2 pi n x / L)) and float(sin(2 pi n x / L)) rounded once from FP64;
+ * the population mean is taken in FP64.
+ * ------------------------------------------------------------------------- */
+double orc_density_mode(int32_t L, int64_t n_clones, const uint8_t* sites, int32_t n) {
+  float* ct = (float*)malloc((size_t)L * sizeof(float));
+  float* st = (float*)malloc((size_t)L * sizeof(float));
+  if (!ct || !st) { free(ct); free(st); return -1.0; }
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int x = 0; x < L; ++x) {
+    double th = two_pi * (double)((int64_t)n * x % L) / (double)L;
+    ct[x] = (float)cos(th);
+    st[x] = (float)sin(th);
+  }
+  double acc = 0.0;
+  for (int64_t j = 0; j < n_clones; ++j) {
+    const uint8_t* occ = sites + j * (int64_t)L;
+    float c = 0.0f, s = 0.0f;
+    for (int x = 0; x < L; ++x) {
+      if (occ[x]) { c = c + ct[x]; s = s + st[x]; }
+    }
+    float v = (c * c + s * s) / (float)L;
+    acc += (double)v;
+  }
+  free(ct); free(st);
+  return acc / (double)n_clones;
+}
+
+/* ---------------------------------------------------------------------------
  * A full run of the cloning algorithm (Sec. 2.3): init, then M intervals of
  * (dynamical stage, cloning stage).  psi_hat = (1/t_obs) sum_beta term_beta
  * (eq. psihat, all M intervals); k_hat = (1/(N_c L t_obs)) sum_j K_j over the

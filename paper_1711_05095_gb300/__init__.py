@@ -31,7 +31,7 @@ POP_MAX_L = 4096
 # every symbol include/pop.h declares
 EXPORTS = ("pop_workspace_bytes", "pop_init", "pop_set_state", "pop_evolve", "pop_resample",
            "pop_run", "pop_estimate_psi", "pop_copy_state", "pop_events", "pop_lattice_words",
-           "pop_select_noalloc", "pop_strerror", "pop_free")
+           "pop_select_noalloc", "pop_density_mode", "pop_strerror", "pop_free")
 POP_NOALLOC_MAX_CLONES = 1 << 20
 
 
@@ -82,6 +82,8 @@ def library():
     L.pop_estimate_psi.restype = ctypes.c_int
     L.pop_copy_state.argtypes = [ctypes.c_void_p, ctypes.c_int32, _u64p, _i32p, _i32p, _i32p]
     L.pop_copy_state.restype = ctypes.c_int
+    L.pop_density_mode.argtypes = [ctypes.c_void_p, ctypes.c_int32, _f64p]
+    L.pop_density_mode.restype = ctypes.c_int
     L.pop_events.argtypes = [ctypes.c_void_p, _u64p]
     L.pop_events.restype = ctypes.c_int
     L.pop_select_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_uint64,
@@ -199,6 +201,12 @@ class PopulationBatch:
                                         anc.ctypes.data_as(_i32p), dK.ctypes.data_as(_i32p)),
                "pop_copy_state")
         return dict(lattice=lat, K=K, anc=anc, dK=dK)
+
+    def density_mode(self, n=1):
+        """Population mean of |delta rho_n|^2 (eq. fourdens) per population."""
+        out = np.zeros(self.n_pops)
+        _check(self._lib.pop_density_mode(self._h, int(n), out.ctypes.data_as(_f64p)), "pop_density_mode")
+        return out
 
     def events(self):
         ev = np.zeros(self.n_pops, dtype=np.uint64)

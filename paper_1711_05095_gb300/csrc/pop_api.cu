@@ -29,7 +29,7 @@ constexpr int kGraphIntervals = 32;
 struct Layout {
   int32_t P = 0, W = 0, ntiles = 0, nunits = 0;
   int64_t nslots = 0;
-  size_t o_pops, o_st, o_tile_pop, o_wtab, o_qtab, o_qm1tab, o_inv, o_logtab, o_exp2, o_A, o_S, o_hist, o_tile_sum, o_beta,
+  size_t o_pops, o_st, o_tile_pop, o_wtab, o_qtab, o_qm1tab, o_inv, o_logtab, o_exp2, o_A, o_S, o_cs, o_tacc, o_hist, o_tile_sum, o_beta,
       o_ksum, o_X, o_Y, o_KX, o_KY, o_dK, o_anc, total;
 };
 
@@ -87,6 +87,8 @@ bool make_layout(const pop_params* params, int32_t n_pops, Layout* lay) {
   l.o_anc = take(ns * sizeof(int32_t));
   l.o_A = take(ns * sizeof(float));
   l.o_S = take(ns * sizeof(unsigned long long));
+  l.o_cs = take(P * kInvStride * sizeof(float2));
+  l.o_tacc = take(nt * sizeof(double));
   l.total = o;
   *lay = l;
   return true;
@@ -559,6 +561,39 @@ int pop_events(pop_t* h, uint64_t* h_events) {
   const int rc = check_device_errors(h, &st);
   if (rc != POP_OK) return rc;
   for (int32_t p = 0; p < h->lay.P; ++p) h_events[p] = st[p].events;
+  return POP_OK;
+}
+
+int pop_density_mode(pop_t* h, int32_t n, double* h_mean) {
+  if (h == nullptr || h_mean == nullptr || n < 0) return POP_ERR_ARG;
+  if (h->phase != kReady) return POP_ERR_STATE;
+  const double two_pi = 6.283185307179586476925286766559;
+  std::vector<float2> cs((size_t)h->lay.P * kInvStride, make_float2(0.0f, 0.0f));
+  for (int32_t p = 0; p < h->lay.P; ++p) {
+    const int L = h->params[p].L;
+    for (int x = 0; x < L; ++x) {
+      const double th = two_pi * (double)((int64_t)n * x % L) / (double)L;
+      cs[(size_t)p * kInvStride + x] = make_float2((float)std::cos(th), (float)std::sin(th));
+    }
+  }
+  float2* d_cs = (float2*)(h->ws + h->lay.o_cs);
+  double* d_tacc = (double*)(h->ws + h->lay.o_tacc);
+  POP_CUDA(cudaMemcpyAsync(d_cs, cs.data(), cs.size() * sizeof(float2), cudaMemcpyHostToDevice,
+                           h->stream));
+  const unsigned grid = (unsigned)h->lay.ntiles;
+  if (h->lay.W == 1) k_density<1><<<grid, kThreads, 0, h->stream>>>(h->B, d_cs, d_tacc);
+  else if (h->lay.W == 2) k_density<2><<<grid, kThreads, 0, h->stream>>>(h->B, d_cs, d_tacc);
+  else k_density<0><<<grid, kThreads, 0, h->stream>>>(h->B, d_cs, d_tacc);
+  POP_CUDA(cudaGetLastError());
+  std::vector<double> tacc((size_t)h->lay.ntiles);
+  POP_CUDA(cudaMemcpyAsync(tacc.data(), d_tacc, tacc.size() * sizeof(double),
+                           cudaMemcpyDeviceToHost, h->stream));
+  POP_CUDA(cudaStreamSynchronize(h->stream));
+  for (int32_t p = 0; p < h->lay.P; ++p) {
+    double sum = 0.0;
+    for (int32_t t = 0; t < h->desc[p].ntiles; ++t) sum += tacc[(size_t)h->desc[p].first_tile + t];
+    h_mean[p] = sum / (double)h->params[p].n_clones;
+  }
   return POP_OK;
 }
 

@@ -733,6 +733,47 @@ __global__ void __launch_bounds__(kThreads) k_evolve_wide(Batch B, float dt_f) {
   }
 }
 
+// Fourier density mode (eq. fourdens): per clone, C and S are the sums over the
+// occupied sites in increasing order of float(cos), float(sin) of 2 pi n x / L
+// (cs[x], from the host); |delta rho_n|^2 = (C^2 + S^2) / L in FP32; per tile the
+// FP64 sum over its clones.
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_density(Batch B, const float2* cs, double* tile_acc) {
+  __shared__ double s_part[kWarps];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int tile = blockIdx.x;
+  const int p = B.tile_pop[tile];
+  const PopDesc d = B.pops[p];
+  const float2* tab = cs + (size_t)p * kInvStride;
+  const int64_t base = (int64_t)tile * kTile;
+  const int nw = W > 0 ? W : B.W;
+  double acc = 0.0;
+  for (int i = tid; i < kTile; i += kThreads) {
+    if (base - d.off + i >= d.nc) continue;
+    float c = 0.0f, sn = 0.0f;
+    for (int q = 0; q < nw; ++q) {
+      unsigned long long bits = B.Y[(base + i) * nw + q];
+      while (bits) {
+        const int b = __ffsll((long long)bits) - 1;
+        const float2 v = tab[64 * q + b];
+        c = __fadd_rn(c, v.x);
+        sn = __fadd_rn(sn, v.y);
+        bits &= bits - 1ull;
+      }
+    }
+    acc += (double)__fdiv_rn(__fadd_rn(__fmul_rn(c, c), __fmul_rn(sn, sn)), (float)d.L);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) s_part[wid] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kWarps; ++w) t += s_part[w];
+    tile_acc[tile] = t;
+  }
+}
+
 // Sum of the carried activities of each population (for k_hat, eq. khat).
 __global__ void __launch_bounds__(kThreads) k_ksum(Batch B) {
   __shared__ long long s_part[kWarps];

@@ -264,3 +264,44 @@ def test_parity_mixed_modes_batch(pg):
             dict(L=50, N=25, n_clones=900, seed=3, selection=IID),
             dict(L=60, N=20, n_clones=1500, seed=4, weight_mode=MOD, selection=IID)]
     run_parity(pg, pops, [0.1, -0.05, 0.02, 0.3], 0.1, 4)
+
+
+@pytest.mark.parametrize("L,N,nc,W_case", [(50, 25, 2500, 1), (100, 50, 1300, 2), (300, 90, 700, 0)])
+def test_density_mode_matches_oracle(pg, L, N, nc, W_case):
+    q = dict(L=L, N=N, n_clones=nc, seed=31 + L)
+    s = 20.0 / L**2
+    batch = pg.PopulationBatch([q])
+    o = oracle.Population(L, N, nc, q["seed"])
+    for _ in range(4):
+        batch.evolve(0.1, [s]); batch.resample()
+        o.evolve(0.1); o.resample(s)
+    for n in (0, 1, 3):
+        got = batch.density_mode(n)[0]
+        np.testing.assert_allclose(got, oracle.density_mode(o.sites, n), rtol=1e-12)
+
+
+def test_full_size_uneven_batch_sampled(pg):
+    # 256 populations of uneven L (32..128), N_c (2^10..2^18) and s, one batch, in
+    # the captured-graph launch (pop_run); three small populations checked bit for
+    # bit, invariants everywhere
+    w = workloads.uneven_batch()
+    M = 3
+    batch = pg.PopulationBatch(w["pops"])
+    batch.run(w["dt"], w["s"], M)
+    psi, _, _ = batch.estimate_psi()
+    ncs = np.array([q["n_clones"] for q in w["pops"]])
+    for p in np.argsort(ncs)[:3]:
+        q = w["pops"][p]
+        o = oracle.Population(q["L"], q["N"], q["n_clones"], q["seed"])
+        for _ in range(M):
+            o.evolve(w["dt"])
+            o.resample(w["s"][p])
+        g = batch.copy_state(int(p))
+        assert np.array_equal(g["anc"], o.anc)
+        assert_state_equal(g, o, batch.W, "uneven pop %d" % p)
+        np.testing.assert_allclose(psi[p], o.estimates()[0], rtol=PSI_RTOL)
+    for p in range(0, 256, 17):
+        g = batch.copy_state(p)
+        assert np.all(np.diff(g["anc"]) >= 0)
+        assert g["anc"].max() < w["pops"][p]["n_clones"]
+        assert np.all(np.isfinite(psi))
