@@ -211,9 +211,10 @@ int launch_evolve(pop_t* h, cudaStream_t st, float dt_f) {
 int launch_resample(pop_t* h, cudaStream_t st) {
   const unsigned grid = (unsigned)h->lay.ntiles;
   k_weights<<<grid, kThreads, 0, st>>>(h->B);
-  if (h->lay.W == 1) k_gather<1><<<grid, kThreads, 0, st>>>(h->B);
-  else if (h->lay.W == 2) k_gather<2><<<grid, kThreads, 0, st>>>(h->B);
-  else k_gather<0><<<grid, kThreads, 0, st>>>(h->B);
+  constexpr int GT = POP_GATHER_THREADS;
+  if (h->lay.W == 1) k_gather<1, GT><<<grid, GT, 0, st>>>(h->B);
+  else if (h->lay.W == 2) k_gather<2, GT><<<grid, GT, 0, st>>>(h->B);
+  else k_gather<0, GT><<<grid, GT, 0, st>>>(h->B);
   if (h->B.any_iid) {
     if (h->lay.W == 1) k_select_iid<1><<<grid, kThreads, 0, st>>>(h->B);
     else if (h->lay.W == 2) k_select_iid<2><<<grid, kThreads, 0, st>>>(h->B);

@@ -301,6 +301,22 @@ __device__ __forceinline__ double warp_sum_f64(double v) {
   return v;
 }
 
+// Block-wide sum of one 64-bit value per thread for blocks of NW warps (result
+// valid in every thread).
+template <int NW>
+__device__ __forceinline__ unsigned long long block_sum_u64_n(unsigned long long v,
+                                                              unsigned long long* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_sum_u64(v);
+  if (lane == 0) scratch[wid] = v;
+  __syncthreads();
+  unsigned long long t = 0ull;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) t += scratch[w];
+  __syncthreads();
+  return t;
+}
+
 // Block-wide sum of one 64-bit value per thread (result valid in every thread).
 __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v,
                                                             unsigned long long* scratch) {

@@ -382,15 +382,20 @@ __global__ void __launch_bounds__(kThreads) k_weights(Batch B) {
 // the psi term; the last block advances the interval counter (no block of this
 // kernel reads it).
 // ---------------------------------------------------------------------------
-template <int W>
-__global__ void __launch_bounds__(kThreads, 6) k_gather(Batch B) {
+#ifndef POP_GATHER_THREADS
+#define POP_GATHER_THREADS 128
+#endif
+template <int W, int NT>
+__global__ void __launch_bounds__(NT, NT == 128 ? 11 : 6) k_gather(Batch B) {
+  constexpr int NI = kTile / NT;   // old clones per thread
+  constexpr int NWARP = NT / 32;
   constexpr int WS = W > 0 ? W : 1;  // W == 0: wide lattices, copied without staging
   __shared__ unsigned long long s_x[W > 0 ? kTile : 1][WS];
   __shared__ int32_t s_K[kTile];
   __shared__ uint32_t s_jlo[kTile + 1];
   __shared__ uint16_t s_src[kMap];
-  __shared__ unsigned long long s_red[kWarps];
-  __shared__ unsigned long long s_wsum[kWarps];
+  __shared__ unsigned long long s_red[NWARP];
+  __shared__ unsigned long long s_wsum[NWARP];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int tile = blockIdx.x;
   const int p = B.tile_pop[tile];
@@ -399,13 +404,18 @@ __global__ void __launch_bounds__(kThreads, 6) k_gather(Batch B) {
   const int lt = tile - d.first_tile;
   const uint32_t nc = (uint32_t)d.nc;
   const int64_t base = (int64_t)tile * kTile;
-  const int64_t j0 = base - d.off + (int64_t)tid * kItems;
+  const int64_t j0 = base - d.off + (int64_t)tid * NI;
 
   // independent loads first: activities and the old clones of this tile
-  const int4 dk4 = reinterpret_cast<const int4*>(B.dK + base)[tid];
+  int dkv[NI];
 #pragma unroll
-  for (int m = 0; m < kItems; ++m) {
-    const int i = m * kThreads + tid;
+  for (int v = 0; v < NI / 4; ++v) {
+    const int4 dk4 = reinterpret_cast<const int4*>(B.dK + base)[tid * (NI / 4) + v];
+    dkv[4 * v] = dk4.x; dkv[4 * v + 1] = dk4.y; dkv[4 * v + 2] = dk4.z; dkv[4 * v + 3] = dk4.w;
+  }
+#pragma unroll
+  for (int m = 0; m < NI; ++m) {
+    const int i = m * NT + tid;
     if (base - d.off + i < d.nc) {
       if constexpr (W > 0) {
         unsigned long long x[W];
@@ -416,10 +426,15 @@ __global__ void __launch_bounds__(kThreads, 6) k_gather(Batch B) {
       s_K[i] = B.KX[base + i];
     }
   }
-  float av[kItems] = {0.0f, 0.0f, 0.0f, 0.0f};
+  float av[NI];
+#pragma unroll
+  for (int i = 0; i < NI; ++i) av[i] = 0.0f;
   if (d.modified) {
-    const float4 a4 = reinterpret_cast<const float4*>(B.A + base)[tid];
-    av[0] = a4.x; av[1] = a4.y; av[2] = a4.z; av[3] = a4.w;
+#pragma unroll
+    for (int v = 0; v < NI / 4; ++v) {
+      const float4 a4 = reinterpret_cast<const float4*>(B.A + base)[tid * (NI / 4) + v];
+      av[4 * v] = a4.x; av[4 * v + 1] = a4.y; av[4 * v + 2] = a4.z; av[4 * v + 3] = a4.w;
+    }
   }
   const int kref = st->kref;
   const float a_ref = st->a_ref;
@@ -427,19 +442,18 @@ __global__ void __launch_bounds__(kThreads, 6) k_gather(Batch B) {
 
   // population total T and this tile's exclusive prefix
   unsigned long long tT = 0ull, tE = 0ull;
-  for (int i = tid; i < d.ntiles; i += kThreads) {
+  for (int i = tid; i < d.ntiles; i += NT) {
     const unsigned long long v = B.tile_sum[d.first_tile + i];
     tT += v;
     if (i < lt) tE += v;
   }
 
   // weights of this tile's clones and their scan within each warp
-  const int dkv[kItems] = {dk4.x, dk4.y, dk4.z, dk4.w};
   const unsigned long long* wt = B.wtab + (size_t)p * kKcap;
-  unsigned long long w[kItems];
+  unsigned long long w[NI];
   unsigned long long tsum = 0ull;
 #pragma unroll
-  for (int i = 0; i < kItems; ++i) {
+  for (int i = 0; i < NI; ++i) {
     w[i] = 0ull;
     if (j0 + i < d.nc) {
       unsigned int k;
@@ -454,8 +468,8 @@ __global__ void __launch_bounds__(kThreads, 6) k_gather(Batch B) {
     if (lane >= o) xs += y;
   }
   if (lane == 31) s_wsum[wid] = xs;
-  const unsigned long long T = block_sum_u64(tT, s_red);
-  const unsigned long long excl = block_sum_u64(tE, s_red);
+  const unsigned long long T = block_sum_u64_n<NWARP>(tT, s_red);
+  const unsigned long long excl = block_sum_u64_n<NWARP>(tE, s_red);
 
   const int sh = max(0, 64 - __clzll((long long)T) - 24);
   const float ratio = __fdiv_rn((float)nc, __uint2float_rn((uint32_t)(T >> sh)));
@@ -464,25 +478,25 @@ __global__ void __launch_bounds__(kThreads, 6) k_gather(Batch B) {
   if (d.iid) {
     // [iid]: publish this tile's prefix sums; k_select_iid draws the points
 #pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-      B.S[base + (int64_t)tid * kItems + i] = run;
+    for (int i = 0; i < NI; ++i) {
+      B.S[base + (int64_t)tid * NI + i] = run;
       run += w[i];
     }
     if (lt == 0 && tid == 0) st->T = T;
   } else {
-  uint32_t jl[kItems + 1];
-  j_lo_run<kItems>(run, w, T, c, nc, sh, ratio, jl);
+  uint32_t jl[NI + 1];
+  j_lo_run<NI>(run, w, T, c, nc, sh, ratio, jl);
 #pragma unroll
-  for (int i = 0; i < kItems; ++i) s_jlo[tid * kItems + i] = jl[i];
-  if (tid == kThreads - 1) s_jlo[kTile] = jl[kItems];
+  for (int i = 0; i < NI; ++i) s_jlo[tid * NI + i] = jl[i];
+  if (tid == NT - 1) s_jlo[kTile] = jl[NI];
   __syncthreads();
 
   const uint32_t J0 = s_jlo[0], J1 = s_jlo[kTile];
   const bool mapped = (J1 - J0) <= (uint32_t)kMap;
   if (mapped) {
 #pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-      const int k = tid * kItems + i;
+    for (int i = 0; i < NI; ++i) {
+      const int k = tid * NI + i;
       for (uint32_t jj = s_jlo[k]; jj < s_jlo[k + 1]; ++jj) s_src[jj - J0] = (uint16_t)k;
     }
     __syncthreads();
@@ -497,7 +511,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_gather(Batch B) {
     return lo;
   };
   if constexpr (W > 0) {
-    for (uint32_t jj = J0 + (uint32_t)tid; jj < J1; jj += kThreads) {
+    for (uint32_t jj = J0 + (uint32_t)tid; jj < J1; jj += NT) {
       const int k = source(jj);
       unsigned long long x[W];
 #pragma unroll
@@ -509,7 +523,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_gather(Batch B) {
     }
   } else {
     // one warp per new clone; its lanes copy the lattice words (coalesced)
-    for (uint32_t jj = J0 + (uint32_t)wid; jj < J1; jj += kWarps) {
+    for (uint32_t jj = J0 + (uint32_t)wid; jj < J1; jj += NWARP) {
       const int k = source(jj);
       const int64_t dst = d.off + (int64_t)jj;
       for (int q = lane; q < B.W; q += 32)
