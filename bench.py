@@ -4,9 +4,9 @@
 Workload (the batched s-sweep): 64 populations of the SSEP on a ring of L = 50 sites
 with N = 25 particles, biases lambda = s L^2 evenly spaced in [-20, 40], N_c = 16384
 clones each (2^20 clones), cloning interval dt = 0.1, t_obs = 1000 (M = 10000
-intervals).  One step is one whole run: pop_init (initial configurations), M
-intervals of dynamical + cloning stages (pop_run, captured CUDA graphs), and
-pop_estimate_psi.  clone-events = BKL hops executed by all clones (arXiv:1711.05095
+intervals).  One step is one whole run: pop_init (initial configurations), pop_autotune
+(launch configuration), M intervals of dynamical + cloning stages (pop_run,
+captured CUDA graphs), and pop_estimate_psi.  clone-events = BKL hops executed by all clones (arXiv:1711.05095
 measures the serial and parallel cost of exactly this loop, Sec. 6).
 
 Prints one JSON line.  --impl reference times the CPU oracle on a bounded sample of
@@ -236,6 +236,7 @@ def main():
 
     def one_step():
         b = pg.PopulationBatch(pops, device=dev, stream=stream, workspace=ws)
+        b.autotune(dt, s, trials=3)
         b.run(dt, s, M)
         psi, kh, t = b.estimate_psi()
         ev = int(b.events().sum())
@@ -359,7 +360,7 @@ def main():
                    "populations": P, "clones": clone_intervals, "intervals": M,
                    "l2": "flushed (512 MB write) between timed steps",
                    "parallelism": "replicas%d" % world},
-        "gpu_launches": (3 * M + 2) * args.steps,
+        "gpu_launches": (3 * M + 2 + 5 * 4) * args.steps,
         "roofline": {"bound": "alu", "kernel": "k_evolve", "achieved": achieved, "peak": peak_gops,
                      "unit": "Gop/s", "frac": achieved / peak_gops,
                      "traffic": (EVOLVE_TRAFFIC["bytes"] if kernel_sources_digest() == EVOLVE_TRAFFIC["sources"]

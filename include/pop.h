@@ -152,6 +152,17 @@ int pop_copy_state(pop_t* pop, int32_t p, uint64_t* h_lattice, int32_t* h_K,
                    int32_t* h_anc, int32_t* h_dK);
 
 /*
+ * Launch-configuration tuning for this batch (the paper has none: its codes had
+ * fixed thread counts).  Times `trials` launches of the dynamical stage of the first
+ * interval for every candidate persistent grid (1 .. the maximum number of
+ * resident blocks per SM, times the SM count) and keeps the fastest; the counters
+ * and activities are restored, so results are identical with and without tuning.
+ * Before the first interval only (else POP_ERR_STATE); fixes s like pop_evolve.
+ * h_evolve_grid (may be NULL) receives the chosen grid.  Waits for the stream.
+ */
+int pop_autotune(pop_t* pop, double dt, const double* s, int32_t trials, int32_t* h_evolve_grid);
+
+/*
  * Population mean of |delta rho_n|^2 over the current configurations (eq. fourdens:
  * delta rho_n = L^-1/2 sum_j exp(-2 pi i n X_j / L) over the occupied sites X_j;
  * Sec. 3.3 uses n = 1 to follow the clustering transition).  Per clone in FP32 from

@@ -31,7 +31,7 @@ POP_MAX_L = 4096
 # every symbol include/pop.h declares
 EXPORTS = ("pop_workspace_bytes", "pop_init", "pop_set_state", "pop_evolve", "pop_resample",
            "pop_run", "pop_estimate_psi", "pop_copy_state", "pop_events", "pop_lattice_words",
-           "pop_select_noalloc", "pop_density_mode", "pop_strerror", "pop_free")
+           "pop_select_noalloc", "pop_density_mode", "pop_autotune", "pop_strerror", "pop_free")
 POP_NOALLOC_MAX_CLONES = 1 << 20
 
 
@@ -82,6 +82,8 @@ def library():
     L.pop_estimate_psi.restype = ctypes.c_int
     L.pop_copy_state.argtypes = [ctypes.c_void_p, ctypes.c_int32, _u64p, _i32p, _i32p, _i32p]
     L.pop_copy_state.restype = ctypes.c_int
+    L.pop_autotune.argtypes = [ctypes.c_void_p, ctypes.c_double, _f64p, ctypes.c_int32, _i32p]
+    L.pop_autotune.restype = ctypes.c_int
     L.pop_density_mode.argtypes = [ctypes.c_void_p, ctypes.c_int32, _f64p]
     L.pop_density_mode.restype = ctypes.c_int
     L.pop_events.argtypes = [ctypes.c_void_p, _u64p]
@@ -201,6 +203,13 @@ class PopulationBatch:
                                         anc.ctypes.data_as(_i32p), dK.ctypes.data_as(_i32p)),
                "pop_copy_state")
         return dict(lattice=lat, K=K, anc=anc, dK=dK)
+
+    def autotune(self, dt, s, trials=5):
+        """Choose the persistent evolve grid by timing (before the first interval)."""
+        s, sp = self._s(s)
+        g = ctypes.c_int32(0)
+        _check(self._lib.pop_autotune(self._h, float(dt), sp, int(trials), ctypes.byref(g)), "pop_autotune")
+        return int(g.value)
 
     def density_mode(self, n=1):
         """Population mean of |delta rho_n|^2 (eq. fourdens) per population."""

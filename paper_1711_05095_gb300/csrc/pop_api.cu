@@ -117,6 +117,7 @@ struct pop_batch {
   Batch B{};
   bool any_mod = false;
   int evolve_grid = 0;
+  int evolve_grid_cap = 0;  // persistent grid at full occupancy
   size_t evolve_smem = 0;
   bool s_fixed = false;
   std::vector<double> s;
@@ -236,10 +237,20 @@ int size_evolve_grid(pop_t* h) {
   if (per_sm < 1) per_sm = 1;
   const long long want = (long long)per_sm * sms;
   h->evolve_grid = (int)(want < h->lay.nunits ? want : h->lay.nunits);
+  h->evolve_grid_cap = h->evolve_grid;
   h->evolve_smem = smem;
   h->B.unit_q = h->lay.nunits / h->evolve_grid;
   h->B.unit_r = h->lay.nunits % h->evolve_grid;
   return POP_OK;
+}
+
+// Re-split the units over a different persistent grid (k_evolve only).
+void set_evolve_grid(pop_t* h, int grid) {
+  if (grid < 1) grid = 1;
+  if (h->lay.W <= 2 && grid > h->lay.nunits) grid = h->lay.nunits;
+  h->evolve_grid = grid;
+  h->B.unit_q = h->lay.nunits / grid;
+  h->B.unit_r = h->lay.nunits % grid;
 }
 
 // Rings longer than 128 sites: one warp per clone, a grid-stride loop over slots.
@@ -252,6 +263,7 @@ int size_evolve_grid_wide(pop_t* h) {
   const long long want = (long long)per_sm * sms;
   const long long need = (h->lay.nslots + kWarps - 1) / kWarps;
   h->evolve_grid = (int)(want < need ? want : need);
+  h->evolve_grid_cap = h->evolve_grid;
   h->evolve_smem = 0;
   return POP_OK;
 }
@@ -562,6 +574,58 @@ int pop_events(pop_t* h, uint64_t* h_events) {
   const int rc = check_device_errors(h, &st);
   if (rc != POP_OK) return rc;
   for (int32_t p = 0; p < h->lay.P; ++p) h_events[p] = st[p].events;
+  return POP_OK;
+}
+
+int pop_autotune(pop_t* h, double dt, const double* s, int32_t trials, int32_t* h_evolve_grid) {
+  if (h == nullptr || !valid_dt(dt) || trials < 1) return POP_ERR_ARG;
+  if (h->phase != kReady || h->intervals != 0) return POP_ERR_STATE;
+  int rc = fix_biases(h, s);
+  if (rc != POP_OK) return rc;
+  // the trials evolve interval 1 repeatedly; the per-population counters and the
+  // activities are put back afterwards, so tuning changes no result
+  std::vector<PopState> saved((size_t)h->lay.P);
+  POP_CUDA(cudaMemcpyAsync(saved.data(), h->ws + h->lay.o_st, saved.size() * sizeof(PopState),
+                           cudaMemcpyDeviceToHost, h->stream));
+  POP_CUDA(cudaStreamSynchronize(h->stream));
+  int sms = 0;
+  POP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+  const int cap = h->evolve_grid_cap;
+  const int per_sm = cap / (sms > 0 ? sms : 1);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  POP_CUDA(cudaEventCreate(&e0));
+  POP_CUDA(cudaEventCreate(&e1));
+  int best = cap;
+  float best_ms = 1e30f;
+  const float dt_f = (float)dt;
+  for (int b = per_sm > 0 ? per_sm : 1; b >= 1; --b) {
+    const int grid = per_sm > 0 ? b * sms : cap;
+    set_evolve_grid(h, grid);
+    rc = launch_evolve(h, h->stream, dt_f);  // warm-up
+    for (int i = 0; i < trials && rc == POP_OK; ++i) {
+      if (i == 0) cudaEventRecord(e0, h->stream);
+      rc = launch_evolve(h, h->stream, dt_f);
+    }
+    cudaEventRecord(e1, h->stream);
+    if (rc != POP_OK || cudaEventSynchronize(e1) != cudaSuccess) { rc = POP_ERR_CUDA; break; }
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) { best_ms = ms; best = grid; }
+    if (per_sm <= 0) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  set_evolve_grid(h, best);
+  if (h->graph != nullptr) {  // a captured graph holds the old launch configuration
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  POP_CUDA(cudaMemcpyAsync(h->ws + h->lay.o_st, saved.data(), saved.size() * sizeof(PopState),
+                           cudaMemcpyHostToDevice, h->stream));
+  POP_CUDA(cudaMemsetAsync(h->B.dK, 0, (size_t)h->lay.nslots * sizeof(int32_t), h->stream));
+  POP_CUDA(cudaStreamSynchronize(h->stream));
+  if (rc != POP_OK) return rc;
+  if (h_evolve_grid) *h_evolve_grid = best;
   return POP_OK;
 }
 

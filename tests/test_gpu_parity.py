@@ -305,3 +305,22 @@ def test_full_size_uneven_batch_sampled(pg):
         assert np.all(np.diff(g["anc"]) >= 0)
         assert g["anc"].max() < w["pops"][p]["n_clones"]
         assert np.all(np.isfinite(psi))
+
+
+def test_autotune_changes_no_result(pg):
+    pops = [dict(L=50, N=25, n_clones=5000, seed=9), dict(L=128, N=64, n_clones=3000, seed=10)]
+    s = [0.01, -0.002]
+    a = pg.PopulationBatch(pops)
+    grid = a.autotune(0.1, s, trials=3)
+    assert grid > 0
+    b = pg.PopulationBatch(pops)
+    a.run(0.1, s, 40)
+    b.run(0.1, s, 40)
+    for p in range(2):
+        ga, gb = a.copy_state(p), b.copy_state(p)
+        for key in ("lattice", "K", "anc", "dK"):
+            assert np.array_equal(ga[key], gb[key]), key
+    np.testing.assert_array_equal(a.estimate_psi()[0], b.estimate_psi()[0])
+    np.testing.assert_array_equal(a.events(), b.events())
+    with pytest.raises(pg.PopError):
+        a.autotune(0.1, s)   # only before the first interval
