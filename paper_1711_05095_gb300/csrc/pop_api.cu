@@ -4,13 +4,17 @@
 // caller's workspace.  Layout of the workspace (each region 256-byte aligned):
 //   PopDesc[P]  PopState[P]  tile_pop[ntiles]  wtab[P][4096] u64  qtab, qm1tab[P][4096] f64
 //   inv_rate[P][129] f32  logtab[64] f32x2  hist[P][4096] u32  tile_sum[ntiles] u64  beta  ksum[P]
-//   X, Y lattices [nslots][W] u64   KX, KY, dK, anc [nslots] i32
+//   X[2], Y lattices [nslots][W] u64   KX[2], KY, dK[2], anc [nslots] i32   A[2] [nslots] f32
 // where every population starts on a 1024-slot tile and nslots is the padded total.
 //
-// One interval = k_evolve, k_weights, k_gather on the caller's stream.  pop_run captures
-// kGraphIntervals intervals into a CUDA graph once (on a private capture stream) and
-// replays it on the caller's stream; the kernels read the interval number and every
-// other changing quantity from device memory, so replays need no new arguments.
+// One interval = k_evolve, k_weights, k_gather on the caller's stream.  pop_run fuses
+// the cloning stage of each interval with the dynamical stage of the next where it can
+// (k_gather<FUSE>), captures kGraphIntervals of its repeated part into a CUDA graph once
+// (on a private capture stream) and replays it on the caller's stream; the kernels read
+// the interval number and every other changing quantity from device memory, so replays
+// need no new arguments.  The evolved lattices, K, dK and A are double-buffered by the
+// parity of the interval, so one interval's dynamical stage never overwrites the
+// population its cloning stage is still reading.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -79,13 +83,13 @@ bool make_layout(const pop_params* params, int32_t n_pops, Layout* lay) {
   l.o_tile_sum = take(nt * sizeof(unsigned long long));
   l.o_beta = take(sizeof(unsigned int));
   l.o_ksum = take(P * sizeof(long long));
-  l.o_X = take(ns * (size_t)l.W * sizeof(unsigned long long));
+  l.o_X = take(2 * ns * (size_t)l.W * sizeof(unsigned long long));
   l.o_Y = take(ns * (size_t)l.W * sizeof(unsigned long long));
-  l.o_KX = take(ns * sizeof(int32_t));
+  l.o_KX = take(2 * ns * sizeof(int32_t));
   l.o_KY = take(ns * sizeof(int32_t));
-  l.o_dK = take(ns * sizeof(int32_t));
+  l.o_dK = take(2 * ns * sizeof(int32_t));
   l.o_anc = take(ns * sizeof(int32_t));
-  l.o_A = take(ns * sizeof(float));
+  l.o_A = take(2 * ns * sizeof(float));
   l.o_S = take(ns * sizeof(unsigned long long));
   l.o_cs = take(P * kInvStride * sizeof(float2));
   l.o_tacc = take(nt * sizeof(double));
@@ -213,13 +217,32 @@ int launch_resample(pop_t* h, cudaStream_t st) {
   const unsigned grid = (unsigned)h->lay.ntiles;
   k_weights<<<grid, kThreads, 0, st>>>(h->B);
   constexpr int GT = POP_GATHER_THREADS;
-  if (h->lay.W == 1) k_gather<1, GT><<<grid, GT, 0, st>>>(h->B);
-  else if (h->lay.W == 2) k_gather<2, GT><<<grid, GT, 0, st>>>(h->B);
-  else k_gather<0, GT><<<grid, GT, 0, st>>>(h->B);
+  if (h->lay.W == 1) k_gather<1, GT><<<grid, GT, 0, st>>>(h->B, 0.0f);
+  else if (h->lay.W == 2) k_gather<2, GT><<<grid, GT, 0, st>>>(h->B, 0.0f);
+  else k_gather<0, GT><<<grid, GT, 0, st>>>(h->B, 0.0f);
   if (h->B.any_iid) {
     if (h->lay.W == 1) k_select_iid<1><<<grid, kThreads, 0, st>>>(h->B);
     else if (h->lay.W == 2) k_select_iid<2><<<grid, kThreads, 0, st>>>(h->B);
     else k_select_iid<0><<<grid, kThreads, 0, st>>>(h->B);
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+// pop_run fuses the cloning stage of one interval with the dynamical stage of
+// the next when every population uses [eq] selection on a ring of at most 128 sites.
+bool fusable(const pop_t* h) { return h->lay.W >= 1 && h->lay.W <= 2 && !h->B.any_iid; }
+
+// Cloning stage of the current interval and dynamical stage of the next one.
+int launch_resample_evolve(pop_t* h, cudaStream_t st, float dt_f) {
+  const unsigned grid = (unsigned)h->lay.ntiles;
+  k_weights<<<grid, kThreads, 0, st>>>(h->B);
+  constexpr int GT = POP_GATHER_THREADS;
+  if (h->any_mod) {
+    if (h->lay.W == 1) k_gather<1, GT, true, true><<<grid, GT, 0, st>>>(h->B, dt_f);
+    else k_gather<2, GT, true, true><<<grid, GT, 0, st>>>(h->B, dt_f);
+  } else {
+    if (h->lay.W == 1) k_gather<1, GT, true, false><<<grid, GT, 0, st>>>(h->B, dt_f);
+    else k_gather<2, GT, true, false><<<grid, GT, 0, st>>>(h->B, dt_f);
   }
   return cuda_status(cudaGetLastError());
 }
@@ -354,10 +377,12 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
   std::vector<PopState> st((size_t)n_pops);
   for (PopState& q : st) {
     std::memset(&q, 0, sizeof q);
-    q.dk_min = INT_MAX;
-    q.dk_max = INT_MIN;
-    q.a_min = INT_MAX;
-    q.a_max = INT_MIN;
+    for (int par = 0; par < 2; ++par) {
+      q.dk_min[par] = INT_MAX;
+      q.dk_max[par] = INT_MIN;
+      q.a_min[par] = INT_MAX;
+      q.a_max[par] = INT_MIN;
+    }
   }
   // MODIFIED weight exponential: 2^(i/64)
   std::vector<float> exp2tab(64);
@@ -392,17 +417,21 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
   B.inv_rate = (const float*)(ws + lay.o_inv);
   B.logtab = (const float2*)(ws + lay.o_logtab);
   B.exp2tab = (const float*)(ws + lay.o_exp2);
-  B.A = (float*)(ws + lay.o_A);
+  B.Ab[0] = (float*)(ws + lay.o_A);
+  B.Ab[1] = B.Ab[0] + lay.nslots;
   B.S = (unsigned long long*)(ws + lay.o_S);
   B.hist = (unsigned int*)(ws + lay.o_hist);
   B.tile_sum = (unsigned long long*)(ws + lay.o_tile_sum);
   B.beta = (unsigned int*)(ws + lay.o_beta);
   B.ksum = (long long*)(ws + lay.o_ksum);
-  B.X = (unsigned long long*)(ws + lay.o_X);
+  B.Xb[0] = (unsigned long long*)(ws + lay.o_X);
+  B.Xb[1] = B.Xb[0] + lay.nslots * lay.W;
   B.Y = (unsigned long long*)(ws + lay.o_Y);
-  B.KX = (int32_t*)(ws + lay.o_KX);
+  B.KXb[0] = (int32_t*)(ws + lay.o_KX);
+  B.KXb[1] = B.KXb[0] + lay.nslots;
   B.KY = (int32_t*)(ws + lay.o_KY);
-  B.dK = (int32_t*)(ws + lay.o_dK);
+  B.dKb[0] = (int32_t*)(ws + lay.o_dK);
+  B.dKb[1] = B.dKb[0] + lay.nslots;
   B.anc = (int32_t*)(ws + lay.o_anc);
   B.ntiles = lay.ntiles;
   B.nunits = lay.nunits;
@@ -486,8 +515,22 @@ int pop_run(pop_t* h, double dt, const double* s, int64_t n_intervals) {
   if (rc != POP_OK) return rc;
   if (n_intervals == 0) return POP_OK;
   const float dt_f = (float)dt;
-  int64_t n_graph = n_intervals / kGraphIntervals;
-  const int64_t n_rest = n_intervals % kGraphIntervals;
+  // fused: evolve, then (n - 1) x [weights, gather + next evolve], then weights, gather;
+  // otherwise n x [evolve, weights, gather].  The graph holds kGraphIntervals of the
+  // repeated part.
+  const bool fuse = fusable(h);
+  if (fuse) {
+    rc = launch_evolve(h, h->stream, dt_f);
+    if (rc != POP_OK) return rc;
+  }
+  const int64_t n_rep = fuse ? n_intervals - 1 : n_intervals;
+  const int64_t n_graph = n_rep / kGraphIntervals;
+  const int64_t n_rest = n_rep % kGraphIntervals;
+  auto one = [&](cudaStream_t st) {
+    if (fuse) return launch_resample_evolve(h, st, dt_f);
+    const int lr = launch_evolve(h, st, dt_f);
+    return lr == POP_OK ? launch_resample(h, st) : lr;
+  };
   if (n_graph > 0 && (h->graph == nullptr || h->graph_dt != dt_f)) {
     if (h->graph != nullptr) {
       cudaGraphExecDestroy(h->graph);
@@ -496,10 +539,7 @@ int pop_run(pop_t* h, double dt, const double* s, int64_t n_intervals) {
     cudaGraph_t g = nullptr;
     POP_CUDA(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
     int lr = POP_OK;
-    for (int i = 0; i < kGraphIntervals && lr == POP_OK; ++i) {
-      lr = launch_evolve(h, h->capture_stream, dt_f);
-      if (lr == POP_OK) lr = launch_resample(h, h->capture_stream);
-    }
+    for (int i = 0; i < kGraphIntervals && lr == POP_OK; ++i) lr = one(h->capture_stream);
     const cudaError_t ec = cudaStreamEndCapture(h->capture_stream, &g);
     if (lr != POP_OK || ec != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
@@ -515,8 +555,11 @@ int pop_run(pop_t* h, double dt, const double* s, int64_t n_intervals) {
   }
   for (int64_t i = 0; i < n_graph; ++i) POP_CUDA(cudaGraphLaunch(h->graph, h->stream));
   for (int64_t i = 0; i < n_rest; ++i) {
-    rc = launch_evolve(h, h->stream, dt_f);
-    if (rc == POP_OK) rc = launch_resample(h, h->stream);
+    rc = one(h->stream);
+    if (rc != POP_OK) return rc;
+  }
+  if (fuse) {
+    rc = launch_resample(h, h->stream);
     if (rc != POP_OK) return rc;
   }
   h->intervals += n_intervals;
@@ -551,8 +594,11 @@ int pop_copy_state(pop_t* h, int32_t p, uint64_t* h_lattice, int32_t* h_K, int32
   const PopDesc& d = h->desc[p];
   const int W = h->lay.W;
   const bool evolved = h->phase == kEvolved;
-  const unsigned long long* lat = evolved ? h->B.X : h->B.Y;
-  const int32_t* K = evolved ? h->B.KX : h->B.KY;
+  // the interval most recently evolved and its buffer parity
+  const int64_t last = h->intervals + (evolved ? 1 : 0);
+  const int par = (int)(last & 1);
+  const unsigned long long* lat = evolved ? h->B.Xb[par] : h->B.Y;
+  const int32_t* K = evolved ? h->B.KXb[par] : h->B.KY;
   if (h_lattice)
     POP_CUDA(cudaMemcpyAsync(h_lattice, lat + d.off * W, (size_t)d.nc * W * 8u,
                              cudaMemcpyDeviceToHost, h->stream));
@@ -563,7 +609,7 @@ int pop_copy_state(pop_t* h, int32_t p, uint64_t* h_lattice, int32_t* h_K, int32
     POP_CUDA(cudaMemcpyAsync(h_anc, h->B.anc + d.off, (size_t)d.nc * 4u,
                              cudaMemcpyDeviceToHost, h->stream));
   if (h_dK)
-    POP_CUDA(cudaMemcpyAsync(h_dK, h->B.dK + d.off, (size_t)d.nc * 4u, cudaMemcpyDeviceToHost,
+    POP_CUDA(cudaMemcpyAsync(h_dK, h->B.dKb[par] + d.off, (size_t)d.nc * 4u, cudaMemcpyDeviceToHost,
                              h->stream));
   return check_device_errors(h, nullptr);
 }
@@ -622,7 +668,7 @@ int pop_autotune(pop_t* h, double dt, const double* s, int32_t trials, int32_t* 
   }
   POP_CUDA(cudaMemcpyAsync(h->ws + h->lay.o_st, saved.data(), saved.size() * sizeof(PopState),
                            cudaMemcpyHostToDevice, h->stream));
-  POP_CUDA(cudaMemsetAsync(h->B.dK, 0, (size_t)h->lay.nslots * sizeof(int32_t), h->stream));
+  POP_CUDA(cudaMemsetAsync(h->B.dKb[0], 0, 2 * (size_t)h->lay.nslots * sizeof(int32_t), h->stream));
   POP_CUDA(cudaStreamSynchronize(h->stream));
   if (rc != POP_OK) return rc;
   if (h_evolve_grid) *h_evolve_grid = best;

@@ -67,13 +67,15 @@ struct PopDesc {
 
 // Mutable per population.
 struct PopState {
-  int32_t dk_min, dk_max;      // interval activity range (k_evolve; reset by k_gather)
+  int32_t dk_min[2], dk_max[2];  // interval activity range by interval parity
+                                 // (k_evolve; reset by k_gather of the same interval)
   int32_t kref;                // reference activity of this interval (k_weights)
   uint32_t U;                  // [eq] offset word of this interval (k_weights)
   double psi_acc;              // sum of psi terms (eq. psihat numerator)
   unsigned long long events;   // executed hops since init
   int32_t err;                 // sticky kernel-side error
-  int32_t a_min, a_max;        // MODIFIED: range of the rate integral A (float bits, A >= 0)
+  int32_t a_min[2], a_max[2];  // MODIFIED: range of the rate integral A by interval parity
+                               // (float bits, A >= 0)
   float a_ref;                 // MODIFIED: reference A of this interval (k_weights)
   uint32_t beta;               // interval being resampled (k_weights)
   int32_t pad;
@@ -90,16 +92,16 @@ struct Batch {
   const float* inv_rate;                // [P][kInvStride] float(1/r)
   const float2* logtab;                 // [64] (1/c_i, ln c_i) of the waiting-time log
   const float* exp2tab;                 // [64] 2^(i/64) of the MODIFIED weight exponential
-  float* A;                             // MODIFIED: rate integral of the last interval
+  float* Ab[2];                         // MODIFIED: rate integral, by interval parity
   unsigned long long* S;                // [iid]: exclusive prefix sums of the weights
   unsigned int* hist;                   // [P][kKcap] activity histogram (zero between intervals)
   unsigned long long* tile_sum;         // [ntiles] weight sum of each tile
   unsigned int* beta;                   // interval being evolved (1-based)
-  unsigned long long* X;                // evolved lattices  [slots][W]
+  unsigned long long* Xb[2];            // evolved lattices [slots][W], by interval parity
   unsigned long long* Y;                // population lattices between intervals [slots][W]
-  int32_t* KX;                          // evolved cumulative activity
+  int32_t* KXb[2];                      // evolved cumulative activity, by interval parity
   int32_t* KY;                          // population cumulative activity
-  int32_t* dK;                          // activity of the last interval
+  int32_t* dKb[2];                      // interval activity, by interval parity
   int32_t* anc;                         // ancestors of the last cloning stage
   long long* ksum;                      // [P] sum of K (estimates)
   int32_t ntiles;

@@ -59,7 +59,8 @@ __global__ void __launch_bounds__(kThreads) k_init(Batch B) {
     store_lat<W>(B.Y, slot, x);
   }
   B.KY[slot] = 0;
-  B.dK[slot] = 0;
+  B.dKb[0][slot] = 0;
+  B.dKb[1][slot] = 0;
 }
 
 // Shared-memory state of k_evolve: one chunk of up to kChunk clones.
@@ -125,6 +126,11 @@ __global__ void __launch_bounds__(kThreads, POP_EVOLVE_MIN_BLOCKS) k_evolve(Batc
   EvolveSmem<W>& S = *reinterpret_cast<EvolveSmem<W>*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31;
   const uint32_t beta = *B.beta;
+  const int par = (int)(beta & 1u);
+  unsigned long long* const Xo = B.Xb[par];
+  int32_t* const KXo = B.KXb[par];
+  int32_t* const dKo = B.dKb[par];
+  float* const Ao = B.Ab[par];
   if (tid < 64) S.logtab[tid] = B.logtab[tid];
   // this block's units: an even split of B.nunits over the grid, B.unit_q units each
   // and one more for the first B.unit_r blocks (no divisions on the device)
@@ -263,10 +269,10 @@ __global__ void __launch_bounds__(kThreads, POP_EVOLVE_MIN_BLOCKS) k_evolve(Batc
           unsigned long long xo[W];
 #pragma unroll
           for (int w = 0; w < W; ++w) xo[w] = S.x[i][w];
-          store_lat<W>(B.X, slot, xo);
-          B.KX[slot] = ky[m] + hh;
-          B.dK[slot] = hh;
-          if (MOD) B.A[slot] = S.a[i];
+          store_lat<W>(Xo, slot, xo);
+          KXo[slot] = ky[m] + hh;
+          dKo[slot] = hh;
+          if (MOD) Ao[slot] = S.a[i];
         }
         if (MOD) {
           // A >= 0, so its float bits order like the values
@@ -291,12 +297,12 @@ __global__ void __launch_bounds__(kThreads, POP_EVOLVE_MIN_BLOCKS) k_evolve(Batc
     __syncthreads();
     if (tid < nu && S.u_min[tid] != INT_MAX) {
       PopState* st = B.st + S.u_pop[tid];
-      atomicMin(&st->dk_min, S.u_min[tid]);
-      atomicMax(&st->dk_max, S.u_max[tid]);
+      atomicMin(&st->dk_min[par], S.u_min[tid]);
+      atomicMax(&st->dk_max[par], S.u_max[tid]);
       atomicAdd(&st->events, (unsigned long long)S.u_ev[tid]);
       if (MOD) {
-        atomicMin(&st->a_min, S.u_amin[tid]);
-        atomicMax(&st->a_max, S.u_amax[tid]);
+        atomicMin(&st->a_min[par], S.u_amin[tid]);
+        atomicMax(&st->a_max[par], S.u_amax[tid]);
       }
     }
     __syncthreads();
@@ -319,17 +325,19 @@ __global__ void __launch_bounds__(kThreads) k_weights(Batch B) {
   PopState* st = B.st + p;
   const int64_t base = (int64_t)tile * kTile;
   const int64_t j0 = base - d.off + (int64_t)tid * kItems;
-  const int4 dk4 = reinterpret_cast<const int4*>(B.dK + base)[tid];
+  const uint32_t beta = *B.beta;  // the interval being resampled (no kernel advances it meanwhile)
+  const int par = (int)(beta & 1u);
+  const int4 dk4 = reinterpret_cast<const int4*>(B.dKb[par] + base)[tid];
   float av[kItems] = {0.0f, 0.0f, 0.0f, 0.0f};
   if (d.modified) {
-    const float4 a4 = reinterpret_cast<const float4*>(B.A + base)[tid];
+    const float4 a4 = reinterpret_cast<const float4*>(B.Ab[par] + base)[tid];
     av[0] = a4.x; av[1] = a4.y; av[2] = a4.z; av[3] = a4.w;
   }
   for (int i = tid; i < kHistSmem; i += kThreads) s_hist[i] = 0u;
-  const int dk_min = st->dk_min, dk_max = st->dk_max;
+  const int dk_min = st->dk_min[par], dk_max = st->dk_max[par];
   const int kref = d.s_neg ? dk_max : dk_min;
   // MODIFIED reference: the smallest (s >= 0) or largest (s < 0) rate integral
-  const float a_ref = __int_as_float(d.s_neg ? st->a_max : st->a_min);
+  const float a_ref = __int_as_float(d.s_neg ? st->a_max[par] : st->a_min[par]);
   __syncthreads();
   const int dkv[kItems] = {dk4.x, dk4.y, dk4.z, dk4.w};
   const unsigned long long* wt = B.wtab + (size_t)p * kKcap;
@@ -363,7 +371,6 @@ __global__ void __launch_bounds__(kThreads) k_weights(Batch B) {
   if (tid == 0) {
     B.tile_sum[tile] = total;
     if (tile == d.first_tile) {
-      const uint32_t beta = *B.beta;
       st->kref = kref;
       st->a_ref = a_ref;
       st->beta = beta;
@@ -381,21 +388,37 @@ __global__ void __launch_bounds__(kThreads) k_weights(Batch B) {
 // tile's range is written once, coalesced.  The first tile of each population adds
 // the psi term; the last block advances the interval counter (no block of this
 // kernel reads it).
+//
+// FUSE: the cloning stage of interval beta and the dynamical stage of interval
+// beta + 1 in one pass (pop_run, [eq] populations of at most 128 sites).  Each new
+// clone is taken straight from its staged ancestor and evolved (the same BKL steps,
+// draws and write-back as k_evolve, into the buffers of the other parity), so the
+// population between the two stages never goes through global memory.  Lanes take
+// new slots from a shared counter as their clones end, as in k_evolve.
 // ---------------------------------------------------------------------------
 #ifndef POP_GATHER_THREADS
 #define POP_GATHER_THREADS 128
 #endif
-template <int W, int NT>
-__global__ void __launch_bounds__(NT, NT == 128 ? 11 : 6) k_gather(Batch B) {
+template <int W, int NT, bool FUSE = false, bool MOD = false>
+__global__ void __launch_bounds__(NT, FUSE ? 8 : (NT == 128 ? 11 : 6))
+    k_gather(Batch B, float dt_f) {
   constexpr int NI = kTile / NT;   // old clones per thread
   constexpr int NWARP = NT / 32;
   constexpr int WS = W > 0 ? W : 1;  // W == 0: wide lattices, copied without staging
+  static_assert(!FUSE || W > 0, "the fused stage needs staged lattices");
   __shared__ unsigned long long s_x[W > 0 ? kTile : 1][WS];
   __shared__ int32_t s_K[kTile];
   __shared__ uint32_t s_jlo[kTile + 1];
   __shared__ uint16_t s_src[kMap];
   __shared__ unsigned long long s_red[NWARP];
   __shared__ unsigned long long s_wsum[NWARP];
+  // FUSE only: the population's waiting-time factors, the log table, the slot
+  // counter and the block's activity range of the next interval
+  __shared__ float s_inv[FUSE ? kMaxL + 1 : 1];
+  __shared__ float2 s_logtab[FUSE ? 64 : 1];
+  __shared__ int s_take;
+  __shared__ int s_nmin, s_nmax, s_namin, s_namax;
+  __shared__ unsigned int s_nev;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int tile = blockIdx.x;
   const int p = B.tile_pop[tile];
@@ -405,12 +428,31 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 11 : 6) k_gather(Batch B) {
   const uint32_t nc = (uint32_t)d.nc;
   const int64_t base = (int64_t)tile * kTile;
   const int64_t j0 = base - d.off + (int64_t)tid * NI;
+  // the interval being resampled, as recorded by k_weights: the device counter is
+  // advanced by this kernel's last block and may not be read here
+  const uint32_t beta = st->beta;
+  const int par = (int)(beta & 1u);
+  const unsigned long long* const Xo = B.Xb[par];
+  const int32_t* const KXo = B.KXb[par];
+  if constexpr (FUSE) {
+    const float* src = B.inv_rate + (size_t)p * kInvStride;
+    for (int r = tid; r <= kMaxL; r += NT) s_inv[r] = (r <= d.L) ? src[r] : 0.0f;
+    if (tid < 64) s_logtab[tid] = B.logtab[tid];
+    if (tid == 0) {
+      s_take = 0;
+      s_nmin = INT_MAX;
+      s_nmax = INT_MIN;
+      s_namin = INT_MAX;
+      s_namax = INT_MIN;
+      s_nev = 0u;
+    }
+  }
 
   // independent loads first: activities and the old clones of this tile
   int dkv[NI];
 #pragma unroll
   for (int v = 0; v < NI / 4; ++v) {
-    const int4 dk4 = reinterpret_cast<const int4*>(B.dK + base)[tid * (NI / 4) + v];
+    const int4 dk4 = reinterpret_cast<const int4*>(B.dKb[par] + base)[tid * (NI / 4) + v];
     dkv[4 * v] = dk4.x; dkv[4 * v + 1] = dk4.y; dkv[4 * v + 2] = dk4.z; dkv[4 * v + 3] = dk4.w;
   }
 #pragma unroll
@@ -419,11 +461,11 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 11 : 6) k_gather(Batch B) {
     if (base - d.off + i < d.nc) {
       if constexpr (W > 0) {
         unsigned long long x[W];
-        load_lat<W>(B.X, base + i, x);
+        load_lat<W>(Xo, base + i, x);
 #pragma unroll
         for (int q = 0; q < W; ++q) s_x[i][q] = x[q];
       }
-      s_K[i] = B.KX[base + i];
+      s_K[i] = KXo[base + i];
     }
   }
   float av[NI];
@@ -432,7 +474,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 11 : 6) k_gather(Batch B) {
   if (d.modified) {
 #pragma unroll
     for (int v = 0; v < NI / 4; ++v) {
-      const float4 a4 = reinterpret_cast<const float4*>(B.A + base)[tid * (NI / 4) + v];
+      const float4 a4 = reinterpret_cast<const float4*>(B.Ab[par] + base)[tid * (NI / 4) + v];
       av[4 * v] = a4.x; av[4 * v + 1] = a4.y; av[4 * v + 2] = a4.z; av[4 * v + 3] = a4.w;
     }
   }
@@ -510,7 +552,116 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 11 : 6) k_gather(Batch B) {
     }
     return lo;
   };
-  if constexpr (W > 0) {
+  if constexpr (FUSE) {
+    // dynamical stage of interval beta + 1 for the new slots [J0, J1)
+    const uint32_t beta1 = beta + 1u;
+    const int pn = par ^ 1;
+    unsigned long long* const Xn = B.Xb[pn];
+    int32_t* const KXn = B.KXb[pn];
+    int32_t* const dKn = B.dKb[pn];
+    float* const An = B.Ab[pn];
+    const int n = (int)(J1 - J0);
+    const int L = d.L;
+    const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
+    int c = -1, src_k = 0;  // the lane's new slot (offset from J0) and its ancestor
+    unsigned long long x[W];
+    float t = 0.0f, acc = 0.0f;
+    int h = 0;
+    uint32_t q = 0u;
+    int hmin = INT_MAX, hmax = INT_MIN, amin = INT_MAX, amax = INT_MIN;
+    unsigned int ev = 0u;
+#pragma unroll
+    for (int w = 0; w < W; ++w) x[w] = 0ull;
+    for (;;) {
+      // one read of the counter per warp keeps every branch below warp-uniform
+      int taken = 0;
+      if (lane == 0) taken = *(volatile int*)&s_take;
+      taken = __shfl_sync(0xffffffffu, taken, 0);
+      const bool need = c < 0;
+      const unsigned int m = __ballot_sync(0xffffffffu, need);
+      if (m != 0u && taken < n) {
+        const int leader = __ffs(m) - 1;
+        int base_i = 0;
+        if (lane == leader) base_i = atomicAdd(&s_take, __popc(m));
+        base_i = __shfl_sync(0xffffffffu, base_i, leader);
+        if (need) {
+          const int idx = base_i + __popc(m & ((1u << lane) - 1u));
+          if (idx < n) {
+            c = idx;
+            src_k = source(J0 + (uint32_t)idx);
+#pragma unroll
+            for (int w = 0; w < W; ++w) x[w] = s_x[src_k][w];
+            t = 0.0f;
+            acc = 0.0f;
+            h = 0;
+            q = 0u;
+          }
+        }
+      }
+      if (__ballot_sync(0xffffffffu, c >= 0) == 0u) {
+        if (lane == 0) taken = *(volatile int*)&s_take;
+        if (__shfl_sync(0xffffffffu, taken, 0) >= n) break;
+      }
+      if (c >= 0) {
+        const uint32_t jj = J0 + (uint32_t)c;
+        const uint4 d4 = philox4x32_10(make_uint4(q, beta1, jj, kTagEvolve), k0, k1);
+        bool run = false;
+        if (bkl_step<W, MOD>(x, t, acc, L, s_inv, s_logtab, d4.x, d4.y, dt_f)) {
+          ++h;
+          if (bkl_step<W, MOD>(x, t, acc, L, s_inv, s_logtab, d4.z, d4.w, dt_f)) {
+            ++h;
+            run = true;
+          }
+        }
+        ++q;
+        if (run && q >= kStepLimit / 2u) {  // guard: an interval must end; report, never spin
+          st->err = kErrRange;
+          run = false;
+        }
+        if (!run) {
+          const int64_t dst = d.off + (int64_t)jj;
+          store_lat<W>(Xn, dst, x);
+          KXn[dst] = s_K[src_k] + h;
+          dKn[dst] = h;
+          if (MOD) {
+            An[dst] = acc;
+            amin = min(amin, __float_as_int(acc));  // A >= 0: float bits order like values
+            amax = max(amax, __float_as_int(acc));
+          }
+          hmin = min(hmin, h);
+          hmax = max(hmax, h);
+          ev += (unsigned int)h;
+          c = -1;
+        }
+      }
+    }
+    hmin = __reduce_min_sync(0xffffffffu, hmin);
+    hmax = __reduce_max_sync(0xffffffffu, hmax);
+    ev = __reduce_add_sync(0xffffffffu, ev);
+    if (MOD) {
+      amin = __reduce_min_sync(0xffffffffu, amin);
+      amax = __reduce_max_sync(0xffffffffu, amax);
+    }
+    if (lane == 0 && hmin != INT_MAX) {
+      atomicMin(&s_nmin, hmin);
+      atomicMax(&s_nmax, hmax);
+      atomicAdd(&s_nev, ev);
+      if (MOD) {
+        atomicMin(&s_namin, amin);
+        atomicMax(&s_namax, amax);
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && s_nmin != INT_MAX) {
+      atomicMin(&st->dk_min[pn], s_nmin);
+      atomicMax(&st->dk_max[pn], s_nmax);
+      atomicAdd(&st->events, (unsigned long long)s_nev);
+      if (MOD) {
+        atomicMin(&st->a_min[pn], s_namin);
+        atomicMax(&st->a_max[pn], s_namax);
+      }
+    }
+  } else if constexpr (W > 0) {
     for (uint32_t jj = J0 + (uint32_t)tid; jj < J1; jj += NT) {
       const int k = source(jj);
       unsigned long long x[W];
@@ -527,7 +678,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 11 : 6) k_gather(Batch B) {
       const int k = source(jj);
       const int64_t dst = d.off + (int64_t)jj;
       for (int q = lane; q < B.W; q += 32)
-        B.Y[dst * B.W + q] = B.X[(base + k) * B.W + q];
+        B.Y[dst * B.W + q] = Xo[(base + k) * B.W + q];
       if (lane == 0) {
         B.KY[dst] = s_K[k];
         B.anc[dst] = lt * kTile + k;
@@ -543,15 +694,15 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 11 : 6) k_gather(Batch B) {
     const double base_w = ldexp((double)d.nc, d.F);
     const long long D = (long long)T - (long long)((unsigned long long)d.nc << d.F);
     st->psi_acc += -(double)d.c_f * (double)a_ref + log1p((double)D / base_w);
-    st->dk_min = INT_MAX;
-    st->dk_max = INT_MIN;
-    st->a_min = INT_MAX;
-    st->a_max = INT_MIN;
+    st->dk_min[par] = INT_MAX;
+    st->dk_max[par] = INT_MIN;
+    st->a_min[par] = INT_MAX;
+    st->a_max[par] = INT_MIN;
   }
   // plain: term = -s k_ref + ln( (1/N_c) sum_k n_k exp(-|s| k) ) from the exact
   // activity histogram, the log taken as log1p of the expm1 sum when the mean is > 1/2.
   if (!d.modified && lt == 0 && wid == 0) {
-    const int dk_min = st->dk_min, dk_max = st->dk_max;
+    const int dk_min = st->dk_min[par], dk_max = st->dk_max[par];
     const int R = hist_bins(dk_min, dk_max, kKcap);
     unsigned int* h = B.hist + (size_t)p * kKcap;
     const double* qt = B.qtab + (size_t)p * kKcap;
@@ -572,10 +723,10 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 11 : 6) k_gather(Batch B) {
       const double mean_q = q / ncd;
       const double ln_mean = (mean_q > 0.5) ? log1p(a / ncd) : log(mean_q);
       st->psi_acc += -d.s * (double)kref + ln_mean;
-      st->dk_min = INT_MAX;
-      st->dk_max = INT_MIN;
-      st->a_min = INT_MAX;
-      st->a_max = INT_MIN;
+      st->dk_min[par] = INT_MAX;
+      st->dk_max[par] = INT_MIN;
+      st->a_min[par] = INT_MAX;
+      st->a_max[par] = INT_MIN;
     }
   }
   // the interval ends here unless [iid] selection still has to run
@@ -599,6 +750,9 @@ __global__ void __launch_bounds__(kThreads) k_select_iid(Batch B) {
     const PopState* st = B.st + p;
     const unsigned long long T = st->T;
     const uint32_t beta = st->beta;
+    const int par = (int)(beta & 1u);
+    const unsigned long long* const Xo = B.Xb[par];
+    const int32_t* const KXo = B.KXb[par];
     const int lt = tile - d.first_tile;
     const unsigned long long* S = B.S + d.off;
     const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
@@ -615,14 +769,14 @@ __global__ void __launch_bounds__(kThreads) k_select_iid(Batch B) {
       const int64_t src = d.off + lo, dst = d.off + j;
       if constexpr (W > 0) {
         unsigned long long x[W];
-        load_lat<W>(B.X, src, x);
+        load_lat<W>(Xo, src, x);
         store_lat<W>(B.Y, dst, x);
-        B.KY[dst] = B.KX[src];
+        B.KY[dst] = KXo[src];
         B.anc[dst] = (int32_t)lo;
       } else {
-        for (int q = lane; q < B.W; q += 32) B.Y[dst * B.W + q] = B.X[src * B.W + q];
+        for (int q = lane; q < B.W; q += 32) B.Y[dst * B.W + q] = Xo[src * B.W + q];
         if (lane == 0) {
-          B.KY[dst] = B.KX[src];
+          B.KY[dst] = KXo[src];
           B.anc[dst] = (int32_t)lo;
         }
       }
@@ -706,6 +860,7 @@ __global__ void __launch_bounds__(kThreads) k_evolve_wide(Batch B, float dt_f) {
   if (tid < 64) s_tab[tid] = B.logtab[tid];
   __syncthreads();
   const uint32_t beta = *B.beta;
+  const int par = (int)(beta & 1u);
   const int64_t nwarps = (int64_t)gridDim.x * kWarps;
   for (int64_t slot = (int64_t)blockIdx.x * kWarps + (tid >> 5); slot < B.nslots; slot += nwarps) {
     const int p = B.tile_pop[slot / kTile];
@@ -730,18 +885,18 @@ __global__ void __launch_bounds__(kThreads) k_evolve_wide(Batch B, float dt_f) {
       if (!wide_step<MOD>(xl, xh, t, acc, d.L, lane, inv, s_tab, d4.z, d4.w, dt_f)) break;
       ++h;
     }
-    if (2 * lane < W) B.X[slot * W + 2 * lane] = xl;
-    if (2 * lane + 1 < W) B.X[slot * W + 2 * lane + 1] = xh;
+    if (2 * lane < W) B.Xb[par][slot * W + 2 * lane] = xl;
+    if (2 * lane + 1 < W) B.Xb[par][slot * W + 2 * lane + 1] = xh;
     if (lane == 0) {
-      B.KX[slot] = B.KY[slot] + h;
-      B.dK[slot] = h;
-      atomicMin(&B.st[p].dk_min, h);
-      atomicMax(&B.st[p].dk_max, h);
+      B.KXb[par][slot] = B.KY[slot] + h;
+      B.dKb[par][slot] = h;
+      atomicMin(&B.st[p].dk_min[par], h);
+      atomicMax(&B.st[p].dk_max[par], h);
       atomicAdd(&B.st[p].events, (unsigned long long)h);
       if (MOD) {
-        B.A[slot] = acc;
-        atomicMin(&B.st[p].a_min, __float_as_int(acc));
-        atomicMax(&B.st[p].a_max, __float_as_int(acc));
+        B.Ab[par][slot] = acc;
+        atomicMin(&B.st[p].a_min[par], __float_as_int(acc));
+        atomicMax(&B.st[p].a_max[par], __float_as_int(acc));
       }
     }
   }

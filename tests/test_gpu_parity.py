@@ -108,17 +108,36 @@ def test_parity_long_dt(pg):
     run_parity(pg, [dict(L=50, N=25, n_clones=1500, seed=3)], [0.02], 2.0, 3)
 
 
-def test_run_equals_steps(pg):
-    pops = [dict(L=50, N=25, n_clones=2000, seed=7), dict(L=100, N=40, n_clones=1300, seed=8)]
-    s = [0.01, -0.004]
+RUN_CASES = {
+    # two-word lattices: fused run, two captured graphs of 32 intervals plus direct ones
+    "w2_plain": ([dict(L=50, N=25, n_clones=2000, seed=7), dict(L=100, N=40, n_clones=1300, seed=8)],
+                 [0.01, -0.004], [70]),
+    # one-word lattices, MODIFIED next to plain, a ragged multi-tile population
+    "w1_mixed_weights": ([dict(L=20, N=10, n_clones=2500, seed=11, weight_mode=1),
+                          dict(L=64, N=31, n_clones=1100, seed=12)], [0.3, -0.2], [37]),
+    # two-word MODIFIED, strong bias (many deletions), runs split across calls
+    "w2_modified_split": ([dict(L=100, N=50, n_clones=1500, seed=13, weight_mode=1),
+                           dict(L=33, N=16, n_clones=700, seed=14)], [0.05, 2.5], [1, 33, 2]),
+    # an [iid] population: every interval through the separate kernels
+    "iid_unfused": ([dict(L=30, N=15, n_clones=1200, seed=15, selection=1),
+                     dict(L=50, N=25, n_clones=900, seed=16, weight_mode=1)], [0.1, -0.05], [35]),
+    # a single interval: the fused run's first and last stages only
+    "one_interval": ([dict(L=40, N=20, n_clones=3000, seed=17)], [0.2], [1]),
+}
+
+
+@pytest.mark.parametrize("case", sorted(RUN_CASES))
+def test_run_equals_steps(pg, case):
+    pops, s, splits = RUN_CASES[case]
     a = pg.PopulationBatch(pops)
     b = pg.PopulationBatch(pops)
-    n = 70  # two captured graphs of 32 intervals plus 6 direct intervals
-    a.run(0.1, s, n)
-    for _ in range(n):
+    for n in splits:
+        a.run(0.1, s, n)
+    for _ in range(sum(splits)):
         b.evolve(0.1, s)
         b.resample()
-    for p in range(2):
+    P = len(pops)
+    for p in range(P):
         ga, gb = a.copy_state(p), b.copy_state(p)
         for key in ("lattice", "K", "anc", "dK"):
             assert np.array_equal(ga[key], gb[key]), key
