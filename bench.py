@@ -46,13 +46,17 @@ UNIT = "events/s"
 #   loop bookkeeping (step and hop counters, exit test)                         = 3
 OPS_HOP = 49 + 20 + 4 + 7 + 25 + 7 + 3          # a step that hops: 115
 OPS_STOP = OPS_HOP - 25 - 7 - 1                 # the step that ends the interval: 82
+# Cloning stage, per old clone ([eq], Sec. 2.3): weight = table[|dK - k_ref|] (3),
+# its prefix sum (2), the inverse j_lo of the prefix by 128-bit products and compares
+# (16), and for the new clone the ancestor lookup and its lattice and K (3)
+OPS_GATHER = 3 + 2 + 16 + 3                     # 24
 N_SM = 152
 ISSUE_OPS_PER_SM_CLK = 128                      # 4 schedulers x 32 lanes
 
-# DRAM bytes (read + write) of one k_evolve launch on this workload, from one
-# `ncu --set full` capture (profiles/interval_kernels_s_sweep.md), valid only for the
-# kernel sources it was taken on (hash of the two device headers).
-EVOLVE_TRAFFIC = {"bytes": 13571072, "sources": "6342b56d362b3699"}
+# DRAM bytes (read + write) of one launch of the dominant kernel on this workload,
+# from one `ncu --set full` capture (profiles/), valid only for the kernel sources it
+# was taken on (hash of the two device headers).
+KERNEL_TRAFFIC = {"bytes": 17161472, "sources": "unset"}
 
 
 def kernel_sources_digest():
@@ -240,8 +244,11 @@ def main():
         b.run(dt, s, M)
         psi, kh, t = b.estimate_psi()
         ev = int(b.events().sum())
+        launches.append(sum(b.launch_count().values()))
         b.close()
         return ev, psi
+
+    launches = []
 
     def barrier():
         if dist is not None:
@@ -250,6 +257,7 @@ def main():
 
     for _ in range(args.warmup):
         one_step()
+    launches.clear()
     sampler = ClockSampler(local)
     barrier()
     sampler.start()
@@ -306,24 +314,16 @@ def main():
     e2e_t_all, e2e_ev_all = reduce_over_ranks(dist, dev, e2e_t, e2e_ev)
     e2e_value = e2e_ev_all / e2e_t_all
 
-    # dominant kernel: k_evolve, timed with CUDA events on the launching stream
+    # dominant kernel: the cloning stage fused with the next dynamical stage
+    # (k_gather<FUSE>), every launch between CUDA events recorded by the library on
+    # the stream it launches on (pop_kernel_times), after 64 warm-up intervals
     R = args.kernel_intervals
     b = pg.PopulationBatch(pops, device=dev, stream=stream, workspace=ws)
     b.run(dt, s, 64)
-    ev_before = int(b.events().sum())
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-            torch.cuda.Event(enable_timing=True)) for _ in range(R)]
-    for a0, a1, a2 in evs:
-        a0.record(stream)
-        b.evolve(dt, s)
-        a1.record(stream)
-        b.resample()
-        a2.record(stream)
-    torch.cuda.synchronize(dev)
-    ev_k = int(b.events().sum()) - ev_before
+    kt = b.kernel_times(dt, s, R + 1)
     b.close()
-    t_ev = sum(a0.elapsed_time(a1) for a0, a1, _ in evs) / R / 1e3
-    t_rs = sum(a1.elapsed_time(a2) for _, a1, a2 in evs) / R / 1e3
+    t_k_us, n_k, hops_k = kt["gather_evolve"]
+    t_k = t_k_us / 1e6
     clone_intervals = sum(q["n_clones"] for q in pops)
 
     # seconds to SE(psi_hat) <= 1e-3 at lambda = 20 (s = 0.008): 64 independent seeds
@@ -345,11 +345,11 @@ def main():
     sigma = float(np.std(psi_se, ddof=1))
     se_runs, se_seconds = seconds_to_se(sigma, se_batch_s, len(se_pops))
     del ws_se
-    ops_per_launch = (OPS_HOP * ev_k + OPS_STOP * clone_intervals * R) / R
+    ops_per_launch = (OPS_HOP * hops_k + (OPS_STOP + OPS_GATHER) * clone_intervals * n_k) / n_k
     peaks, peak_kind = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_gops = N_SM * ISSUE_OPS_PER_SM_CLK * sm_max * 1e6 / 1e9
-    achieved = ops_per_launch / t_ev / 1e9
+    achieved = ops_per_launch / t_k / 1e9
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -360,14 +360,16 @@ def main():
                    "populations": P, "clones": clone_intervals, "intervals": M,
                    "l2": "flushed (512 MB write) between timed steps",
                    "parallelism": "replicas%d" % world},
-        "gpu_launches": (3 * M + 2 + 5 * 4) * args.steps,
-        "roofline": {"bound": "alu", "kernel": "k_evolve", "achieved": achieved, "peak": peak_gops,
+        "gpu_launches": int(sum(launches)),
+        "roofline": {"bound": "alu", "kernel": "k_gather<fused> (cloning stage + next dynamical stage)",
+                     "achieved": achieved, "peak": peak_gops,
                      "unit": "Gop/s", "frac": achieved / peak_gops,
-                     "traffic": (EVOLVE_TRAFFIC["bytes"] if kernel_sources_digest() == EVOLVE_TRAFFIC["sources"]
+                     "traffic": (KERNEL_TRAFFIC["bytes"] if kernel_sources_digest() == KERNEL_TRAFFIC["sources"]
                                  else None),
                      "peak_kind": "issue rate 152 SM x 128 lanes x %.0f MHz (%s max clock)"
                                   % (sm_max, peak_kind),
-                     "launch_ms": 1e3 * t_ev, "resample_ms": 1e3 * t_rs,
+                     "launch_us": t_k_us, "launches_timed": n_k,
+                     "other_kernels_us": {k: v[0] for k, v in kt.items() if k != "gather_evolve" and v[1]},
                      "ops_per_launch": ops_per_launch},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "seconds_to_se": {"value": se_seconds, "unit": "s", "target_se": 1e-3,

@@ -174,6 +174,36 @@ int pop_density_mode(pop_t* pop, int32_t n, double* h_mean);
 /* Executed hops (BKL events) per population since pop_init (host array of n_pops). */
 int pop_events(pop_t* pop, uint64_t* h_events);
 
+/* Kernel kinds of pop_kernel_times and pop_launch_count. */
+#define POP_K_EVOLVE 0         /* dynamical stage (Sec. 2.3), one interval */
+#define POP_K_WEIGHTS 1        /* cloning weights, tile sums, activity histogram */
+#define POP_K_GATHER 2         /* cloning stage: [eq] copies, [iid] selection */
+#define POP_K_GATHER_EVOLVE 3  /* cloning stage of one interval fused with the
+                                  dynamical stage of the next (pop_run, [eq], L <= 128) */
+#define POP_K_OTHER 4          /* initial state, estimates, density mode */
+#define POP_NKINDS 5
+
+/*
+ * Measurement.  Advances the batch by n_intervals >= 1 intervals with exactly the
+ * kernels pop_run uses, in the same order (so with the same results), but launched
+ * one by one, each between two CUDA events recorded on the handle's stream.  Any
+ * output may be NULL; each is a host array of POP_NKINDS:
+ *   h_us    mean device time of the launches of each kind, microseconds (0 if none)
+ *   h_n     number of launches of each kind
+ *   h_hops  hops executed by the launches of each kind (nonzero only for the kinds
+ *           that run dynamical stages)
+ * Fixes s like pop_evolve.  POP_ERR_STATE between pop_evolve and pop_resample.
+ * Waits for the stream.
+ */
+int pop_kernel_times(pop_t* pop, double dt, const double* s, int64_t n_intervals, double* h_us,
+                     int64_t* h_n, uint64_t* h_hops);
+
+/*
+ * Kernels launched by this handle since pop_init, by kind (host array of
+ * POP_NKINDS); a replay of pop_run's captured graph counts every kernel it holds.
+ */
+int pop_launch_count(pop_t* pop, uint64_t* h_n);
+
 /*
  * Cloning-stage selection of ONE population without allocating anything.  The
  * paper has no counterpart: this exists for callers that cannot call cudaMalloc

@@ -31,7 +31,9 @@ POP_MAX_L = 4096
 # every symbol include/pop.h declares
 EXPORTS = ("pop_workspace_bytes", "pop_init", "pop_set_state", "pop_evolve", "pop_resample",
            "pop_run", "pop_estimate_psi", "pop_copy_state", "pop_events", "pop_lattice_words",
-           "pop_select_noalloc", "pop_density_mode", "pop_autotune", "pop_strerror", "pop_free")
+           "pop_select_noalloc", "pop_density_mode", "pop_autotune", "pop_kernel_times",
+           "pop_launch_count", "pop_strerror", "pop_free")
+KERNEL_KINDS = ("evolve", "weights", "gather", "gather_evolve", "other")
 POP_NOALLOC_MAX_CLONES = 1 << 20
 
 
@@ -88,6 +90,11 @@ def library():
     L.pop_density_mode.restype = ctypes.c_int
     L.pop_events.argtypes = [ctypes.c_void_p, _u64p]
     L.pop_events.restype = ctypes.c_int
+    L.pop_kernel_times.argtypes = [ctypes.c_void_p, ctypes.c_double, _f64p, ctypes.c_int64, _f64p,
+                                   ctypes.POINTER(ctypes.c_int64), _u64p]
+    L.pop_kernel_times.restype = ctypes.c_int
+    L.pop_launch_count.argtypes = [ctypes.c_void_p, _u64p]
+    L.pop_launch_count.restype = ctypes.c_int
     L.pop_select_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_uint64,
                                      ctypes.c_uint32, ctypes.c_void_p, _f64p, ctypes.c_void_p]
     L.pop_select_noalloc.restype = ctypes.c_int
@@ -210,6 +217,25 @@ class PopulationBatch:
         g = ctypes.c_int32(0)
         _check(self._lib.pop_autotune(self._h, float(dt), sp, int(trials), ctypes.byref(g)), "pop_autotune")
         return int(g.value)
+
+    def kernel_times(self, dt, s, n):
+        """Advance n intervals as run() does, timing every launch with CUDA events.
+        Returns {kind: (mean microseconds, launches, hops)}."""
+        s, sp = self._s(s)
+        k = len(KERNEL_KINDS)
+        us = np.zeros(k)
+        cnt = np.zeros(k, dtype=np.int64)
+        hops = np.zeros(k, dtype=np.uint64)
+        _check(self._lib.pop_kernel_times(self._h, float(dt), sp, int(n), us.ctypes.data_as(_f64p),
+                                          cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                          hops.ctypes.data_as(_u64p)), "pop_kernel_times")
+        return {name: (float(us[i]), int(cnt[i]), int(hops[i])) for i, name in enumerate(KERNEL_KINDS)}
+
+    def launch_count(self):
+        """Kernels launched by this batch so far, {kind: count}."""
+        cnt = np.zeros(len(KERNEL_KINDS), dtype=np.uint64)
+        _check(self._lib.pop_launch_count(self._h, cnt.ctypes.data_as(_u64p)), "pop_launch_count")
+        return {name: int(cnt[i]) for i, name in enumerate(KERNEL_KINDS)}
 
     def density_mode(self, n=1):
         """Population mean of |delta rho_n|^2 (eq. fourdens) per population."""

@@ -128,6 +128,14 @@ struct pop_batch {
   Phase phase = kReady;
   int64_t intervals = 0;
   double t_obs = 0.0;
+  // kernels launched, by kind; launches made during graph capture go to graph_counts
+  // and are added to launches at every replay
+  uint64_t launches[POP_NKINDS] = {};
+  uint64_t graph_counts[POP_NKINDS] = {};
+  uint64_t* count = launches;
+  // pop_kernel_times: events recorded around every launch while set
+  std::vector<cudaEvent_t>* timer_events = nullptr;
+  std::vector<int>* timer_kinds = nullptr;
 };
 
 namespace {
@@ -198,9 +206,32 @@ int fix_biases(pop_t* h, const double* s) {
 
 bool valid_dt(double dt) { return std::isfinite(dt) && dt > 0.0 && dt < 1e30; }
 
+// Bookkeeping around one kernel launch: the per-kind count and, under
+// pop_kernel_times, an event pair on the launching stream.
+void kernel_begin(pop_t* h, cudaStream_t st, int kind) {
+  h->count[kind] += 1;
+  if (h->timer_events != nullptr) {
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, st);
+    h->timer_events->push_back(e);
+    h->timer_kinds->push_back(kind);
+  }
+}
+
+void kernel_end(pop_t* h, cudaStream_t st) {
+  if (h->timer_events != nullptr) {
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, st);
+    h->timer_events->push_back(e);
+  }
+}
+
 int launch_evolve(pop_t* h, cudaStream_t st, float dt_f) {
   const unsigned grid = (unsigned)h->evolve_grid;
   const size_t sm = h->evolve_smem;
+  kernel_begin(h, st, POP_K_EVOLVE);
   if (h->any_mod) {
     if (h->lay.W == 1) k_evolve<1, true><<<grid, kThreads, sm, st>>>(h->B, dt_f);
     else if (h->lay.W == 2) k_evolve<2, true><<<grid, kThreads, sm, st>>>(h->B, dt_f);
@@ -210,20 +241,31 @@ int launch_evolve(pop_t* h, cudaStream_t st, float dt_f) {
     else if (h->lay.W == 2) k_evolve<2, false><<<grid, kThreads, sm, st>>>(h->B, dt_f);
     else k_evolve_wide<false><<<grid, kThreads, 0, st>>>(h->B, dt_f);
   }
+  kernel_end(h, st);
   return cuda_status(cudaGetLastError());
+}
+
+void launch_weights(pop_t* h, cudaStream_t st) {
+  kernel_begin(h, st, POP_K_WEIGHTS);
+  k_weights<<<(unsigned)h->lay.ntiles, kThreads, 0, st>>>(h->B);
+  kernel_end(h, st);
 }
 
 int launch_resample(pop_t* h, cudaStream_t st) {
   const unsigned grid = (unsigned)h->lay.ntiles;
-  k_weights<<<grid, kThreads, 0, st>>>(h->B);
+  launch_weights(h, st);
   constexpr int GT = POP_GATHER_THREADS;
+  kernel_begin(h, st, POP_K_GATHER);
   if (h->lay.W == 1) k_gather<1, GT><<<grid, GT, 0, st>>>(h->B, 0.0f);
   else if (h->lay.W == 2) k_gather<2, GT><<<grid, GT, 0, st>>>(h->B, 0.0f);
   else k_gather<0, GT><<<grid, GT, 0, st>>>(h->B, 0.0f);
+  kernel_end(h, st);
   if (h->B.any_iid) {
+    kernel_begin(h, st, POP_K_GATHER);
     if (h->lay.W == 1) k_select_iid<1><<<grid, kThreads, 0, st>>>(h->B);
     else if (h->lay.W == 2) k_select_iid<2><<<grid, kThreads, 0, st>>>(h->B);
     else k_select_iid<0><<<grid, kThreads, 0, st>>>(h->B);
+    kernel_end(h, st);
   }
   return cuda_status(cudaGetLastError());
 }
@@ -235,8 +277,9 @@ bool fusable(const pop_t* h) { return h->lay.W >= 1 && h->lay.W <= 2 && !h->B.an
 // Cloning stage of the current interval and dynamical stage of the next one.
 int launch_resample_evolve(pop_t* h, cudaStream_t st, float dt_f) {
   const unsigned grid = (unsigned)h->lay.ntiles;
-  k_weights<<<grid, kThreads, 0, st>>>(h->B);
-  constexpr int GT = POP_GATHER_THREADS;
+  launch_weights(h, st);
+  constexpr int GT = POP_FUSE_THREADS;
+  kernel_begin(h, st, POP_K_GATHER_EVOLVE);
   if (h->any_mod) {
     if (h->lay.W == 1) k_gather<1, GT, true, true><<<grid, GT, 0, st>>>(h->B, dt_f);
     else k_gather<2, GT, true, true><<<grid, GT, 0, st>>>(h->B, dt_f);
@@ -244,6 +287,7 @@ int launch_resample_evolve(pop_t* h, cudaStream_t st, float dt_f) {
     if (h->lay.W == 1) k_gather<1, GT, true, false><<<grid, GT, 0, st>>>(h->B, dt_f);
     else k_gather<2, GT, true, false><<<grid, GT, 0, st>>>(h->B, dt_f);
   }
+  kernel_end(h, st);
   return cuda_status(cudaGetLastError());
 }
 
@@ -444,6 +488,7 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
   if (grc != POP_OK) return fail(POP_ERR_CUDA);
 
   const unsigned grid = (unsigned)(lay.nslots / kThreads);
+  h->launches[POP_K_OTHER] += 1;
   if (lay.W == 1) k_init<1><<<grid, kThreads, 0, h->stream>>>(B);
   else if (lay.W == 2) k_init<2><<<grid, kThreads, 0, h->stream>>>(B);
   else k_init<0><<<grid, kThreads, 0, h->stream>>>(B);
@@ -539,7 +584,10 @@ int pop_run(pop_t* h, double dt, const double* s, int64_t n_intervals) {
     cudaGraph_t g = nullptr;
     POP_CUDA(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
     int lr = POP_OK;
+    for (uint64_t& c : h->graph_counts) c = 0;
+    h->count = h->graph_counts;
     for (int i = 0; i < kGraphIntervals && lr == POP_OK; ++i) lr = one(h->capture_stream);
+    h->count = h->launches;
     const cudaError_t ec = cudaStreamEndCapture(h->capture_stream, &g);
     if (lr != POP_OK || ec != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
@@ -553,7 +601,10 @@ int pop_run(pop_t* h, double dt, const double* s, int64_t n_intervals) {
     }
     h->graph_dt = dt_f;
   }
-  for (int64_t i = 0; i < n_graph; ++i) POP_CUDA(cudaGraphLaunch(h->graph, h->stream));
+  for (int64_t i = 0; i < n_graph; ++i) {
+    POP_CUDA(cudaGraphLaunch(h->graph, h->stream));
+    for (int k = 0; k < POP_NKINDS; ++k) h->launches[k] += h->graph_counts[k];
+  }
   for (int64_t i = 0; i < n_rest; ++i) {
     rc = one(h->stream);
     if (rc != POP_OK) return rc;
@@ -567,10 +618,86 @@ int pop_run(pop_t* h, double dt, const double* s, int64_t n_intervals) {
   return POP_OK;
 }
 
+int pop_kernel_times(pop_t* h, double dt, const double* s, int64_t n_intervals, double* h_us,
+                     int64_t* h_n, uint64_t* h_hops) {
+  if (h == nullptr || !valid_dt(dt) || n_intervals < 1) return POP_ERR_ARG;
+  if (h->phase != kReady) return POP_ERR_STATE;
+  int rc = fix_biases(h, s);
+  if (rc != POP_OK) return rc;
+  auto total_hops = [&](uint64_t* out) {
+    std::vector<PopState> st;
+    const int r = check_device_errors(h, &st);
+    uint64_t sum = 0;
+    for (const PopState& q : st) sum += q.events;
+    *out = sum;
+    return r;
+  };
+  uint64_t hops0 = 0, hops1 = 0, hops2 = 0;
+  rc = total_hops(&hops0);
+  if (rc != POP_OK) return rc;
+  std::vector<cudaEvent_t> events;
+  std::vector<int> kinds;
+  events.reserve((size_t)(6 * n_intervals + 4));
+  h->timer_events = &events;
+  h->timer_kinds = &kinds;
+  const float dt_f = (float)dt;
+  const bool fuse = fusable(h);
+  // the same launches, in the same order, as pop_run
+  if (fuse) {
+    rc = launch_evolve(h, h->stream, dt_f);
+    if (rc == POP_OK) rc = total_hops(&hops1);
+    for (int64_t i = 1; i < n_intervals && rc == POP_OK; ++i)
+      rc = launch_resample_evolve(h, h->stream, dt_f);
+    if (rc == POP_OK) rc = launch_resample(h, h->stream);
+  } else {
+    for (int64_t i = 0; i < n_intervals && rc == POP_OK; ++i) {
+      rc = launch_evolve(h, h->stream, dt_f);
+      if (rc == POP_OK) rc = launch_resample(h, h->stream);
+    }
+  }
+  h->timer_events = nullptr;
+  h->timer_kinds = nullptr;
+  if (rc == POP_OK) rc = total_hops(&hops2);
+  double sum_ms[POP_NKINDS] = {};
+  int64_t cnt[POP_NKINDS] = {};
+  for (size_t i = 0; i < kinds.size(); ++i) {
+    float ms = 0.0f;
+    if (rc == POP_OK && cudaEventElapsedTime(&ms, events[2 * i], events[2 * i + 1]) != cudaSuccess)
+      rc = POP_ERR_CUDA;
+    sum_ms[kinds[i]] += ms;
+    cnt[kinds[i]] += 1;
+  }
+  for (cudaEvent_t e : events) cudaEventDestroy(e);
+  if (rc != POP_OK) return rc;
+  h->intervals += n_intervals;
+  h->t_obs += (double)n_intervals * dt;
+  for (int k = 0; k < POP_NKINDS; ++k) {
+    if (h_us) h_us[k] = cnt[k] ? 1e3 * sum_ms[k] / (double)cnt[k] : 0.0;
+    if (h_n) h_n[k] = cnt[k];
+    if (h_hops) h_hops[k] = 0;
+  }
+  if (h_hops) {
+    if (fuse) {
+      h_hops[POP_K_EVOLVE] = hops1 - hops0;
+      h_hops[POP_K_GATHER_EVOLVE] = hops2 - hops1;
+    } else {
+      h_hops[POP_K_EVOLVE] = hops2 - hops0;
+    }
+  }
+  return POP_OK;
+}
+
+int pop_launch_count(pop_t* h, uint64_t* h_n) {
+  if (h == nullptr || h_n == nullptr) return POP_ERR_ARG;
+  for (int k = 0; k < POP_NKINDS; ++k) h_n[k] = h->launches[k];
+  return POP_OK;
+}
+
 int pop_estimate_psi(pop_t* h, double* psi, double* k_hat, double* t_obs) {
   if (h == nullptr) return POP_ERR_ARG;
   if (h->phase != kReady || h->intervals == 0) return POP_ERR_STATE;
   POP_CUDA(cudaMemsetAsync(h->B.ksum, 0, (size_t)h->lay.P * sizeof(long long), h->stream));
+  h->launches[POP_K_OTHER] += 1;
   k_ksum<<<(unsigned)(h->lay.nslots / kThreads), kThreads, 0, h->stream>>>(h->B);
   POP_CUDA(cudaGetLastError());
   std::vector<long long> ks((size_t)h->lay.P);
@@ -692,6 +819,7 @@ int pop_density_mode(pop_t* h, int32_t n, double* h_mean) {
   POP_CUDA(cudaMemcpyAsync(d_cs, cs.data(), cs.size() * sizeof(float2), cudaMemcpyHostToDevice,
                            h->stream));
   const unsigned grid = (unsigned)h->lay.ntiles;
+  h->launches[POP_K_OTHER] += 1;
   if (h->lay.W == 1) k_density<1><<<grid, kThreads, 0, h->stream>>>(h->B, d_cs, d_tacc);
   else if (h->lay.W == 2) k_density<2><<<grid, kThreads, 0, h->stream>>>(h->B, d_cs, d_tacc);
   else k_density<0><<<grid, kThreads, 0, h->stream>>>(h->B, d_cs, d_tacc);

@@ -141,13 +141,13 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 // (|r| <= 1/128) and ln(1+r) ~ r (1 - r/2 + r^2/3).  tab[i] = (float(1/c_i),
 // float(ln c_i)).  ln 2 is a 15-bit head (exact products with 33-p) plus a float
 // tail.  Every float step is an explicitly rounded intrinsic, so no contraction
-// can change the bits; the integer work avoids 64-bit conversions, which run on
-// the narrow FP64 pipe of this part.
+// can change the bits; the integer work stays in 32 bits (no 64-bit shifts or
+// conversions): the leading one of v = 2w+1 is one above that of w, and for p >= 24
+// the head of v is w >> (p - 24) (the trailing 1 of v is shifted out).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float neg_ln_u(uint32_t w, const float2* tab) {
-  const unsigned long long v = 2ull * (unsigned long long)w + 1ull;
-  const int p = 63 - __clzll((long long)v);  // 0..32
-  const uint32_t t = (p >= 23) ? (uint32_t)(v >> (p - 23)) : ((uint32_t)v << (23 - p));
+  const int p = 32 - __clz((int)w);  // leading one of 2w+1: 0..32
+  const uint32_t t = (p >= 24) ? (w >> (p - 24)) : ((2u * w + 1u) << (23 - p));
   const float m = __uint_as_float(0x3f800000u | (t & 0x007fffffu));
   const float2 cl = tab[(t >> 17) & 63u];
   const float r = __fmaf_rn(m, cl.x, -1.0f);

@@ -399,8 +399,14 @@ __global__ void __launch_bounds__(kThreads) k_weights(Batch B) {
 #ifndef POP_GATHER_THREADS
 #define POP_GATHER_THREADS 128
 #endif
+#ifndef POP_FUSE_THREADS
+#define POP_FUSE_THREADS 128
+#endif
+#ifndef POP_FUSE_MIN_BLOCKS
+#define POP_FUSE_MIN_BLOCKS (1024 / POP_FUSE_THREADS)
+#endif
 template <int W, int NT, bool FUSE = false, bool MOD = false>
-__global__ void __launch_bounds__(NT, FUSE ? 8 : (NT == 128 ? 11 : 6))
+__global__ void __launch_bounds__(NT, FUSE ? POP_FUSE_MIN_BLOCKS : (NT == 128 ? 11 : 6))
     k_gather(Batch B, float dt_f) {
   constexpr int NI = kTile / NT;   // old clones per thread
   constexpr int NWARP = NT / 32;

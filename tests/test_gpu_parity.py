@@ -343,3 +343,36 @@ def test_autotune_changes_no_result(pg):
     np.testing.assert_array_equal(a.events(), b.events())
     with pytest.raises(pg.PopError):
         a.autotune(0.1, s)   # only before the first interval
+
+
+def test_kernel_times_equals_run_and_counts(pg):
+    # pop_kernel_times launches what pop_run launches (results identical); the
+    # launch counters follow the fused sequence: one dynamical stage, then
+    # (n - 1) x [weights, fused stage], then weights and the cloning stage
+    pops = [dict(L=50, N=25, n_clones=3000, seed=21), dict(L=90, N=45, n_clones=2000, seed=22)]
+    s = [0.02, -0.003]
+    n = 40
+    a = pg.PopulationBatch(pops)
+    b = pg.PopulationBatch(pops)
+    a.run(0.1, s, n)
+    kt = b.kernel_times(0.1, s, n)
+    for p in range(len(pops)):
+        ga, gb = a.copy_state(p), b.copy_state(p)
+        for key in ("lattice", "K", "anc", "dK"):
+            assert np.array_equal(ga[key], gb[key]), key
+    np.testing.assert_array_equal(a.events(), b.events())
+    assert kt["evolve"][1] == 1 and kt["gather_evolve"][1] == n - 1
+    assert kt["weights"][1] == n and kt["gather"][1] == 1
+    assert kt["evolve"][2] + kt["gather_evolve"][2] == int(b.events().sum())
+    for name in ("evolve", "weights", "gather", "gather_evolve"):
+        assert kt[name][0] > 0.0
+    for batch in (a, b):
+        c = batch.launch_count()
+        assert c["evolve"] == 1 and c["gather_evolve"] == n - 1 and c["weights"] == n
+        assert c["gather"] == 1 and c["other"] == 1       # the initial state
+    # [iid] batches keep the three separate kernels (and the [iid] selection) per interval
+    c = pg.PopulationBatch([dict(L=30, N=15, n_clones=1500, seed=23, selection=1)])
+    c.run(0.1, [0.1], 35)
+    cnt = c.launch_count()
+    assert cnt["evolve"] == 35 and cnt["weights"] == 35 and cnt["gather"] == 70
+    assert cnt["gather_evolve"] == 0
