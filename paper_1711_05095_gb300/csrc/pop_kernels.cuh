@@ -80,9 +80,10 @@ struct EvolveSmem {
   int take;                         // next unclaimed clone of the chunk
 };
 
-// One BKL step (Sec. 4 BKL; Sec. 3.1 rates 1 per possible hop) with the step's two
-// words (wa, wb): r = active bonds (escape rate; r = 0 ends the interval);
-// tau = E(wa) * float(1/r); t_new = t + tau; t_new >= dt ends the interval (the
+// One BKL step (Sec. 4 BKL; Sec. 3.1 rates 1 per possible hop) with the step's
+// exponential variate E = -ln u(wa) and bond word wb: r = active bonds (escape rate;
+// r = 0 ends the interval); tau = E * float(1/r); t_new = t + tau; t_new >= dt ends
+// the interval (the
 // residual waiting time is dropped, as the exponential law's memorylessness
 // allows); otherwise hop across the floor(wb r / 2^32)-th active bond.
 // Returns true if the clone hopped (and is still running).
@@ -91,13 +92,12 @@ struct EvolveSmem {
 // A <- fma(r, dt - t, A) for the last segment.
 template <int W, bool MOD>
 __device__ __forceinline__ bool bkl_step(unsigned long long (&x)[W], float& t, float& acc, int L,
-                                         const float* inv, const float2* tab, uint32_t wa,
-                                         uint32_t wb, float dt_f) {
+                                         const float* inv, float E, uint32_t wb, float dt_f) {
   unsigned long long a[W];
   active_bonds<W>(x, L, a);
   const int r = popc_lat<W>(a);
   if (r == 0) return false;
-  const float tau = __fmul_rn(neg_ln_u(wa, tab), inv[r]);
+  const float tau = __fmul_rn(E, inv[r]);
   const float t_new = __fadd_rn(t, tau);
   if (t_new >= dt_f) {
     if (MOD) acc = __fmaf_rn((float)r, __fsub_rn(dt_f, t), acc);
@@ -233,10 +233,13 @@ __global__ void __launch_bounds__(kThreads, POP_EVOLVE_MIN_BLOCKS) k_evolve(Batc
       }
       if (c >= 0) {
         const uint4 d4 = philox4x32_10(make_uint4(q, beta, j, kTagEvolve), key.x, key.y);
+        // both waiting-time variates up front: independent of the lattice, so the two
+        // logarithms overlap
+        const float E1 = neg_ln_u(d4.x, S.logtab), E2 = neg_ln_u(d4.z, S.logtab);
         bool run = false;
-        if (bkl_step<W, MOD>(x, t, acc, L, inv, S.logtab, d4.x, d4.y, dt_f)) {
+        if (bkl_step<W, MOD>(x, t, acc, L, inv, E1, d4.y, dt_f)) {
           ++h;
-          if (bkl_step<W, MOD>(x, t, acc, L, inv, S.logtab, d4.z, d4.w, dt_f)) {
+          if (bkl_step<W, MOD>(x, t, acc, L, inv, E2, d4.w, dt_f)) {
             ++h;
             run = true;
           }
@@ -403,7 +406,7 @@ __global__ void __launch_bounds__(kThreads) k_weights(Batch B) {
 #define POP_FUSE_THREADS 128
 #endif
 #ifndef POP_FUSE_MIN_BLOCKS
-#define POP_FUSE_MIN_BLOCKS (1024 / POP_FUSE_THREADS)
+#define POP_FUSE_MIN_BLOCKS 7  // 64 + 8 registers; a wave of 1024 tiles needs 6.7 blocks/SM
 #endif
 template <int W, int NT, bool FUSE = false, bool MOD = false>
 __global__ void __launch_bounds__(NT, FUSE ? POP_FUSE_MIN_BLOCKS : (NT == 128 ? 11 : 6))
@@ -611,10 +614,11 @@ __global__ void __launch_bounds__(NT, FUSE ? POP_FUSE_MIN_BLOCKS : (NT == 128 ? 
       if (c >= 0) {
         const uint32_t jj = J0 + (uint32_t)c;
         const uint4 d4 = philox4x32_10(make_uint4(q, beta1, jj, kTagEvolve), k0, k1);
+        const float E1 = neg_ln_u(d4.x, s_logtab), E2 = neg_ln_u(d4.z, s_logtab);
         bool run = false;
-        if (bkl_step<W, MOD>(x, t, acc, L, s_inv, s_logtab, d4.x, d4.y, dt_f)) {
+        if (bkl_step<W, MOD>(x, t, acc, L, s_inv, E1, d4.y, dt_f)) {
           ++h;
-          if (bkl_step<W, MOD>(x, t, acc, L, s_inv, s_logtab, d4.z, d4.w, dt_f)) {
+          if (bkl_step<W, MOD>(x, t, acc, L, s_inv, E2, d4.w, dt_f)) {
             ++h;
             run = true;
           }
