@@ -80,6 +80,24 @@ def lib():
         L.orc_ancestors_iid.restype = ctypes.c_int
         L.orc_density_mode.argtypes = [ctypes.c_int32, ctypes.c_int64, _u8p, ctypes.c_int32]
         L.orc_density_mode.restype = ctypes.c_double
+        L.orc_phi_fixed.argtypes = [_f32p, _i32p]
+        L.orc_phi_fixed.restype = ctypes.c_int
+        L.orc_potential.argtypes = [ctypes.c_int32, _u8p, _i32p]
+        L.orc_potential.restype = ctypes.c_int64
+        L.orc_ln_spec.argtypes = [ctypes.c_uint64]
+        L.orc_ln_spec.restype = ctypes.c_float
+        L.orc_guided_rate.argtypes = [ctypes.c_int32, _u8p, ctypes.c_int, _i32p, ctypes.c_float]
+        L.orc_guided_rate.restype = ctypes.c_uint64
+        L.orc_evolve_guided.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_uint32, ctypes.c_uint64, _i32p, _u8p, _i32p, _i32p, _f32p]
+        L.orc_evolve_guided.restype = ctypes.c_int
+        L.orc_evolve_guided_table.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_uint32, ctypes.c_uint64, _f64p, _u8p, _i32p, _i32p, _f32p]
+        L.orc_evolve_guided_table.restype = ctypes.c_int
+        L.orc_weights_guided.argtypes = [ctypes.c_int64, _f32p, _u64p]
+        L.orc_weights_guided.restype = ctypes.c_int
+        L.orc_psi_term_guided.argtypes = [ctypes.c_int64, _f32p]
+        L.orc_psi_term_guided.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -103,11 +121,16 @@ def neg_ln_u(w):
 
 class Population:
     """One population of clones, one byte per site (clone-major).  modified: the
-    MODIFIED dynamics and weights (reading R13); iid: [iid] selection (R14)."""
+    MODIFIED dynamics and weights (reading R13); iid: [iid] selection (R14);
+    phi: 512 potential values, GUIDED dynamics and weights (R15); U_table: a
+    potential over all 2^L configurations instead (GUIDED, test pins only)."""
 
-    def __init__(self, L, N, n_clones, seed, modified=False, iid=False):
+    def __init__(self, L, N, n_clones, seed, modified=False, iid=False, phi=None, U_table=None):
         self.L, self.N, self.n_clones, self.seed = int(L), int(N), int(n_clones), int(seed)
         self.modified, self.iid = bool(modified), bool(iid)
+        self.guided = phi is not None or U_table is not None
+        self.phi_q = None if phi is None else phi_fixed(phi)
+        self.U_table = None if U_table is None else np.ascontiguousarray(np.asarray(U_table, dtype=np.float64))
         self.s = None
         self.A = np.zeros(int(n_clones), dtype=np.float32)
         self.sites = np.zeros((self.n_clones, self.L), dtype=np.uint8)
@@ -126,7 +149,17 @@ class Population:
     def evolve(self, dt, s=None):
         """Dynamical stage of the next interval (MODIFIED mode needs s)."""
         self.beta += 1
-        if self.modified:
+        if self.guided:
+            self.s = float(s)
+            if self.U_table is not None:
+                rc = lib().orc_evolve_guided_table(self.L, self.n_clones, float(dt), self.s, self.beta,
+                                                   self.seed, _p(self.U_table, _f64p), _p(self.sites, _u8p),
+                                                   _p(self.K, _i32p), _p(self.dK, _i32p), _p(self.A, _f32p))
+            else:
+                rc = lib().orc_evolve_guided(self.L, self.n_clones, float(dt), self.s, self.beta, self.seed,
+                                             _p(self.phi_q, _i32p), _p(self.sites, _u8p), _p(self.K, _i32p),
+                                             _p(self.dK, _i32p), _p(self.A, _f32p))
+        elif self.modified:
             self.s = float(s)
             rc = lib().orc_evolve_modified(self.L, self.n_clones, float(dt), self.s, self.beta, self.seed,
                                            _p(self.sites, _u8p), _p(self.K, _i32p), _p(self.dK, _i32p),
@@ -141,13 +174,17 @@ class Population:
 
     def weights(self, s):
         w = np.zeros(self.n_clones, dtype=np.uint64)
-        if self.modified:
+        if self.guided:
+            rc = lib().orc_weights_guided(self.n_clones, _p(self.A, _f32p), _p(w, _u64p))
+        elif self.modified:
             rc = lib().orc_weights_modified(float(s), self.n_clones, _p(self.A, _f32p), _p(w, _u64p))
         else:
             rc = lib().orc_weights(float(s), self.n_clones, _p(self.dK, _i32p), _p(w, _u64p))
         return w, rc
 
     def psi_term(self, s):
+        if self.guided:
+            return lib().orc_psi_term_guided(self.n_clones, _p(self.A, _f32p))
         if self.modified:
             return lib().orc_psi_term_modified(float(s), self.n_clones, _p(self.A, _f32p))
         return lib().orc_psi_term(float(s), self.n_clones, _p(self.dK, _i32p))
@@ -282,6 +319,60 @@ def run(L, N, n_clones, seed, s, dt, M, want_state=False, modified=False, iid=Fa
     if want_state:
         out.update(sites=sites, K=K)
     return out
+
+
+def phi_fixed(phi):
+    """The 512 potential values as the fixed point of reading R15 (int32, phi 2^16)."""
+    phi = np.ascontiguousarray(np.asarray(phi, dtype=np.float32).reshape(512))
+    out = np.zeros(512, dtype=np.int32)
+    if lib().orc_phi_fixed(_p(phi, _f32p), _p(out, _i32p)) != 0:
+        raise ValueError("potential values must satisfy |phi| <= 64")
+    return out
+
+
+def potential(sites, phi):
+    """U(C) of each configuration (rows of sites) in units of 2^-16 (exact integers)."""
+    sites = np.ascontiguousarray(np.atleast_2d(np.asarray(sites, dtype=np.uint8)))
+    q = phi_fixed(phi)
+    return np.array([lib().orc_potential(sites.shape[1], _p(np.ascontiguousarray(r), _u8p), _p(q, _i32p))
+                     for r in sites], dtype=np.int64)
+
+
+def ln_spec(Q):
+    """The specified FP32 ln(Q) of an integer Q >= 1 (R15)."""
+    return np.float32(lib().orc_ln_spec(ctypes.c_uint64(int(Q))))
+
+
+def guided_rate(sites_row, b, phi, s):
+    """Q_b of reading R15 for one configuration (one byte per site) and bond b."""
+    row = np.ascontiguousarray(np.asarray(sites_row, dtype=np.uint8))
+    q = phi_fixed(phi)
+    return int(lib().orc_guided_rate(row.size, _p(row, _u8p), int(b), _p(q, _i32p), ctypes.c_float(float(s))))
+
+
+def evolve_sites_guided(L, sites, dt, s, beta, seed, phi=None, U_table=None, K=None):
+    """GUIDED dynamics of given configurations; returns (sites, K, dK, X)."""
+    sites = np.ascontiguousarray(np.array(sites, dtype=np.uint8))
+    n = sites.shape[0]
+    K = np.zeros(n, dtype=np.int32) if K is None else np.ascontiguousarray(np.array(K, dtype=np.int32))
+    dK = np.zeros(n, dtype=np.int32)
+    X = np.zeros(n, dtype=np.float32)
+    if U_table is not None:
+        U = np.ascontiguousarray(np.asarray(U_table, dtype=np.float64))
+        rc = lib().orc_evolve_guided_table(int(L), n, float(dt), float(s), int(beta), int(seed), _p(U, _f64p),
+                                           _p(sites, _u8p), _p(K, _i32p), _p(dK, _i32p), _p(X, _f32p))
+    else:
+        q = phi_fixed(phi)
+        rc = lib().orc_evolve_guided(int(L), n, float(dt), float(s), int(beta), int(seed), _p(q, _i32p),
+                                     _p(sites, _u8p), _p(K, _i32p), _p(dK, _i32p), _p(X, _f32p))
+    if rc != 0:
+        raise ValueError("orc_evolve_guided rc=%d" % rc)
+    return sites, K, dK, X
+
+
+def psi_term_guided(X):
+    X = np.ascontiguousarray(np.asarray(X, dtype=np.float32))
+    return float(lib().orc_psi_term_guided(X.size, _p(X, _f32p)))
 
 
 def sites_to_words(sites, W=None):

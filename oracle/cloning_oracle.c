@@ -59,6 +59,31 @@
  *      from the exact integer total T of those weights.
  *   R14 [iid] selection (Sec. 4.1): alpha_j = floor(U64_j T / 2^64), U64_j = w1 2^32 + w0
  *      of draw (j, beta, 0, 4); the ancestor is the k with S_k <= alpha_j < S_{k+1}.
+ *   R15 GUIDED dynamics (Sec. 2.2, eqs. modpdef and upsdef, with a local potential
+ *      in place of the uniform e^-s of Sec. 3.2).  U(C) = sum_i phi(window_i), window_i
+ *      the 9 sites i-4..i+4 (mod L) read as a 9-bit number (bit k = site i-4+k);
+ *      phi is given as 512 floats and used as fixed point phi_q = nearest(phi 2^16)
+ *      (|phi| <= 64), so every sum of U is an exact integer.  Requires 10 <= L.
+ *      Rate of the hop across active bond b: W'_b = Q_b 2^-24 with
+ *        dU_b = U(C^b) - U(C) = sum_{m=0..9} phi_q(seg' >> m & 511) - phi_q(seg >> m & 511),
+ *        seg = the 18 sites b-8..b+9 (bit k = site b-8+k), seg' = seg with bits 8, 9 flipped,
+ *        g_b = float(dU_b) 2^-17 - float(s), clamped to [-16, 16],
+ *        Q_b = max(1, floor(2^24 exp_spec(g_b)))   (exp_spec as in R13),
+ *      i.e. W'_b ~ e^-s e^{dU_b/2}; R' = sum_b Q_b exactly (64-bit integer).
+ *      Step e of the interval uses draw (e, beta, j, 5): E = -ln u(w0) as in R2,
+ *      tau = E / r'_f with r'_f = float(R') 2^-24 formed as fma(float(R'_hi), 2^32,
+ *      float(R'_lo)) * 2^-24; t_new >= dt ends the interval; otherwise the hop is across
+ *      the first active bond (increasing b) whose inclusive cumulative Q exceeds
+ *      k = floor((w2 2^32 + w1) R' / 2^64).
+ *      Weight (eq. upsdef with P / P-hat of the simulated rates): ln Upsilon =
+ *      sum_hops (24 ln 2 - s - ln Q_b) - integral (r - r') dt, in FP32:
+ *        per segment  a_r <- fma(float(r) - r'_f, tau, a_r)  (last: dt - t in place of tau),
+ *        per hop      a_h <- a_h + (c24s - ln_spec(Q_b)),  c24s = float(24 ln 2 - s),
+ *      ln_spec the FP32 logarithm of R2's construction applied to the 24-bit head of
+ *      Q_b; X = a_h - a_r.  Since the weight uses the rates actually simulated, the
+ *      estimator is unbiased for any potential (quantisation and clamping included).
+ *      Selection weights w = floor(2^F exp_spec(X - X_ref)), X_ref = max X; psi term
+ *      X_ref + log1p((T - N_c 2^F)/(N_c 2^F)).
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared (see oracle/build.py).
  * Contraction must stay off: every float operation below is a separately rounded
@@ -501,6 +526,193 @@ double orc_psi_term_modified(double s, int64_t n_clones, const float* A) {
   const double base = ldexp((double)n_clones, F);
   const int64_t D = (int64_t)T - (int64_t)(((uint64_t)n_clones) << F);
   return -(double)c * (double)ref + log1p((double)D / base);
+}
+
+/* ---------------------------------------------------------------------------
+ * Reading R15: GUIDED dynamics with a local potential (see the header).
+ * ------------------------------------------------------------------------- */
+#define ORC_TAG_GUIDED 5u
+#define ORC_GUIDE_R 24
+#define ORC_GUIDE_CLAMP 16.0f
+
+/* phi (512 floats, |phi| <= 64) to the fixed point used by every U sum. */
+int orc_phi_fixed(const float* phi, int32_t* phi_q) {
+  for (int i = 0; i < 512; ++i) {
+    if (!(fabsf(phi[i]) <= 64.0f)) return ORC_ERR_ARG;
+    phi_q[i] = (int32_t)nearbyint(ldexp((double)phi[i], 16));
+  }
+  return ORC_OK;
+}
+
+/* U(C) = sum_i phi_q(window_i) as an exact integer. */
+int64_t orc_potential(int32_t L, const uint8_t* n, const int32_t* phi_q) {
+  int64_t U = 0;
+  for (int i = 0; i < L; ++i) {
+    int pat = 0;
+    for (int k = 0; k < 9; ++k) pat |= (int)n[((i - 4 + k) % L + L) % L] << k;
+    U += phi_q[pat];
+  }
+  return U;
+}
+
+/* ln(Q) in FP32 for an integer Q >= 1: the construction of orc_neg_ln_u applied to
+ * the 24 leading bits of Q (Q = m 2^p, ln Q = p ln 2 + ln m). */
+float orc_ln_spec(uint64_t Q) {
+  if (!orc_tab_ready) orc_log_table();
+  int p = 0;
+  while ((Q >> (p + 1)) != 0u) ++p;
+  uint32_t t = (p >= 23) ? (uint32_t)(Q >> (p - 23)) : (uint32_t)(Q << (23 - p));
+  uint32_t mbits = 0x3f800000u | (t & 0x007fffffu);
+  float m;
+  memcpy(&m, &mbits, sizeof m);
+  int i = (int)((t >> 17) & 63u);
+  float r = fmaf(m, orc_tab_inv_c[i], -1.0f);
+  float q = fmaf(r, ORC_THIRD, -0.5f);
+  q = fmaf(q, r, 1.0f);
+  float ln_m = orc_tab_ln_c[i] + q * r;
+  float pf = (float)p;
+  float lq = fmaf(pf, ORC_LN2_LO, ln_m);
+  return fmaf(pf, ORC_LN2_HI, lq);
+}
+
+/* Guided rate of the hop across active bond b: Q_b of reading R15. */
+uint64_t orc_guided_rate(int32_t L, const uint8_t* n, int b, const int32_t* phi_q, float s_f) {
+  uint32_t seg = 0;
+  for (int k = 0; k < 18; ++k) seg |= (uint32_t)n[((b - 8 + k) % L + L) % L] << k;
+  uint32_t seg2 = seg ^ (3u << 8);
+  int32_t dU = 0;
+  for (int m = 0; m < 10; ++m) dU += phi_q[(seg2 >> m) & 511u] - phi_q[(seg >> m) & 511u];
+  float g = ldexpf((float)dU, -17) - s_f;
+  if (g > ORC_GUIDE_CLAMP) g = ORC_GUIDE_CLAMP;
+  if (g < -ORC_GUIDE_CLAMP) g = -ORC_GUIDE_CLAMP;
+  uint64_t q = orc_weight_exp(g, ORC_GUIDE_R);
+  return q > 0 ? q : 1;
+}
+
+/* A rate function for the guided step: the LUT potential above, or (for pins
+ * only) an arbitrary potential given as a table over all 2^L configurations. */
+typedef uint64_t (*orc_rate_fn)(int32_t L, const uint8_t* n, int b, const void* ctx, float s_f);
+
+static uint64_t rate_lut(int32_t L, const uint8_t* n, int b, const void* ctx, float s_f) {
+  return orc_guided_rate(L, n, b, (const int32_t*)ctx, s_f);
+}
+
+/* Potential table over configurations (bit i of the index = site i): dU in FP64,
+ * g = float(dU / 2 - s), then the same clamp and quantisation as the LUT rate. */
+static uint64_t rate_table(int32_t L, const uint8_t* n, int b, const void* ctx, float s_f) {
+  const double* U = (const double*)ctx;
+  uint64_t c = 0;
+  for (int i = 0; i < L; ++i) c |= (uint64_t)n[i] << i;
+  int b1 = (b + 1) % L;
+  uint64_t c2 = c ^ ((1ull << b) | (1ull << b1));
+  float g = (float)((U[c2] - U[c]) / 2.0 - (double)s_f);
+  if (g > ORC_GUIDE_CLAMP) g = ORC_GUIDE_CLAMP;
+  if (g < -ORC_GUIDE_CLAMP) g = -ORC_GUIDE_CLAMP;
+  uint64_t q = orc_weight_exp(g, ORC_GUIDE_R);
+  return q > 0 ? q : 1;
+}
+
+static int guided_evolve(int32_t L, int64_t n_clones, double dt, double s, uint32_t beta,
+                         uint64_t seed, orc_rate_fn rate, const void* ctx, uint8_t* sites,
+                         int32_t* K, int32_t* dK, float* X) {
+  if (L < 10 || n_clones < 1 || !(dt > 0.0)) return ORC_ERR_ARG;
+  const float dt_f = (float)dt;
+  const float s_f = (float)s;
+  const float c24s = (float)(24.0 * 0.693147180559945309417232121458 - s);
+  uint64_t* q = (uint64_t*)malloc((size_t)L * sizeof(uint64_t));
+  if (!q) return ORC_ERR_ARG;
+  for (int64_t j = 0; j < n_clones; ++j) {
+    uint8_t* n = sites + j * (int64_t)L;
+    float t = 0.0f, a_r = 0.0f, a_h = 0.0f;
+    int32_t hops = 0;
+    for (uint32_t e = 0;; ++e) {
+      /* rates of every active bond of the current configuration */
+      int r = 0;
+      uint64_t R = 0;
+      for (int b = 0; b < L; ++b) {
+        if (n[b] != n[(b + 1) % L]) {
+          q[b] = rate(L, n, b, ctx, s_f);
+          R += q[b];
+          ++r;
+        } else {
+          q[b] = 0;
+        }
+      }
+      if (r == 0) break;
+      const float rp = ldexpf(fmaf((float)(uint32_t)(R >> 32), 4294967296.0f,
+                                   (float)(uint32_t)R), -ORC_GUIDE_R);
+      const float d = (float)r - rp;
+      uint32_t w[4];
+      philox_at(e, beta, (uint32_t)j, ORC_TAG_GUIDED, seed, w);
+      const float E = orc_neg_ln_u(w[0]);
+      const float tau = E / rp;
+      const float t_new = t + tau;
+      if (t_new >= dt_f) {
+        a_r = fmaf(d, dt_f - t, a_r);
+        break;
+      }
+      a_r = fmaf(d, tau, a_r);
+      t = t_new;
+      const uint64_t kk = mul_hi_64(((uint64_t)w[2] << 32) | w[1], R);
+      uint64_t cum = 0;
+      int b = -1;
+      for (int i = 0; i < L; ++i) {
+        cum += q[i];
+        if (q[i] != 0 && cum > kk) { b = i; break; }
+      }
+      a_h = a_h + (c24s - orc_ln_spec(q[b]));
+      const int b1 = (b + 1) % L;
+      const uint8_t tmp = n[b];
+      n[b] = n[b1];
+      n[b1] = tmp;
+      ++hops;
+    }
+    dK[j] = hops;
+    K[j] += hops;
+    X[j] = a_h - a_r;
+  }
+  free(q);
+  return ORC_OK;
+}
+
+/* Dynamical stage of one interval under the LUT potential (reading R15).
+ * X receives each clone's log weight ln Upsilon for the interval. */
+int orc_evolve_guided(int32_t L, int64_t n_clones, double dt, double s, uint32_t beta,
+                      uint64_t seed, const int32_t* phi_q, uint8_t* sites, int32_t* K,
+                      int32_t* dK, float* X) {
+  return guided_evolve(L, n_clones, dt, s, beta, seed, rate_lut, phi_q, sites, K, dK, X);
+}
+
+/* The same with a potential table over all 2^L configurations (L <= 20); test pins only. */
+int orc_evolve_guided_table(int32_t L, int64_t n_clones, double dt, double s, uint32_t beta,
+                            uint64_t seed, const double* U, uint8_t* sites, int32_t* K,
+                            int32_t* dK, float* X) {
+  if (L > 20) return ORC_ERR_ARG;
+  return guided_evolve(L, n_clones, dt, s, beta, seed, rate_table, U, sites, K, dK, X);
+}
+
+float orc_x_ref(int64_t n_clones, const float* X) {
+  float ref = X[0];
+  for (int64_t j = 1; j < n_clones; ++j) if (X[j] > ref) ref = X[j];
+  return ref;
+}
+
+int orc_weights_guided(int64_t n_clones, const float* X, uint64_t* w) {
+  if (n_clones < 1) return ORC_ERR_ARG;
+  const int F = orc_weight_scale(n_clones);
+  const float ref = orc_x_ref(n_clones, X);
+  for (int64_t j = 0; j < n_clones; ++j) w[j] = orc_weight_exp(X[j] - ref, F);
+  return ORC_OK;
+}
+
+double orc_psi_term_guided(int64_t n_clones, const float* X) {
+  const int F = orc_weight_scale(n_clones);
+  const float ref = orc_x_ref(n_clones, X);
+  uint64_t T = 0;
+  for (int64_t j = 0; j < n_clones; ++j) T += orc_weight_exp(X[j] - ref, F);
+  const double base = ldexp((double)n_clones, F);
+  const int64_t D = (int64_t)T - (int64_t)(((uint64_t)n_clones) << F);
+  return (double)ref + log1p((double)D / base);
 }
 
 /* Reading R14: [iid] clone selection. */
