@@ -64,21 +64,21 @@
  *      the 9 sites i-4..i+4 (mod L) read as a 9-bit number (bit k = site i-4+k);
  *      phi is given as 512 floats and used as fixed point phi_q = nearest(phi 2^16)
  *      (|phi| <= 64), so every sum of U is an exact integer.  Requires 10 <= L.
- *      Rate of the hop across active bond b: W'_b = Q_b 2^-24 with
+ *      Rate of the hop across active bond b: W'_b = Q_b 2^-20 with
  *        dU_b = U(C^b) - U(C) = sum_{m=0..9} phi_q(seg' >> m & 511) - phi_q(seg >> m & 511),
  *        seg = the 18 sites b-8..b+9 (bit k = site b-8+k), seg' = seg with bits 8, 9 flipped,
- *        g_b = float(dU_b) 2^-17 - float(s), clamped to [-16, 16],
- *        Q_b = max(1, floor(2^24 exp_spec(g_b)))   (exp_spec as in R13),
+ *        g_b = float(dU_b) 2^-17 - float(s), clamped to [-8, 8],
+ *        Q_b = max(1, floor(2^20 exp_spec(g_b)))   (exp_spec as in R13; Q_b < 2^32),
  *      i.e. W'_b ~ e^-s e^{dU_b/2}; R' = sum_b Q_b exactly (64-bit integer).
  *      Step e of the interval uses draw (e, beta, j, 5): E = -ln u(w0) as in R2,
- *      tau = E / r'_f with r'_f = float(R') 2^-24 formed as fma(float(R'_hi), 2^32,
- *      float(R'_lo)) * 2^-24; t_new >= dt ends the interval; otherwise the hop is across
+ *      tau = E / r'_f with r'_f = float(R') 2^-20 formed as fma(float(R'_hi), 2^32,
+ *      float(R'_lo)) * 2^-20; t_new >= dt ends the interval; otherwise the hop is across
  *      the first active bond (increasing b) whose inclusive cumulative Q exceeds
  *      k = floor((w2 2^32 + w1) R' / 2^64).
  *      Weight (eq. upsdef with P / P-hat of the simulated rates): ln Upsilon =
- *      sum_hops (24 ln 2 - s - ln Q_b) - integral (r - r') dt, in FP32:
+ *      sum_hops (20 ln 2 - s - ln Q_b) - integral (r - r') dt, in FP32:
  *        per segment  a_r <- fma(float(r) - r'_f, tau, a_r)  (last: dt - t in place of tau),
- *        per hop      a_h <- a_h + (c24s - ln_spec(Q_b)),  c24s = float(24 ln 2 - s),
+ *        per hop      a_h <- a_h + (c20s - ln_spec(Q_b)),  c20s = float(20 ln 2 - s),
  *      ln_spec the FP32 logarithm of R2's construction applied to the 24-bit head of
  *      Q_b; X = a_h - a_r.  Since the weight uses the rates actually simulated, the
  *      estimator is unbiased for any potential (quantisation and clamping included).
@@ -532,8 +532,8 @@ double orc_psi_term_modified(double s, int64_t n_clones, const float* A) {
  * Reading R15: GUIDED dynamics with a local potential (see the header).
  * ------------------------------------------------------------------------- */
 #define ORC_TAG_GUIDED 5u
-#define ORC_GUIDE_R 24
-#define ORC_GUIDE_CLAMP 16.0f
+#define ORC_GUIDE_R 20
+#define ORC_GUIDE_CLAMP 8.0f
 
 /* phi (512 floats, |phi| <= 64) to the fixed point used by every U sum. */
 int orc_phi_fixed(const float* phi, int32_t* phi_q) {
@@ -618,7 +618,7 @@ static int guided_evolve(int32_t L, int64_t n_clones, double dt, double s, uint3
   if (L < 10 || n_clones < 1 || !(dt > 0.0)) return ORC_ERR_ARG;
   const float dt_f = (float)dt;
   const float s_f = (float)s;
-  const float c24s = (float)(24.0 * 0.693147180559945309417232121458 - s);
+  const float c20s = (float)(ORC_GUIDE_R * 0.693147180559945309417232121458 - s);
   uint64_t* q = (uint64_t*)malloc((size_t)L * sizeof(uint64_t));
   if (!q) return ORC_ERR_ARG;
   for (int64_t j = 0; j < n_clones; ++j) {
@@ -660,7 +660,7 @@ static int guided_evolve(int32_t L, int64_t n_clones, double dt, double s, uint3
         cum += q[i];
         if (q[i] != 0 && cum > kk) { b = i; break; }
       }
-      a_h = a_h + (c24s - orc_ln_spec(q[b]));
+      a_h = a_h + (c20s - orc_ln_spec(q[b]));
       const int b1 = (b + 1) % L;
       const uint8_t tmp = n[b];
       n[b] = n[b1];

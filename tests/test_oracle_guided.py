@@ -76,12 +76,13 @@ def test_guided_rate_is_the_global_potential_difference(L):
             hopped[b], hopped[b1] = row[b1], row[b]
             dU = int(full_potential(hopped, phi_q)[0] - full_potential(row, phi_q)[0])
             g = np.float32(np.float32(dU) * np.float32(2.0 ** -17)) - np.float32(s)
-            g = float(min(max(g, np.float32(-16.0)), np.float32(16.0)))
-            want = max(1, oracle.weight_exp(g, 24))
+            g = float(min(max(g, np.float32(-8.0)), np.float32(8.0)))
+            want = max(1, oracle.weight_exp(g, 20))
             assert oracle.guided_rate(row, b, phi, s) == want, (L, trial, b)
-            # and it is e^-s e^{dU/2} in units of 2^-24 to FP32 accuracy
-            exact = math.ldexp(math.exp(min(max(dU / 2.0 ** 17 - s, -16.0), 16.0)), 24)
+            # and it is e^-s e^{dU/2} in units of 2^-20 to FP32 accuracy, below 2^32
+            exact = math.ldexp(math.exp(min(max(dU / 2.0 ** 17 - s, -8.0), 8.0)), 20)
             assert abs(want - exact) <= 4e-7 * exact + 1.0
+            assert want < 2 ** 32
 
 
 def test_potential_is_the_window_sum():
