@@ -58,6 +58,14 @@ extern "C" {
 #define POP_MODIFIED 1 /* every rate times e^-s, Upsilon = exp(-(1-e^-s) int r dt)
                           (Sec. 3.2, eq. def-ups-ssep); the integral is accumulated in
                           FP32 and the weights use a specified FP32 exponential */
+#define POP_GUIDED 2   /* modified dynamics of Sec. 2.2 (eqs. modpdef, upsdef) with a
+                          local potential U(C) = sum_i phi(sites i-4..i+4): the hop
+                          across bond b has rate ~ e^-s e^{(U(C^b) - U(C))/2} (held as
+                          an integer in units of 2^-20, exponent clamped to [-8, 8]);
+                          Upsilon = prod_hops (e^-s / rate) exp(-int (r - r') dt) of the
+                          rates simulated, so the estimate is unbiased for any phi.
+                          18 <= L <= 128, and every population of the batch must be
+                          GUIDED.  phi is set by pop_set_potential (default 0) */
 
 /* clone selection (Sec. 4.1) */
 #define POP_EQ 0  /* equally spaced alpha_j, eq. (alpha-Ups) */
@@ -75,7 +83,7 @@ typedef struct pop_params {
   int32_t N;           /* particles, 0 <= N <= L */
   int64_t n_clones;    /* N_c, 1 <= N_c <= POP_MAX_CLONES */
   uint64_t seed;       /* Philox key of this population's streams */
-  int32_t weight_mode; /* POP_PLAIN or POP_MODIFIED */
+  int32_t weight_mode; /* POP_PLAIN, POP_MODIFIED or POP_GUIDED */
   int32_t selection;   /* POP_EQ or POP_IID */
 } pop_params;
 
@@ -170,6 +178,16 @@ int pop_autotune(pop_t* pop, double dt, const double* s, int32_t trials, int32_t
  * n >= 0.  POP_ERR_STATE between pop_evolve and pop_resample.  Waits for the stream.
  */
 int pop_density_mode(pop_t* pop, int32_t n, double* h_mean);
+
+/*
+ * Potential of a GUIDED population p: h_phi is a host array of 512 floats, phi of
+ * the 9-site window whose site i-4+k is bit k of the index (the compiled lookup
+ * table of a learned potential).  |phi| <= 64, else POP_ERR_ARG; held as the
+ * fixed-point integers nearest to phi 2^16, so every potential difference is exact.
+ * POP_ERR_STATE for a population that is not GUIDED, or between pop_evolve and
+ * pop_resample.  May change between intervals.  Waits for the stream.
+ */
+int pop_set_potential(pop_t* pop, int32_t p, const float* h_phi);
 
 /* Executed hops (BKL events) per population since pop_init (host array of n_pops). */
 int pop_events(pop_t* pop, uint64_t* h_events);

@@ -23,6 +23,7 @@ POP_ERR_TIMEOUT = -4
 POP_ERR_STATE = -5
 POP_PLAIN = 0
 POP_MODIFIED = 1
+POP_GUIDED = 2
 POP_EQ = 0
 POP_IID = 1
 POP_KCAP = 4096
@@ -32,6 +33,7 @@ POP_MAX_L = 4096
 EXPORTS = ("pop_workspace_bytes", "pop_init", "pop_set_state", "pop_evolve", "pop_resample",
            "pop_run", "pop_estimate_psi", "pop_copy_state", "pop_events", "pop_lattice_words",
            "pop_select_noalloc", "pop_density_mode", "pop_autotune", "pop_kernel_times",
+           "pop_set_potential",
            "pop_launch_count", "pop_strerror", "pop_free")
 KERNEL_KINDS = ("evolve", "weights", "gather", "gather_evolve", "other")
 POP_NOALLOC_MAX_CLONES = 1 << 20
@@ -88,6 +90,8 @@ def library():
     L.pop_autotune.restype = ctypes.c_int
     L.pop_density_mode.argtypes = [ctypes.c_void_p, ctypes.c_int32, _f64p]
     L.pop_density_mode.restype = ctypes.c_int
+    L.pop_set_potential.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]
+    L.pop_set_potential.restype = ctypes.c_int
     L.pop_events.argtypes = [ctypes.c_void_p, _u64p]
     L.pop_events.restype = ctypes.c_int
     L.pop_kernel_times.argtypes = [ctypes.c_void_p, ctypes.c_double, _f64p, ctypes.c_int64, _f64p,
@@ -217,6 +221,12 @@ class PopulationBatch:
         g = ctypes.c_int32(0)
         _check(self._lib.pop_autotune(self._h, float(dt), sp, int(trials), ctypes.byref(g)), "pop_autotune")
         return int(g.value)
+
+    def set_potential(self, p, phi):
+        """GUIDED population p: the 512-entry window potential (|phi| <= 64)."""
+        phi = np.ascontiguousarray(np.asarray(phi, dtype=np.float32).reshape(512))
+        _check(self._lib.pop_set_potential(self._h, int(p), phi.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+               "pop_set_potential")
 
     def kernel_times(self, dt, s, n):
         """Advance n intervals as run() does, timing every launch with CUDA events.

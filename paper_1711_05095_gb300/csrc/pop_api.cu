@@ -33,7 +33,7 @@ constexpr int kGraphIntervals = 32;
 struct Layout {
   int32_t P = 0, W = 0, ntiles = 0, nunits = 0;
   int64_t nslots = 0;
-  size_t o_pops, o_st, o_tile_pop, o_wtab, o_qtab, o_qm1tab, o_inv, o_logtab, o_exp2, o_A, o_S, o_cs, o_tacc, o_hist, o_tile_sum, o_beta,
+  size_t o_pops, o_st, o_tile_pop, o_wtab, o_qtab, o_qm1tab, o_inv, o_logtab, o_exp2, o_A, o_S, o_cs, o_tacc, o_hist, o_tile_sum, o_beta, o_phi,
       o_ksum, o_X, o_Y, o_KX, o_KY, o_dK, o_anc, total;
 };
 
@@ -46,8 +46,13 @@ bool valid_params(const pop_params* params, int32_t n_pops) {
     if (q.L < 3 || q.L > POP_MAX_L) return false;
     if (q.N < 0 || q.N > q.L) return false;
     if (q.n_clones < 1 || q.n_clones > POP_MAX_CLONES) return false;
-    if (q.weight_mode != POP_PLAIN && q.weight_mode != POP_MODIFIED) return false;
+    if (q.weight_mode != POP_PLAIN && q.weight_mode != POP_MODIFIED &&
+        q.weight_mode != POP_GUIDED)
+      return false;
     if (q.selection != POP_EQ && q.selection != POP_IID) return false;
+    // GUIDED: one clone per thread with 18-site windows, and the whole batch guided
+    if ((q.weight_mode == POP_GUIDED) != (params[0].weight_mode == POP_GUIDED)) return false;
+    if (q.weight_mode == POP_GUIDED && (q.L < 18 || q.L > kMaxL)) return false;
   }
   return true;
 }
@@ -83,6 +88,7 @@ bool make_layout(const pop_params* params, int32_t n_pops, Layout* lay) {
   l.o_tile_sum = take(nt * sizeof(unsigned long long));
   l.o_beta = take(sizeof(unsigned int));
   l.o_ksum = take(P * sizeof(long long));
+  l.o_phi = take(P * 512 * sizeof(int32_t));
   l.o_X = take(2 * ns * (size_t)l.W * sizeof(unsigned long long));
   l.o_Y = take(ns * (size_t)l.W * sizeof(unsigned long long));
   l.o_KX = take(2 * ns * sizeof(int32_t));
@@ -120,6 +126,7 @@ struct pop_batch {
   unsigned char* ws = nullptr;
   Batch B{};
   bool any_mod = false;
+  bool guided = false;       // every population GUIDED
   int evolve_grid = 0;
   int evolve_grid_cap = 0;  // persistent grid at full occupancy
   size_t evolve_smem = 0;
@@ -177,11 +184,13 @@ int fix_biases(pop_t* h, const double* s) {
     h->desc[p].abs_s = a;
     h->desc[p].s_neg = s[p] < 0.0 ? 1 : 0;
     h->desc[p].c_f = (float)(-std::expm1(-s[p]));
+    h->desc[p].s_f = (float)s[p];
+    h->desc[p].c20s = (float)((double)kGuideR * 0.693147180559945309417232121458 - s[p]);
   }
   // MODIFIED dynamics: every rate times e^-s, so the waiting-time factor is e^s / r
   std::vector<float> inv_mod;
   for (int32_t p = 0; p < h->lay.P; ++p) {
-    if (!h->desc[p].modified) continue;
+    if (!h->desc[p].modified || h->desc[p].guided) continue;
     inv_mod.assign(kInvStride, 0.0f);
     const double es = std::exp(s[p]);
     for (int r = 1; r <= h->params[p].L; ++r) inv_mod[r] = (float)(es / (double)r);
@@ -232,7 +241,11 @@ int launch_evolve(pop_t* h, cudaStream_t st, float dt_f) {
   const unsigned grid = (unsigned)h->evolve_grid;
   const size_t sm = h->evolve_smem;
   kernel_begin(h, st, POP_K_EVOLVE);
-  if (h->any_mod) {
+  if (h->guided) {
+    const unsigned gg = (unsigned)(h->lay.nslots / kGuideThreads);
+    if (h->lay.W == 1) k_evolve_guided<1><<<gg, kGuideThreads, 0, st>>>(h->B, dt_f);
+    else k_evolve_guided<2><<<gg, kGuideThreads, 0, st>>>(h->B, dt_f);
+  } else if (h->any_mod) {
     if (h->lay.W == 1) k_evolve<1, true><<<grid, kThreads, sm, st>>>(h->B, dt_f);
     else if (h->lay.W == 2) k_evolve<2, true><<<grid, kThreads, sm, st>>>(h->B, dt_f);
     else k_evolve_wide<true><<<grid, kThreads, 0, st>>>(h->B, dt_f);
@@ -272,7 +285,9 @@ int launch_resample(pop_t* h, cudaStream_t st) {
 
 // pop_run fuses the cloning stage of one interval with the dynamical stage of
 // the next when every population uses [eq] selection on a ring of at most 128 sites.
-bool fusable(const pop_t* h) { return h->lay.W >= 1 && h->lay.W <= 2 && !h->B.any_iid; }
+bool fusable(const pop_t* h) {
+  return h->lay.W >= 1 && h->lay.W <= 2 && !h->B.any_iid && !h->guided;
+}
 
 // Cloning stage of the current interval and dynamical stage of the next one.
 int launch_resample_evolve(pop_t* h, cudaStream_t st, float dt_f) {
@@ -398,11 +413,15 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
     d.s = 0.0;
     d.abs_s = 0.0;
     d.s_neg = 0;
-    d.modified = params[p].weight_mode == POP_MODIFIED ? 1 : 0;
+    d.guided = params[p].weight_mode == POP_GUIDED ? 1 : 0;
+    // GUIDED weights take the continuous-weight path of MODIFIED (log weight in A)
+    d.modified = (params[p].weight_mode == POP_MODIFIED || d.guided) ? 1 : 0;
     d.iid = params[p].selection == POP_IID ? 1 : 0;
     d.F = 61 - ceil_log2(params[p].n_clones);
     d.c_f = 0.0f;
-    d.pad = 0;
+    d.s_f = 0.0f;
+    d.c20s = 0.0f;
+    h->guided = d.guided != 0;
     h->any_mod = h->any_mod || d.modified;
     h->B.any_iid = h->B.any_iid || d.iid;
     for (int32_t t = 0; t < d.ntiles; ++t) tile_pop[(size_t)tile + t] = p;
@@ -467,6 +486,7 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
   B.hist = (unsigned int*)(ws + lay.o_hist);
   B.tile_sum = (unsigned long long*)(ws + lay.o_tile_sum);
   B.beta = (unsigned int*)(ws + lay.o_beta);
+  B.phi = (const int32_t*)(ws + lay.o_phi);
   B.ksum = (long long*)(ws + lay.o_ksum);
   B.Xb[0] = (unsigned long long*)(ws + lay.o_X);
   B.Xb[1] = B.Xb[0] + lay.nslots * lay.W;
@@ -739,6 +759,20 @@ int pop_copy_state(pop_t* h, int32_t p, uint64_t* h_lattice, int32_t* h_K, int32
     POP_CUDA(cudaMemcpyAsync(h_dK, h->B.dKb[par] + d.off, (size_t)d.nc * 4u, cudaMemcpyDeviceToHost,
                              h->stream));
   return check_device_errors(h, nullptr);
+}
+
+int pop_set_potential(pop_t* h, int32_t p, const float* h_phi) {
+  if (h == nullptr || p < 0 || p >= h->lay.P || h_phi == nullptr) return POP_ERR_ARG;
+  if (!h->desc[p].guided || h->phase != kReady) return POP_ERR_STATE;
+  std::vector<int32_t> q(512);
+  for (int i = 0; i < 512; ++i) {
+    if (!(std::fabs(h_phi[i]) <= 64.0f)) return POP_ERR_ARG;
+    q[i] = (int32_t)std::nearbyint(std::ldexp((double)h_phi[i], 16));
+  }
+  POP_CUDA(cudaMemcpyAsync(h->ws + h->lay.o_phi + (size_t)p * 512 * sizeof(int32_t), q.data(),
+                           512 * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+  POP_CUDA(cudaStreamSynchronize(h->stream));
+  return POP_OK;
 }
 
 int pop_events(pop_t* h, uint64_t* h_events) {

@@ -48,6 +48,11 @@ constexpr uint32_t kStepLimit = 1u << 24; // BKL steps per clone per interval
 
 constexpr int32_t kErrRange = -3;
 
+// GUIDED dynamics: hop rates in units of 2^-kGuideR, exponent clamped to +-kGuideClamp.
+constexpr int kGuideR = 20;
+constexpr float kGuideClamp = 8.0f;
+constexpr uint32_t kTagGuided = 5u;
+
 // Constant per run.
 struct PopDesc {
   int32_t L, N;
@@ -60,9 +65,11 @@ struct PopDesc {
   int32_t iid;       // [iid] selection (Sec. 4.1)
   int32_t F;         // fixed-point weight scale, 61 - ceil(log2 N_c)
   float c_f;         // float(1 - e^-s), the MODIFIED weight coefficient
-  int32_t pad;
+  int32_t guided;    // GUIDED dynamics and weights (local potential; modified is also set)
   double s;          // bias
   double abs_s;
+  float s_f;         // float(s)
+  float c20s;        // GUIDED: float(20 ln 2 - s), the per-hop weight constant
 };
 
 // Mutable per population.
@@ -92,6 +99,7 @@ struct Batch {
   const float* inv_rate;                // [P][kInvStride] float(1/r)
   const float2* logtab;                 // [64] (1/c_i, ln c_i) of the waiting-time log
   const float* exp2tab;                 // [64] 2^(i/64) of the MODIFIED weight exponential
+  const int32_t* phi;                   // GUIDED: [P][512] potential, fixed point phi 2^16
   float* Ab[2];                         // MODIFIED: rate integral, by interval parity
   unsigned long long* S;                // [iid]: exclusive prefix sums of the weights
   unsigned int* hist;                   // [P][kKcap] activity histogram (zero between intervals)
@@ -429,12 +437,28 @@ __device__ __forceinline__ unsigned long long weight_exp(float x, int F, const f
   return mant >> (-sa);
 }
 
-// The weight of one clone: plain (table of 2^F exp(-|s| k), k = |dK - k_ref|) or
-// MODIFIED (weight_exp of -c (A - A_ref)).  Returns false on a plain range error.
+// Float bits mapped to an int of the same order (an involution), so that atomic
+// integer min/max order any floats, negative ones included.
+__device__ __forceinline__ int float_order(float f) {
+  const int i = __float_as_int(f);
+  return i ^ ((i >> 31) & 0x7fffffff);
+}
+__device__ __forceinline__ float order_float(int i) {
+  return __int_as_float(i ^ ((i >> 31) & 0x7fffffff));
+}
+
+// The weight of one clone: plain (table of 2^F exp(-|s| k), k = |dK - k_ref|),
+// MODIFIED (weight_exp of -c (A - A_ref)) or GUIDED (weight_exp of X - X_ref, X the
+// clone's log weight held in A, X_ref the maximum).  Returns false on a plain range error.
 __device__ __forceinline__ bool clone_weight(const PopDesc& d, int dk, int kref, float a,
                                             float a_ref, const unsigned long long* wt,
                                             const float* tab2, unsigned long long& w,
                                             unsigned int& k_out) {
+  if (d.guided) {
+    w = weight_exp(__fsub_rn(a, a_ref), d.F, tab2);
+    k_out = 0u;
+    return true;
+  }
   if (d.modified) {
     w = weight_exp(__fmul_rn(-d.c_f, __fsub_rn(a, a_ref)), d.F, tab2);
     k_out = 0u;

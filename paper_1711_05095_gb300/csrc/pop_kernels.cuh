@@ -339,8 +339,10 @@ __global__ void __launch_bounds__(kThreads) k_weights(Batch B) {
   for (int i = tid; i < kHistSmem; i += kThreads) s_hist[i] = 0u;
   const int dk_min = st->dk_min[par], dk_max = st->dk_max[par];
   const int kref = d.s_neg ? dk_max : dk_min;
-  // MODIFIED reference: the smallest (s >= 0) or largest (s < 0) rate integral
-  const float a_ref = __int_as_float(d.s_neg ? st->a_max[par] : st->a_min[par]);
+  // MODIFIED reference: the smallest (s >= 0) or largest (s < 0) rate integral;
+  // GUIDED: the largest log weight (held as an order-preserving int)
+  const float a_ref = d.guided ? order_float(st->a_max[par])
+                               : __int_as_float(d.s_neg ? st->a_max[par] : st->a_min[par]);
   __syncthreads();
   const int dkv[kItems] = {dk4.x, dk4.y, dk4.z, dk4.w};
   const unsigned long long* wt = B.wtab + (size_t)p * kKcap;
@@ -700,10 +702,12 @@ __global__ void __launch_bounds__(NT, FUSE ? POP_FUSE_MIN_BLOCKS : (NT == 128 ? 
   // psi term of eq. (psihat) for this interval, once per population.
   // MODIFIED (reading of eq. def-ups-ssep): -c A_ref + log1p((T - N_c 2^F) / (N_c 2^F))
   // from the exact total T of the quantised weights.
+  // GUIDED: X_ref + log1p(...) with X_ref the largest log weight.
   if (d.modified && lt == 0 && tid == 0) {
     const double base_w = ldexp((double)d.nc, d.F);
     const long long D = (long long)T - (long long)((unsigned long long)d.nc << d.F);
-    st->psi_acc += -(double)d.c_f * (double)a_ref + log1p((double)D / base_w);
+    const double ref = d.guided ? (double)a_ref : -(double)d.c_f * (double)a_ref;
+    st->psi_acc += ref + log1p((double)D / base_w);
     st->dk_min[par] = INT_MAX;
     st->dk_max[par] = INT_MIN;
     st->a_min[par] = INT_MAX;
@@ -793,6 +797,210 @@ __global__ void __launch_bounds__(kThreads) k_select_iid(Batch B) {
     }
   }
   if (blockIdx.x == gridDim.x - 1 && tid == 0) *B.beta += 1u;
+}
+
+// ---------------------------------------------------------------------------
+// GUIDED dynamical stage (Sec. 2.2, eqs. modpdef and upsdef, with a local potential
+// U(C) = sum_i phi(sites i-4..i+4) in place of the uniform e^-s of Sec. 3.2).  The hop
+// across active bond b has rate Q_b 2^-20, Q_b = max(1, floor(2^20 exp_spec(g_b))),
+// g_b = float(dU_b) 2^-17 - float(s) clamped to [-8, 8], dU_b = U(C^b) - U(C) from the
+// ten windows that contain the bond's sites (exact fixed-point integers).  One clone
+// per thread; its rates live in shared memory (bond-major, so the threads of a warp
+// never share a bank), with sums over groups of 16 bonds for the bond choice.  After a
+// hop only the 19 bonds whose windows see the two flipped sites get new rates.
+// Step e uses draw (e, beta, j, 5): E = -ln u(w0); tau = E / r' (r' = R 2^-20 as a
+// float); the bond is the first whose cumulative Q exceeds floor((w2 2^32 + w1) R / 2^64).
+// Log weight of the interval, in FP32:
+//   X = sum_hops (float(20 ln 2 - s) - ln_spec(Q_b)) - sum_segments (r - r') tau,
+// the weight of the rates actually simulated (so unbiased for any potential).
+// Requires 18 <= L <= 128.
+// ---------------------------------------------------------------------------
+constexpr int kGuideThreads = 64;
+constexpr int kGuideGroup = 16;
+
+// 18 sites starting at `start` (site start + k is bit k), 18 <= L, ring wrap included.
+template <int W>
+__device__ __forceinline__ uint32_t guided_seg(const unsigned long long (&x)[W], int L,
+                                               int start) {
+  if (W == 1 || L <= 64) {
+    const unsigned long long x0 = x[0];
+    const unsigned long long y = (start == 0) ? x0 : ((x0 >> start) | (x0 << (L - start)));
+    return (uint32_t)(y & 0x3FFFFull);
+  } else {
+    const unsigned long long x0 = x[0], x1 = x[W - 1];
+    auto bits_at = [&](int pos) -> unsigned long long {
+      if (pos == 0) return x0;
+      if (pos < 64) return (x0 >> pos) | (x1 << (64 - pos));
+      return x1 >> (pos - 64);
+    };
+    if (start + 18 <= L) return (uint32_t)(bits_at(start) & 0x3FFFFull);
+    const int n1 = L - start;
+    const uint32_t lo = (uint32_t)(bits_at(start) & ((1ull << n1) - 1ull));
+    const uint32_t hi = (uint32_t)(x0 & ((1ull << (18 - n1)) - 1ull));
+    return lo | (hi << n1);
+  }
+}
+
+template <int W>
+__device__ __forceinline__ uint32_t guided_rate(const unsigned long long (&x)[W], int L, int b,
+                                                const int32_t* phi, float s_f,
+                                                const float* exp2tab) {
+  int start = b - 8;
+  if (start < 0) start += L;
+  const uint32_t seg = guided_seg<W>(x, L, start);
+  const uint32_t seg2 = seg ^ (3u << 8);
+  int dU = 0;
+#pragma unroll
+  for (int m = 0; m < 10; ++m) dU += phi[(seg2 >> m) & 511u] - phi[(seg >> m) & 511u];
+  float g = __fsub_rn(__fmul_rn(__int2float_rn(dU), 0x1p-17f), s_f);
+  g = fminf(fmaxf(g, -kGuideClamp), kGuideClamp);
+  const unsigned long long q = weight_exp(g, kGuideR, exp2tab);
+  return q > 0ull ? (uint32_t)q : 1u;
+}
+
+// ln(Q) in FP32 for an integer Q >= 1: the construction of neg_ln_u applied to the
+// 24 leading bits of Q (Q = m 2^p, ln Q = p ln 2 + ln m).
+__device__ __forceinline__ float ln_spec(uint32_t Q, const float2* tab) {
+  const int p = 31 - __clz((int)Q);
+  const uint32_t t = (p >= 23) ? (Q >> (p - 23)) : (Q << (23 - p));
+  const float m = __uint_as_float(0x3f800000u | (t & 0x007fffffu));
+  const float2 cl = tab[(t >> 17) & 63u];
+  const float r = __fmaf_rn(m, cl.x, -1.0f);
+  float q = __fmaf_rn(r, 0x1.555556p-2f, -0.5f);
+  q = __fmaf_rn(q, r, 1.0f);
+  const float ln_m = __fadd_rn(cl.y, __fmul_rn(q, r));
+  const float pf = __int2float_rn(p);
+  const float lq = __fmaf_rn(pf, 0x1.7f7d1cp-20f, ln_m);
+  return __fmaf_rn(pf, 0x1.62e4p-1f, lq);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kGuideThreads) k_evolve_guided(Batch B, float dt_f) {
+  __shared__ int32_t s_phi[512];
+  __shared__ float s_exp2[64];
+  __shared__ float2 s_log[64];
+  __shared__ uint32_t s_q[kMaxL][kGuideThreads];
+  __shared__ unsigned long long s_g[kMaxL / kGuideGroup][kGuideThreads];
+  __shared__ int s_min, s_max, s_amin, s_amax;
+  __shared__ unsigned int s_ev;
+  const int tid = threadIdx.x;
+  const int64_t slot0 = (int64_t)blockIdx.x * kGuideThreads;
+  const int p = B.tile_pop[slot0 / kTile];
+  const PopDesc d = B.pops[p];
+  for (int i = tid; i < 512; i += kGuideThreads) s_phi[i] = B.phi[(size_t)p * 512 + i];
+  s_exp2[tid] = B.exp2tab[tid];
+  s_log[tid] = B.logtab[tid];
+  if (tid == 0) {
+    s_min = INT_MAX;
+    s_max = INT_MIN;
+    s_amin = INT_MAX;
+    s_amax = INT_MIN;
+    s_ev = 0u;
+  }
+  __syncthreads();
+  const uint32_t beta = *B.beta;
+  const int par = (int)(beta & 1u);
+  const int64_t slot = slot0 + tid;
+  const int64_t j = slot - d.off;
+  const int L = d.L;
+  if (j < d.nc) {
+    unsigned long long x[W];
+    load_lat<W>(B.Y, slot, x);
+    const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
+    // rates of every bond, group sums, total
+    unsigned long long a[W];
+    active_bonds<W>(x, L, a);
+    int r = popc_lat<W>(a);
+    unsigned long long R = 0ull;
+    for (int g = 0; g < kMaxL / kGuideGroup; ++g) {
+      unsigned long long gs = 0ull;
+      for (int b = g * kGuideGroup; b < (g + 1) * kGuideGroup; ++b) {
+        uint32_t q = 0u;
+        if (b < L && ((a[b >> 6] >> (b & 63)) & 1ull)) q = guided_rate<W>(x, L, b, s_phi, d.s_f, s_exp2);
+        s_q[b][tid] = q;
+        gs += q;
+      }
+      s_g[g][tid] = gs;
+      R += gs;
+    }
+    float t = 0.0f, a_r = 0.0f, a_h = 0.0f;
+    int h = 0;
+    for (uint32_t e = 0;; ++e) {
+      if (r == 0) break;
+      if (e >= kStepLimit) {  // guard: an interval must end; report, never spin
+        B.st[p].err = kErrRange;
+        break;
+      }
+      const float rp = __fmul_rn(__fmaf_rn(__uint2float_rn((uint32_t)(R >> 32)), 4294967296.0f,
+                                           __uint2float_rn((uint32_t)R)),
+                                 0x1p-20f);
+      const float dr = __fsub_rn(__int2float_rn(r), rp);
+      const uint4 w = philox4x32_10(make_uint4(e, beta, (uint32_t)j, kTagGuided), k0, k1);
+      const float E = neg_ln_u(w.x, s_log);
+      const float tau = __fdiv_rn(E, rp);
+      const float t_new = __fadd_rn(t, tau);
+      if (t_new >= dt_f) {
+        a_r = __fmaf_rn(dr, __fsub_rn(dt_f, t), a_r);
+        break;
+      }
+      a_r = __fmaf_rn(dr, tau, a_r);
+      t = t_new;
+      const unsigned long long kk = __umul64hi(((unsigned long long)w.z << 32) | w.y, R);
+      // the first bond whose inclusive cumulative rate exceeds kk
+      // (kk < R = the sum of the group sums, so both loops stop inside the arrays;
+      // the index bounds only make that explicit)
+      unsigned long long cum = 0ull;
+      int g = 0;
+      while (g < kMaxL / kGuideGroup - 1 && cum + s_g[g][tid] <= kk) {
+        cum += s_g[g][tid];
+        ++g;
+      }
+      int b = g * kGuideGroup;
+      for (; b < kMaxL - 1; ++b) {
+        cum += s_q[b][tid];
+        if (cum > kk) break;
+      }
+      a_h = __fadd_rn(a_h, __fsub_rn(d.c20s, ln_spec(s_q[b][tid], s_log)));
+      hop<W>(x, b, L);
+      ++h;
+      active_bonds<W>(x, L, a);
+      r = popc_lat<W>(a);
+      // new rates for the bonds whose windows contain site b or b+1
+      for (int db = -9; db <= 9; ++db) {
+        int c = b + db;
+        if (c < 0) c += L;
+        if (c >= L) c -= L;
+        const uint32_t q = ((a[c >> 6] >> (c & 63)) & 1ull)
+                               ? guided_rate<W>(x, L, c, s_phi, d.s_f, s_exp2) : 0u;
+        const uint32_t old = s_q[c][tid];
+        if (q != old) {
+          s_q[c][tid] = q;
+          const long long diff = (long long)q - (long long)old;
+          s_g[c / kGuideGroup][tid] += (unsigned long long)diff;
+          R += (unsigned long long)diff;
+        }
+      }
+    }
+    const float X = __fsub_rn(a_h, a_r);
+    store_lat<W>(B.Xb[par], slot, x);
+    B.KXb[par][slot] = B.KY[slot] + h;
+    B.dKb[par][slot] = h;
+    B.Ab[par][slot] = X;
+    atomicMin(&s_min, h);
+    atomicMax(&s_max, h);
+    atomicAdd(&s_ev, (unsigned int)h);
+    atomicMin(&s_amin, float_order(X));
+    atomicMax(&s_amax, float_order(X));
+  }
+  __syncthreads();
+  if (tid == 0 && s_min != INT_MAX) {
+    PopState* st = B.st + p;
+    atomicMin(&st->dk_min[par], s_min);
+    atomicMax(&st->dk_max[par], s_max);
+    atomicAdd(&st->events, (unsigned long long)s_ev);
+    atomicMin(&st->a_min[par], s_amin);
+    atomicMax(&st->a_max[par], s_amax);
+  }
 }
 
 // ---------------------------------------------------------------------------

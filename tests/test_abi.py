@@ -48,6 +48,15 @@ def test_workspace_bytes(lib):
     assert pg.workspace_bytes([P(weight_mode=1, selection=1)]) > 0
     for bad in (P(L=2), P(L=4097), P(N=-1), P(N=21), P(n_clones=0), P(weight_mode=7), P(selection=9)):
         assert pg.workspace_bytes([bad]) == 0, bad
+    # GUIDED: 18 <= L <= 128, and the whole batch GUIDED
+    G = pg.POP_GUIDED
+    assert pg.workspace_bytes([P(L=18, N=9, weight_mode=G), P(L=128, N=64, weight_mode=G)]) > 0
+    assert pg.workspace_bytes([P(L=17, N=8, weight_mode=G)]) == 0
+    assert pg.workspace_bytes([P(L=129, N=64, weight_mode=G)]) == 0
+    assert pg.workspace_bytes([P(weight_mode=G), P()]) == 0
+    assert pg.workspace_bytes([P(), P(weight_mode=G)]) == 0
+    # the potential table is part of the workspace
+    assert pg.workspace_bytes([P(weight_mode=G)]) == pg.workspace_bytes([P()])
 
 
 def test_init_rejects_bad_arguments_without_device(lib):
@@ -63,6 +72,7 @@ def test_init_rejects_bad_arguments_without_device(lib):
     assert h.value is None
     assert lib.pop_evolve(None, 0.1, None) == pg.POP_ERR_ARG
     assert lib.pop_resample(None) == pg.POP_ERR_ARG
+    assert lib.pop_set_potential(None, 0, None) == pg.POP_ERR_ARG
     lib.pop_free(None)
 
 
