@@ -84,10 +84,12 @@ def lib():
         L.orc_phi_fixed.restype = ctypes.c_int
         L.orc_potential.argtypes = [ctypes.c_int32, _u8p, _i32p]
         L.orc_potential.restype = ctypes.c_int64
-        L.orc_ln_spec.argtypes = [ctypes.c_uint64]
-        L.orc_ln_spec.restype = ctypes.c_float
-        L.orc_guided_rate.argtypes = [ctypes.c_int32, _u8p, ctypes.c_int, _i32p, ctypes.c_float]
-        L.orc_guided_rate.restype = ctypes.c_uint64
+        L.orc_guided_q.argtypes = [ctypes.c_int32]
+        L.orc_guided_q.restype = ctypes.c_uint64
+        L.orc_s_q.argtypes = [ctypes.c_double]
+        L.orc_s_q.restype = ctypes.c_int32
+        L.orc_guided_k.argtypes = [ctypes.c_int32, _u8p, ctypes.c_int, _i32p, ctypes.c_int32]
+        L.orc_guided_k.restype = ctypes.c_int32
         L.orc_evolve_guided.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_uint32, ctypes.c_uint64, _i32p, _u8p, _i32p, _i32p, _f32p]
         L.orc_evolve_guided.restype = ctypes.c_int
@@ -338,16 +340,21 @@ def potential(sites, phi):
                      for r in sites], dtype=np.int64)
 
 
-def ln_spec(Q):
-    """The specified FP32 ln(Q) of an integer Q >= 1 (R15)."""
-    return np.float32(lib().orc_ln_spec(ctypes.c_uint64(int(Q))))
+def guided_q(k):
+    """Q(k) = floor(TA[a] TB[c] / 2^44), the rate 2^40 exp(k 2^-17) of reading R15."""
+    return int(lib().orc_guided_q(int(k)))
 
 
-def guided_rate(sites_row, b, phi, s):
-    """Q_b of reading R15 for one configuration (one byte per site) and bond b."""
+def s_q(s):
+    """s in units of 2^-17 (nearest integer), as the guided rates use it (R15)."""
+    return int(lib().orc_s_q(float(s)))
+
+
+def guided_k(sites_row, b, phi, s):
+    """Rate exponent k_b (units of 2^-17) of reading R15 for one configuration and bond b."""
     row = np.ascontiguousarray(np.asarray(sites_row, dtype=np.uint8))
     q = phi_fixed(phi)
-    return int(lib().orc_guided_rate(row.size, _p(row, _u8p), int(b), _p(q, _i32p), ctypes.c_float(float(s))))
+    return int(lib().orc_guided_k(row.size, _p(row, _u8p), int(b), _p(q, _i32p), s_q(s)))
 
 
 def evolve_sites_guided(L, sites, dt, s, beta, seed, phi=None, U_table=None, K=None):

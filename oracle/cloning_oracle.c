@@ -64,24 +64,30 @@
  *      the 9 sites i-4..i+4 (mod L) read as a 9-bit number (bit k = site i-4+k);
  *      phi is given as 512 floats and used as fixed point phi_q = nearest(phi 2^16)
  *      (|phi| <= 64), so every sum of U is an exact integer.  Requires 10 <= L.
- *      Rate of the hop across active bond b: W'_b = Q_b 2^-20 with
+ *      Rate of the hop across active bond b, ~ e^-s e^{dU_b/2}, with an exactly known
+ *      logarithm:
  *        dU_b = U(C^b) - U(C) = sum_{m=0..9} phi_q(seg' >> m & 511) - phi_q(seg >> m & 511),
- *        seg = the 18 sites b-8..b+9 (bit k = site b-8+k), seg' = seg with bits 8, 9 flipped,
- *        g_b = float(dU_b) 2^-17 - float(s), clamped to [-8, 8],
- *        Q_b = max(1, floor(2^20 exp_spec(g_b)))   (exp_spec as in R13; Q_b < 2^32),
- *      i.e. W'_b ~ e^-s e^{dU_b/2}; R' = sum_b Q_b exactly (64-bit integer).
- *      Step e of the interval uses draw (e, beta, j, 5): E = -ln u(w0) as in R2,
- *      tau = E / r'_f with r'_f = float(R') 2^-20 formed as fma(float(R'_hi), 2^32,
- *      float(R'_lo)) * 2^-20; t_new >= dt ends the interval; otherwise the hop is across
- *      the first active bond (increasing b) whose inclusive cumulative Q exceeds
- *      k = floor((w2 2^32 + w1) R' / 2^64).
- *      Weight (eq. upsdef with P / P-hat of the simulated rates): ln Upsilon =
- *      sum_hops (20 ln 2 - s - ln Q_b) - integral (r - r') dt, in FP32:
- *        per segment  a_r <- fma(float(r) - r'_f, tau, a_r)  (last: dt - t in place of tau),
- *        per hop      a_h <- a_h + (c20s - ln_spec(Q_b)),  c20s = float(20 ln 2 - s),
- *      ln_spec the FP32 logarithm of R2's construction applied to the 24-bit head of
- *      Q_b; X = a_h - a_r.  Since the weight uses the rates actually simulated, the
- *      estimator is unbiased for any potential (quantisation and clamping included).
+ *        seg = the 18 sites b-8..b+9 (bit k = site b-8+k), seg' = seg with bits 8, 9 flipped;
+ *        exponent k_b = clamp(dU_b - s_q, -2^20, 2^20) in units of 2^-17, s_q = nearest(s 2^17)
+ *        (dU_b in units of 2^-16 is dU/2 in units of 2^-17);
+ *        Q_b = floor(TA[a] TB[c] / 2^44), k_b + 2^20 = 2^11 a + c, with the tables
+ *        TA[a] = nearest(2^44 exp(a/64 - 8)), TB[c] = nearest(2^40 exp(c/2^17)) (FP64 exp),
+ *      so Q_b = 2^40 exp(k_b 2^-17) (1 + d), |d| < 3e-9.  R' = sum_b Q_b (64-bit, exact).
+ *      Step e of the interval uses draw (e, beta, j, 5): E = -ln u(w0) as in R2;
+ *      r'_f = float(R') 2^-40 (one rounding); tau = E / r'_f; t_new >= dt ends the
+ *      interval; otherwise the hop is across the first active bond (increasing b) whose
+ *      inclusive cumulative Q exceeds floor((w2 2^32 + w1) R' / 2^64).
+ *      Weight (eq. upsdef with the P-hat of the simulated process: waiting rate r'_f,
+ *      bond b with probability Q_b / R', i.e. hop rate 2^-40 Q_b (1 + eta), eta =
+ *      (2^40 r'_f - R') / R' from the rounding of r'_f, computed from exact integers):
+ *        ln Upsilon = sum_hops (-s - ln(2^-40 Q_b) - eta) - integral (r - r'_f) dt,
+ *      with ln(2^-40 Q_b) taken as k_b 2^-17 (the table error d is below 3e-9) and
+ *      -s = -s_q 2^-17 + c_s, c_s = float(s_q 2^-17 - s) (|c_s| <= 2^-18), in FP32:
+ *        per hop      a_h <- a_h + ((c_s - float(k_b + s_q) 2^-17) - eta),
+ *        per segment  a_r <- fma(float(r) - r'_f, tau, a_r)  (last: dt - t in place of tau);
+ *      X = a_h - a_r.  Each term is computed from quantities of its own size, so no
+ *      rounding is repeated hop after hop into a systematic shift of psi; since the
+ *      weight is that of the rates simulated, the estimate is unbiased for any potential.
  *      Selection weights w = floor(2^F exp_spec(X - X_ref)), X_ref = max X; psi term
  *      X_ref + log1p((T - N_c 2^F)/(N_c 2^F)).
  *
@@ -532,8 +538,7 @@ double orc_psi_term_modified(double s, int64_t n_clones, const float* A) {
  * Reading R15: GUIDED dynamics with a local potential (see the header).
  * ------------------------------------------------------------------------- */
 #define ORC_TAG_GUIDED 5u
-#define ORC_GUIDE_R 20
-#define ORC_GUIDE_CLAMP 8.0f
+#define ORC_GUIDE_KMAX (1 << 20) /* exponent clamp, units of 2^-17: |ln rate + s| <= 8 */
 
 /* phi (512 floats, |phi| <= 64) to the fixed point used by every U sum. */
 int orc_phi_fixed(const float* phi, int32_t* phi_q) {
@@ -555,61 +560,57 @@ int64_t orc_potential(int32_t L, const uint8_t* n, const int32_t* phi_q) {
   return U;
 }
 
-/* ln(Q) in FP32 for an integer Q >= 1: the construction of orc_neg_ln_u applied to
- * the 24 leading bits of Q (Q = m 2^p, ln Q = p ln 2 + ln m). */
-float orc_ln_spec(uint64_t Q) {
-  if (!orc_tab_ready) orc_log_table();
-  int p = 0;
-  while ((Q >> (p + 1)) != 0u) ++p;
-  uint32_t t = (p >= 23) ? (uint32_t)(Q >> (p - 23)) : (uint32_t)(Q << (23 - p));
-  uint32_t mbits = 0x3f800000u | (t & 0x007fffffu);
-  float m;
-  memcpy(&m, &mbits, sizeof m);
-  int i = (int)((t >> 17) & 63u);
-  float r = fmaf(m, orc_tab_inv_c[i], -1.0f);
-  float q = fmaf(r, ORC_THIRD, -0.5f);
-  q = fmaf(q, r, 1.0f);
-  float ln_m = orc_tab_ln_c[i] + q * r;
-  float pf = (float)p;
-  float lq = fmaf(pf, ORC_LN2_LO, ln_m);
-  return fmaf(pf, ORC_LN2_HI, lq);
+/* The exponential tables of reading R15. */
+static uint64_t orc_ta[1025], orc_tb[2048];
+static int orc_guide_ready = 0;
+static void orc_guide_tables(void) {
+  for (int a = 0; a <= 1024; ++a) orc_ta[a] = (uint64_t)nearbyint(ldexp(exp(a / 64.0 - 8.0), 44));
+  for (int c = 0; c < 2048; ++c) orc_tb[c] = (uint64_t)nearbyint(ldexp(exp(c / 131072.0), 40));
+  orc_guide_ready = 1;
 }
 
-/* Guided rate of the hop across active bond b: Q_b of reading R15. */
-uint64_t orc_guided_rate(int32_t L, const uint8_t* n, int b, const int32_t* phi_q, float s_f) {
+/* Q(k) = floor(TA[a] TB[c] / 2^44) = 2^40 exp(k 2^-17) (1 + d), for |k| <= 2^20. */
+uint64_t orc_guided_q(int32_t k) {
+  if (!orc_guide_ready) orc_guide_tables();
+  const uint32_t u = (uint32_t)(k + ORC_GUIDE_KMAX);
+  return (uint64_t)(((u128)orc_ta[u >> 11] * (u128)orc_tb[u & 2047u]) >> 44);
+}
+
+int32_t orc_s_q(double s) { return (int32_t)nearbyint(ldexp(s, 17)); }
+
+static int32_t clamp_k(int64_t k) {
+  if (k > ORC_GUIDE_KMAX) return ORC_GUIDE_KMAX;
+  if (k < -ORC_GUIDE_KMAX) return -ORC_GUIDE_KMAX;
+  return (int32_t)k;
+}
+
+/* Rate exponent k_b of the hop across active bond b under the LUT potential. */
+int32_t orc_guided_k(int32_t L, const uint8_t* n, int b, const int32_t* phi_q, int32_t s_q) {
   uint32_t seg = 0;
   for (int k = 0; k < 18; ++k) seg |= (uint32_t)n[((b - 8 + k) % L + L) % L] << k;
   uint32_t seg2 = seg ^ (3u << 8);
   int32_t dU = 0;
   for (int m = 0; m < 10; ++m) dU += phi_q[(seg2 >> m) & 511u] - phi_q[(seg >> m) & 511u];
-  float g = ldexpf((float)dU, -17) - s_f;
-  if (g > ORC_GUIDE_CLAMP) g = ORC_GUIDE_CLAMP;
-  if (g < -ORC_GUIDE_CLAMP) g = -ORC_GUIDE_CLAMP;
-  uint64_t q = orc_weight_exp(g, ORC_GUIDE_R);
-  return q > 0 ? q : 1;
+  return clamp_k((int64_t)dU - s_q);
 }
 
-/* A rate function for the guided step: the LUT potential above, or (for pins
- * only) an arbitrary potential given as a table over all 2^L configurations. */
-typedef uint64_t (*orc_rate_fn)(int32_t L, const uint8_t* n, int b, const void* ctx, float s_f);
+/* A rate-exponent function for the guided step: the LUT potential above, or (for
+ * pins only) an arbitrary potential given as a table over all 2^L configurations. */
+typedef int32_t (*orc_rate_fn)(int32_t L, const uint8_t* n, int b, const void* ctx, int32_t s_q);
 
-static uint64_t rate_lut(int32_t L, const uint8_t* n, int b, const void* ctx, float s_f) {
-  return orc_guided_rate(L, n, b, (const int32_t*)ctx, s_f);
+static int32_t rate_lut(int32_t L, const uint8_t* n, int b, const void* ctx, int32_t s_q) {
+  return orc_guided_k(L, n, b, (const int32_t*)ctx, s_q);
 }
 
-/* Potential table over configurations (bit i of the index = site i): dU in FP64,
- * g = float(dU / 2 - s), then the same clamp and quantisation as the LUT rate. */
-static uint64_t rate_table(int32_t L, const uint8_t* n, int b, const void* ctx, float s_f) {
+/* Potential table over configurations (bit i of the index = site i): k_b =
+ * nearest(dU / 2 2^17) - s_q, clamped. */
+static int32_t rate_table(int32_t L, const uint8_t* n, int b, const void* ctx, int32_t s_q) {
   const double* U = (const double*)ctx;
   uint64_t c = 0;
   for (int i = 0; i < L; ++i) c |= (uint64_t)n[i] << i;
   int b1 = (b + 1) % L;
   uint64_t c2 = c ^ ((1ull << b) | (1ull << b1));
-  float g = (float)((U[c2] - U[c]) / 2.0 - (double)s_f);
-  if (g > ORC_GUIDE_CLAMP) g = ORC_GUIDE_CLAMP;
-  if (g < -ORC_GUIDE_CLAMP) g = -ORC_GUIDE_CLAMP;
-  uint64_t q = orc_weight_exp(g, ORC_GUIDE_R);
-  return q > 0 ? q : 1;
+  return clamp_k((int64_t)nearbyint(ldexp((U[c2] - U[c]) / 2.0, 17)) - s_q);
 }
 
 static int guided_evolve(int32_t L, int64_t n_clones, double dt, double s, uint32_t beta,
@@ -617,10 +618,11 @@ static int guided_evolve(int32_t L, int64_t n_clones, double dt, double s, uint3
                          int32_t* K, int32_t* dK, float* X) {
   if (L < 10 || n_clones < 1 || !(dt > 0.0)) return ORC_ERR_ARG;
   const float dt_f = (float)dt;
-  const float s_f = (float)s;
-  const float c20s = (float)(ORC_GUIDE_R * 0.693147180559945309417232121458 - s);
+  const int32_t s_q = orc_s_q(s);
+  const float c_s = (float)(ldexp((double)s_q, -17) - s);
+  int32_t* kb = (int32_t*)malloc((size_t)L * sizeof(int32_t));
   uint64_t* q = (uint64_t*)malloc((size_t)L * sizeof(uint64_t));
-  if (!q) return ORC_ERR_ARG;
+  if (!kb || !q) { free(kb); free(q); return ORC_ERR_ARG; }
   for (int64_t j = 0; j < n_clones; ++j) {
     uint8_t* n = sites + j * (int64_t)L;
     float t = 0.0f, a_r = 0.0f, a_h = 0.0f;
@@ -631,7 +633,8 @@ static int guided_evolve(int32_t L, int64_t n_clones, double dt, double s, uint3
       uint64_t R = 0;
       for (int b = 0; b < L; ++b) {
         if (n[b] != n[(b + 1) % L]) {
-          q[b] = rate(L, n, b, ctx, s_f);
+          kb[b] = rate(L, n, b, ctx, s_q);
+          q[b] = orc_guided_q(kb[b]);
           R += q[b];
           ++r;
         } else {
@@ -639,8 +642,10 @@ static int guided_evolve(int32_t L, int64_t n_clones, double dt, double s, uint3
         }
       }
       if (r == 0) break;
-      const float rp = ldexpf(fmaf((float)(uint32_t)(R >> 32), 4294967296.0f,
-                                   (float)(uint32_t)R), -ORC_GUIDE_R);
+      const float Rf = (float)R;               /* one rounding */
+      const float rp = ldexpf(Rf, -40);
+      const int64_t D = (int64_t)((uint64_t)Rf - R);
+      const float eta = (float)D / Rf;
       const float d = (float)r - rp;
       uint32_t w[4];
       philox_at(e, beta, (uint32_t)j, ORC_TAG_GUIDED, seed, w);
@@ -660,7 +665,7 @@ static int guided_evolve(int32_t L, int64_t n_clones, double dt, double s, uint3
         cum += q[i];
         if (q[i] != 0 && cum > kk) { b = i; break; }
       }
-      a_h = a_h + (c20s - orc_ln_spec(q[b]));
+      a_h = a_h + ((c_s - ldexpf((float)(kb[b] + s_q), -17)) - eta);
       const int b1 = (b + 1) % L;
       const uint8_t tmp = n[b];
       n[b] = n[b1];
@@ -671,6 +676,7 @@ static int guided_evolve(int32_t L, int64_t n_clones, double dt, double s, uint3
     K[j] += hops;
     X[j] = a_h - a_r;
   }
+  free(kb);
   free(q);
   return ORC_OK;
 }

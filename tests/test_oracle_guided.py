@@ -2,7 +2,7 @@
 eqs. modpdef and upsdef, with rates e^-s e^{dU/2} from a local potential U), against
 what the mathematics fixes:
 
-* the specified FP32 ln(Q) against FP64 log;
+* the rate tables: Q(k) = 2^40 exp(k 2^-17) to 3e-9, so ln Q is known exactly;
 * the local rate (10 windows around the bond) against U(C') - U(C) summed over all
   L windows, computed here independently in numpy;
 * the importance-sampling identity: E[Upsilon 1{C_dt = y} | C_0] of the guided
@@ -35,16 +35,20 @@ def row_of(mask, L):
     return np.array([(mask >> i) & 1 for i in range(L)], dtype=np.uint8)
 
 
-def test_ln_spec_against_fp64_log():
+def test_guided_rate_tables_have_exact_logarithms():
+    # Q(k) = 2^40 exp(k 2^-17) to 3e-9 relative over the whole clamp range, so the
+    # weight may take ln(2^-40 Q) as k 2^-17; and Q never vanishes
     rng = np.random.default_rng(11)
-    Qs = [1, 2, 3, 5, 7, (1 << 23) - 1, 1 << 23, (1 << 24) + 1, (1 << 40) + 12345, (1 << 63) - 1]
-    Qs += [int(x) for x in rng.integers(1, 1 << 62, size=3000, dtype=np.int64)]
-    Qs += [int(x) for x in rng.integers(1, 1 << 20, size=1000)]
-    for Q in Qs:
-        got = float(oracle.ln_spec(Q))
-        exact = math.log(Q)
-        # 24-bit head of Q (relative 2^-23), the cubic (below 1e-9), FP32 rounding
-        assert abs(got - exact) <= 2.5e-7 + 2.0 ** -22 * abs(exact), (Q, got, exact)
+    ks = list(range(-(1 << 20), -(1 << 20) + 3000)) + list(range(-2000, 2000)) + \
+        list(range((1 << 20) - 3000, (1 << 20) + 1)) + [int(x) for x in rng.integers(-(1 << 20), 1 << 20, 20000)]
+    for k in ks:
+        Q = oracle.guided_q(k)
+        exact = math.ldexp(math.exp(k / 131072.0), 40)
+        assert Q >= 1 and abs(Q - exact) <= 3e-9 * exact + 1.0, (k, Q, exact)
+    assert oracle.guided_q(1 << 20) < 2 ** 52
+    # monotone in k (the cumulative rates order the bonds consistently)
+    qs = [oracle.guided_q(k) for k in range(-5000, 5000)]
+    assert all(b >= a for a, b in zip(qs, qs[1:]))
 
 
 def full_potential(rows, phi_q):
@@ -75,14 +79,10 @@ def test_guided_rate_is_the_global_potential_difference(L):
             hopped = row.copy()
             hopped[b], hopped[b1] = row[b1], row[b]
             dU = int(full_potential(hopped, phi_q)[0] - full_potential(row, phi_q)[0])
-            g = np.float32(np.float32(dU) * np.float32(2.0 ** -17)) - np.float32(s)
-            g = float(min(max(g, np.float32(-8.0)), np.float32(8.0)))
-            want = max(1, oracle.weight_exp(g, 20))
-            assert oracle.guided_rate(row, b, phi, s) == want, (L, trial, b)
-            # and it is e^-s e^{dU/2} in units of 2^-20 to FP32 accuracy, below 2^32
-            exact = math.ldexp(math.exp(min(max(dU / 2.0 ** 17 - s, -8.0), 8.0)), 20)
-            assert abs(want - exact) <= 4e-7 * exact + 1.0
-            assert want < 2 ** 32
+            # the exponent is dU/2 - s in units of 2^-17, exactly (dU is in units of 2^-16)
+            sq = int(round(s * 2 ** 17))
+            want = min(max(dU - sq, -(1 << 20)), 1 << 20)
+            assert oracle.guided_k(row, b, phi, s) == want, (L, trial, b)
 
 
 def test_potential_is_the_window_sum():
