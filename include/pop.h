@@ -60,8 +60,9 @@ extern "C" {
                           FP32 and the weights use a specified FP32 exponential */
 #define POP_GUIDED 2   /* modified dynamics of Sec. 2.2 (eqs. modpdef, upsdef) with a
                           local potential U(C) = sum_i phi(sites i-4..i+4): the hop
-                          across bond b has rate ~ e^-s e^{(U(C^b) - U(C))/2} (held as
-                          an integer in units of 2^-20, exponent clamped to [-8, 8]);
+                          across bond b has rate e^-s e^{(U(C^b) - U(C))/2}, the exponent
+                          rounded to a multiple of 2^-17 and clamped to [-8, 8], held as
+                          an integer in units of 2^-40 whose logarithm is known to 3e-9;
                           Upsilon = prod_hops (e^-s / rate) exp(-int (r - r') dt) of the
                           rates simulated, so the estimate is unbiased for any phi.
                           18 <= L <= 128, and every population of the batch must be
@@ -188,6 +189,69 @@ int pop_density_mode(pop_t* pop, int32_t n, double* h_mean);
  * pop_resample.  May change between intervals.  Waits for the stream.
  */
 int pop_set_potential(pop_t* pop, int32_t p, const float* h_phi);
+
+/*
+ * Ancestry across the last cloning stage (Sec. 2.2: the ancestral population that
+ * defines p_ave is found by following the clones' histories backwards): for every
+ * clone j of every population, d_out[off + j] = d_in[off + anc_j], anc_j the
+ * population-local ancestor written by the last pop_resample and off the
+ * population's first slot.  d_in and d_out are device int32 arrays of
+ * pop_slots() entries; starting from d_in[off + j] = j and applying this after every
+ * cloning stage gives, for each current clone, its ancestor's index at the start.
+ * Needs the per-step calls (pop_run does not record ancestors).  Asynchronous.
+ */
+int pop_lineage(pop_t* pop, const int32_t* d_in, int32_t* d_out);
+
+/* Slots of the batch (populations padded to 1024-slot tiles) and the first slot of
+ * population p; -1 for an invalid handle or p. */
+int64_t pop_slots(pop_t* pop);
+int64_t pop_first_slot(pop_t* pop, int32_t p);
+
+/*
+ * Learned guiding potential: a window network phi (MLP 9 -> 128 -> 128 -> 1, GELU)
+ * trained on the GPU as a classifier of time-averaged (ancestral, label 1) against
+ * end-of-interval (label 0) configurations (Sec. 2.2, eqs. Opave and Opend).  The
+ * logit of a configuration is z = (1/2) sum_i phi(w_i) + c over its L windows w_i
+ * (sites i-4..i+4, bit k = site i-4+k); the loss is the mean of softplus(z) - y z.
+ * Products take BF16 operands with FP32 accumulation; parameters are FP32, in the
+ * order W1[128][9], b1[128], W2[128][128], b2[128], W3[128], b3, c (POP_MLP_PARAMS
+ * floats).  The trained phi, evaluated at the 512 window patterns, is the table that
+ * pop_set_potential takes.
+ */
+#define POP_MLP_HIDDEN 128
+#define POP_MLP_PARAMS 17922
+typedef struct pop_mlp pop_mlp_t;
+
+/* Device workspace of a trainer (bytes, a multiple of 256). */
+size_t pop_mlp_workspace_bytes(void);
+
+/* Create a trainer with parameters h_theta (host, POP_MLP_PARAMS floats) and zero
+ * Adam state in the caller's 256-byte aligned workspace.  Waits for the stream. */
+int pop_mlp_init(pop_mlp_t** out, const float* h_theta, void* d_workspace, size_t workspace_bytes,
+                 void* cuda_stream);
+
+/* Loss and gradient of a batch without updating: d_lattice (device, n x W words, the
+ * configurations as pop_copy_state returns them, 1 <= W <= 2, 9 <= L <= 64 W),
+ * d_labels (device, n bytes, 0 or 1).  h_loss (may be NULL): mean loss; h_grad (may
+ * be NULL): POP_MLP_PARAMS floats.  Waits for the stream. */
+int pop_mlp_grad(pop_mlp_t* mlp, const uint64_t* d_lattice, int32_t W, int32_t L,
+                 const uint8_t* d_labels, int64_t n, double* h_loss, float* h_grad);
+
+/* One Adam step (betas 0.9, 0.999, eps 1e-8) at learning rate lr > 0 on a batch as
+ * above.  Asynchronous unless h_loss is given (then waits and stores the batch loss,
+ * taken before the update). */
+int pop_mlp_step(pop_mlp_t* mlp, const uint64_t* d_lattice, int32_t W, int32_t L,
+                 const uint8_t* d_labels, int64_t n, float lr, double* h_loss);
+
+/* Current parameters (host, POP_MLP_PARAMS floats).  Waits for the stream. */
+int pop_mlp_params(pop_mlp_t* mlp, float* h_theta);
+
+/* The compiled potential: phi at the 512 window patterns (host, 512 floats), from
+ * the current parameters.  Waits for the stream. */
+int pop_mlp_potential(pop_mlp_t* mlp, float* h_phi);
+
+/* Release the trainer (never the caller's workspace). */
+void pop_mlp_free(pop_mlp_t* mlp);
 
 /* Executed hops (BKL events) per population since pop_init (host array of n_pops). */
 int pop_events(pop_t* pop, uint64_t* h_events);

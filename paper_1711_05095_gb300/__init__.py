@@ -33,7 +33,9 @@ POP_MAX_L = 4096
 EXPORTS = ("pop_workspace_bytes", "pop_init", "pop_set_state", "pop_evolve", "pop_resample",
            "pop_run", "pop_estimate_psi", "pop_copy_state", "pop_events", "pop_lattice_words",
            "pop_select_noalloc", "pop_density_mode", "pop_autotune", "pop_kernel_times",
-           "pop_set_potential",
+           "pop_set_potential", "pop_lineage", "pop_slots", "pop_first_slot",
+           "pop_mlp_workspace_bytes", "pop_mlp_init", "pop_mlp_grad", "pop_mlp_step",
+           "pop_mlp_params", "pop_mlp_potential", "pop_mlp_free",
            "pop_launch_count", "pop_strerror", "pop_free")
 KERNEL_KINDS = ("evolve", "weights", "gather", "gather_evolve", "other")
 POP_NOALLOC_MAX_CLONES = 1 << 20
@@ -92,6 +94,30 @@ def library():
     L.pop_density_mode.restype = ctypes.c_int
     L.pop_set_potential.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]
     L.pop_set_potential.restype = ctypes.c_int
+    L.pop_lineage.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.pop_lineage.restype = ctypes.c_int
+    L.pop_slots.argtypes = [ctypes.c_void_p]
+    L.pop_slots.restype = ctypes.c_int64
+    L.pop_first_slot.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+    L.pop_first_slot.restype = ctypes.c_int64
+    _f32p = ctypes.POINTER(ctypes.c_float)
+    L.pop_mlp_workspace_bytes.argtypes = []
+    L.pop_mlp_workspace_bytes.restype = ctypes.c_size_t
+    L.pop_mlp_init.argtypes = [ctypes.POINTER(ctypes.c_void_p), _f32p, ctypes.c_void_p, ctypes.c_size_t,
+                               ctypes.c_void_p]
+    L.pop_mlp_init.restype = ctypes.c_int
+    L.pop_mlp_grad.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                               ctypes.c_int64, _f64p, _f32p]
+    L.pop_mlp_grad.restype = ctypes.c_int
+    L.pop_mlp_step.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                               ctypes.c_int64, ctypes.c_float, _f64p]
+    L.pop_mlp_step.restype = ctypes.c_int
+    L.pop_mlp_params.argtypes = [ctypes.c_void_p, _f32p]
+    L.pop_mlp_params.restype = ctypes.c_int
+    L.pop_mlp_potential.argtypes = [ctypes.c_void_p, _f32p]
+    L.pop_mlp_potential.restype = ctypes.c_int
+    L.pop_mlp_free.argtypes = [ctypes.c_void_p]
+    L.pop_mlp_free.restype = None
     L.pop_events.argtypes = [ctypes.c_void_p, _u64p]
     L.pop_events.restype = ctypes.c_int
     L.pop_kernel_times.argtypes = [ctypes.c_void_p, ctypes.c_double, _f64p, ctypes.c_int64, _f64p,
@@ -221,6 +247,23 @@ class PopulationBatch:
         g = ctypes.c_int32(0)
         _check(self._lib.pop_autotune(self._h, float(dt), sp, int(trials), ctypes.byref(g)), "pop_autotune")
         return int(g.value)
+
+    @property
+    def slots(self):
+        """Slots of the batch (populations padded to 1024-slot tiles)."""
+        return int(self._lib.pop_slots(self._h))
+
+    def first_slot(self, p):
+        return int(self._lib.pop_first_slot(self._h, int(p)))
+
+    def lineage(self, d_in, d_out):
+        """d_out[off + j] = d_in[off + anc_j] across the last cloning stage (torch int32
+        tensors of ``slots`` entries on the batch's device)."""
+        for t in (d_in, d_out):
+            if t.dtype != __import__("torch").int32 or t.numel() < self.slots or not t.is_cuda:
+                raise PopError(POP_ERR_ARG, "lineage buffers")
+        _check(self._lib.pop_lineage(self._h, ctypes.c_void_p(d_in.data_ptr()), ctypes.c_void_p(d_out.data_ptr())),
+               "pop_lineage")
 
     def set_potential(self, p, phi):
         """GUIDED population p: the 512-entry window potential (|phi| <= 64)."""

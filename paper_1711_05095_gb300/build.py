@@ -4,7 +4,8 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SOURCES = [os.path.join(HERE, "csrc", "pop_api.cu"), os.path.join(HERE, "csrc", "pop_noalloc.cu")]
+SOURCES = [os.path.join(HERE, "csrc", "pop_api.cu"), os.path.join(HERE, "csrc", "pop_noalloc.cu"),
+           os.path.join(HERE, "csrc", "pop_mlp.cu")]
 DEPS = SOURCES + [os.path.join(HERE, "csrc", "pop_common.cuh"), os.path.join(HERE, "csrc", "pop_kernels.cuh"), os.path.join(ROOT, "include", "pop.h")]
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpopgb300.so")

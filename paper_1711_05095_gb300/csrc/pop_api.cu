@@ -33,7 +33,7 @@ constexpr int kGraphIntervals = 32;
 struct Layout {
   int32_t P = 0, W = 0, ntiles = 0, nunits = 0;
   int64_t nslots = 0;
-  size_t o_pops, o_st, o_tile_pop, o_wtab, o_qtab, o_qm1tab, o_inv, o_logtab, o_exp2, o_A, o_S, o_cs, o_tacc, o_hist, o_tile_sum, o_beta, o_phi,
+  size_t o_pops, o_st, o_tile_pop, o_wtab, o_qtab, o_qm1tab, o_inv, o_logtab, o_exp2, o_A, o_S, o_cs, o_tacc, o_hist, o_tile_sum, o_beta, o_phi, o_gtab,
       o_ksum, o_X, o_Y, o_KX, o_KY, o_dK, o_anc, total;
 };
 
@@ -89,6 +89,7 @@ bool make_layout(const pop_params* params, int32_t n_pops, Layout* lay) {
   l.o_beta = take(sizeof(unsigned int));
   l.o_ksum = take(P * sizeof(long long));
   l.o_phi = take(P * 512 * sizeof(int32_t));
+  l.o_gtab = take((kGuideTabA + kGuideTabB) * sizeof(unsigned long long));
   l.o_X = take(2 * ns * (size_t)l.W * sizeof(unsigned long long));
   l.o_Y = take(ns * (size_t)l.W * sizeof(unsigned long long));
   l.o_KX = take(2 * ns * sizeof(int32_t));
@@ -184,8 +185,8 @@ int fix_biases(pop_t* h, const double* s) {
     h->desc[p].abs_s = a;
     h->desc[p].s_neg = s[p] < 0.0 ? 1 : 0;
     h->desc[p].c_f = (float)(-std::expm1(-s[p]));
-    h->desc[p].s_f = (float)s[p];
-    h->desc[p].c20s = (float)((double)kGuideR * 0.693147180559945309417232121458 - s[p]);
+    h->desc[p].s_q = (int32_t)std::nearbyint(std::ldexp(s[p], 17));
+    h->desc[p].c_s = (float)(std::ldexp((double)h->desc[p].s_q, -17) - s[p]);
   }
   // MODIFIED dynamics: every rate times e^-s, so the waiting-time factor is e^s / r
   std::vector<float> inv_mod;
@@ -419,8 +420,8 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
     d.iid = params[p].selection == POP_IID ? 1 : 0;
     d.F = 61 - ceil_log2(params[p].n_clones);
     d.c_f = 0.0f;
-    d.s_f = 0.0f;
-    d.c20s = 0.0f;
+    d.s_q = 0;
+    d.c_s = 0.0f;
     h->guided = d.guided != 0;
     h->any_mod = h->any_mod || d.modified;
     h->B.any_iid = h->B.any_iid || d.iid;
@@ -447,6 +448,13 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
       q.a_max[par] = INT_MIN;
     }
   }
+  // GUIDED rate tables: TA[a] = nearest(2^44 exp(a/64 - 8)), TB[c] = nearest(2^40 exp(c/2^17))
+  std::vector<unsigned long long> gtab((size_t)(kGuideTabA + kGuideTabB));
+  for (int a = 0; a < kGuideTabA; ++a)
+    gtab[(size_t)a] = (unsigned long long)std::nearbyint(std::ldexp(std::exp(a / 64.0 - 8.0), 44));
+  for (int c = 0; c < kGuideTabB; ++c)
+    gtab[(size_t)kGuideTabA + c] =
+        (unsigned long long)std::nearbyint(std::ldexp(std::exp(c / 131072.0), 40));
   // MODIFIED weight exponential: 2^(i/64)
   std::vector<float> exp2tab(64);
   for (int i = 0; i < 64; ++i) exp2tab[i] = (float)std::exp2((double)i / 64.0);
@@ -465,6 +473,8 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
       cudaMemcpyAsync(ws + lay.o_logtab, logtab.data(), logtab.size() * sizeof(float2),
                       cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
       cudaMemcpyAsync(ws + lay.o_exp2, exp2tab.data(), exp2tab.size() * sizeof(float),
+                      cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(ws + lay.o_gtab, gtab.data(), gtab.size() * sizeof(unsigned long long),
                       cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
       cudaMemcpyAsync(ws + lay.o_beta, &beta0, sizeof beta0, cudaMemcpyHostToDevice,
                       h->stream) != cudaSuccess)
@@ -487,6 +497,7 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
   B.tile_sum = (unsigned long long*)(ws + lay.o_tile_sum);
   B.beta = (unsigned int*)(ws + lay.o_beta);
   B.phi = (const int32_t*)(ws + lay.o_phi);
+  B.gtab = (const unsigned long long*)(ws + lay.o_gtab);
   B.ksum = (long long*)(ws + lay.o_ksum);
   B.Xb[0] = (unsigned long long*)(ws + lay.o_X);
   B.Xb[1] = B.Xb[0] + lay.nslots * lay.W;
@@ -773,6 +784,21 @@ int pop_set_potential(pop_t* h, int32_t p, const float* h_phi) {
                            512 * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
   POP_CUDA(cudaStreamSynchronize(h->stream));
   return POP_OK;
+}
+
+int pop_lineage(pop_t* h, const int32_t* d_in, int32_t* d_out) {
+  if (h == nullptr || d_in == nullptr || d_out == nullptr || d_in == d_out) return POP_ERR_ARG;
+  if (h->intervals == 0 || h->phase != kReady) return POP_ERR_STATE;
+  h->launches[POP_K_OTHER] += 1;
+  k_lineage<<<(unsigned)(h->lay.nslots / kThreads), kThreads, 0, h->stream>>>(h->B, d_in, d_out);
+  return cuda_status(cudaGetLastError());
+}
+
+int64_t pop_slots(pop_t* h) { return h == nullptr ? -1 : h->lay.nslots; }
+
+int64_t pop_first_slot(pop_t* h, int32_t p) {
+  if (h == nullptr || p < 0 || p >= h->lay.P) return -1;
+  return h->desc[p].off;
 }
 
 int pop_events(pop_t* h, uint64_t* h_events) {

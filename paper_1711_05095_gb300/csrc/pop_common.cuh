@@ -48,9 +48,9 @@ constexpr uint32_t kStepLimit = 1u << 24; // BKL steps per clone per interval
 
 constexpr int32_t kErrRange = -3;
 
-// GUIDED dynamics: hop rates in units of 2^-kGuideR, exponent clamped to +-kGuideClamp.
-constexpr int kGuideR = 20;
-constexpr float kGuideClamp = 8.0f;
+// GUIDED dynamics: hop rates 2^-40 Q(k), Q(k) = 2^40 exp(k 2^-17), |k| <= kGuideKmax.
+constexpr int kGuideKmax = 1 << 20;
+constexpr int kGuideTabA = 1025, kGuideTabB = 2048;
 constexpr uint32_t kTagGuided = 5u;
 
 // Constant per run.
@@ -68,8 +68,8 @@ struct PopDesc {
   int32_t guided;    // GUIDED dynamics and weights (local potential; modified is also set)
   double s;          // bias
   double abs_s;
-  float s_f;         // float(s)
-  float c20s;        // GUIDED: float(20 ln 2 - s), the per-hop weight constant
+  int32_t s_q;       // GUIDED: s in units of 2^-17 (nearest integer)
+  float c_s;         // GUIDED: float(s_q 2^-17 - s)
 };
 
 // Mutable per population.
@@ -100,6 +100,7 @@ struct Batch {
   const float2* logtab;                 // [64] (1/c_i, ln c_i) of the waiting-time log
   const float* exp2tab;                 // [64] 2^(i/64) of the MODIFIED weight exponential
   const int32_t* phi;                   // GUIDED: [P][512] potential, fixed point phi 2^16
+  const unsigned long long* gtab;       // GUIDED: TA[1025] then TB[2048], the rate tables
   float* Ab[2];                         // MODIFIED: rate integral, by interval parity
   unsigned long long* S;                // [iid]: exclusive prefix sums of the weights
   unsigned int* hist;                   // [P][kKcap] activity histogram (zero between intervals)

@@ -802,21 +802,25 @@ __global__ void __launch_bounds__(kThreads) k_select_iid(Batch B) {
 // ---------------------------------------------------------------------------
 // GUIDED dynamical stage (Sec. 2.2, eqs. modpdef and upsdef, with a local potential
 // U(C) = sum_i phi(sites i-4..i+4) in place of the uniform e^-s of Sec. 3.2).  The hop
-// across active bond b has rate Q_b 2^-20, Q_b = max(1, floor(2^20 exp_spec(g_b))),
-// g_b = float(dU_b) 2^-17 - float(s) clamped to [-8, 8], dU_b = U(C^b) - U(C) from the
-// ten windows that contain the bond's sites (exact fixed-point integers).  One clone
-// per thread; its rates live in shared memory (bond-major, so the threads of a warp
-// never share a bank), with sums over groups of 16 bonds for the bond choice.  After a
-// hop only the 19 bonds whose windows see the two flipped sites get new rates.
-// Step e uses draw (e, beta, j, 5): E = -ln u(w0); tau = E / r' (r' = R 2^-20 as a
-// float); the bond is the first whose cumulative Q exceeds floor((w2 2^32 + w1) R / 2^64).
-// Log weight of the interval, in FP32:
-//   X = sum_hops (float(20 ln 2 - s) - ln_spec(Q_b)) - sum_segments (r - r') tau,
-// the weight of the rates actually simulated (so unbiased for any potential).
-// Requires 18 <= L <= 128.
+// across active bond b has rate 2^-40 Q(k_b), Q(k) = floor(TA[a] TB[c] / 2^44) =
+// 2^40 exp(k 2^-17) to 3e-9 (k + 2^20 = 2^11 a + c), with the exponent
+// k_b = clamp(dU_b - s_q, +-2^20): dU_b = U(C^b) - U(C) from the ten windows that
+// contain the bond's sites (exact fixed-point integers), s_q = s in units of 2^-17.
+// One clone per thread; its exponents live in shared memory (bond-major, so the
+// threads of a warp never share a bank), with rate sums over groups of 16 bonds for
+// the bond choice.  After a hop only the 19 bonds whose windows see the two flipped
+// sites get new exponents.  Step e uses draw (e, beta, j, 5): E = -ln u(w0);
+// r'_f = float(R) 2^-40 with R = sum Q; tau = E / r'_f; the bond is the first whose
+// cumulative Q exceeds floor((w2 2^32 + w1) R / 2^64).  Log weight in FP32, every term
+// formed at its own size (no large terms that cancel):
+//   X = sum_hops ((c_s - float(k_b + s_q) 2^-17) - eta) - sum_segments (r - r'_f) tau,
+// c_s = float(s_q 2^-17 - s), eta = (2^40 r'_f - R) / R the rounding of the total rate;
+// this is the weight of the rates simulated, so the estimate is unbiased for any
+// potential.  Requires 18 <= L <= 128.
 // ---------------------------------------------------------------------------
 constexpr int kGuideThreads = 64;
 constexpr int kGuideGroup = 16;
+constexpr int kGuideOff = INT_MIN;  // exponent slot of an inactive bond
 
 // 18 sites starting at `start` (site start + k is bit k), 18 <= L, ring wrap included.
 template <int W>
@@ -841,10 +845,10 @@ __device__ __forceinline__ uint32_t guided_seg(const unsigned long long (&x)[W],
   }
 }
 
+// Rate exponent of the hop across active bond b.
 template <int W>
-__device__ __forceinline__ uint32_t guided_rate(const unsigned long long (&x)[W], int L, int b,
-                                                const int32_t* phi, float s_f,
-                                                const float* exp2tab) {
+__device__ __forceinline__ int guided_k(const unsigned long long (&x)[W], int L, int b,
+                                        const int32_t* phi, int s_q) {
   int start = b - 8;
   if (start < 0) start += L;
   const uint32_t seg = guided_seg<W>(x, L, start);
@@ -852,34 +856,22 @@ __device__ __forceinline__ uint32_t guided_rate(const unsigned long long (&x)[W]
   int dU = 0;
 #pragma unroll
   for (int m = 0; m < 10; ++m) dU += phi[(seg2 >> m) & 511u] - phi[(seg >> m) & 511u];
-  float g = __fsub_rn(__fmul_rn(__int2float_rn(dU), 0x1p-17f), s_f);
-  g = fminf(fmaxf(g, -kGuideClamp), kGuideClamp);
-  const unsigned long long q = weight_exp(g, kGuideR, exp2tab);
-  return q > 0ull ? (uint32_t)q : 1u;
+  return min(max(dU - s_q, -kGuideKmax), kGuideKmax);
 }
 
-// ln(Q) in FP32 for an integer Q >= 1: the construction of neg_ln_u applied to the
-// 24 leading bits of Q (Q = m 2^p, ln Q = p ln 2 + ln m).
-__device__ __forceinline__ float ln_spec(uint32_t Q, const float2* tab) {
-  const int p = 31 - __clz((int)Q);
-  const uint32_t t = (p >= 23) ? (Q >> (p - 23)) : (Q << (23 - p));
-  const float m = __uint_as_float(0x3f800000u | (t & 0x007fffffu));
-  const float2 cl = tab[(t >> 17) & 63u];
-  const float r = __fmaf_rn(m, cl.x, -1.0f);
-  float q = __fmaf_rn(r, 0x1.555556p-2f, -0.5f);
-  q = __fmaf_rn(q, r, 1.0f);
-  const float ln_m = __fadd_rn(cl.y, __fmul_rn(q, r));
-  const float pf = __int2float_rn(p);
-  const float lq = __fmaf_rn(pf, 0x1.7f7d1cp-20f, ln_m);
-  return __fmaf_rn(pf, 0x1.62e4p-1f, lq);
+// Q(k) = floor(TA[a] TB[c] / 2^44); 0 for an inactive bond.
+__device__ __forceinline__ unsigned long long guided_q(int k, const unsigned long long* tab) {
+  if (k == kGuideOff) return 0ull;
+  const uint32_t u = (uint32_t)(k + kGuideKmax);
+  const unsigned long long ta = __ldg(tab + (u >> 11)), tb = __ldg(tab + kGuideTabA + (u & 2047u));
+  return (__umul64hi(ta, tb) << 20) | ((ta * tb) >> 44);
 }
 
 template <int W>
 __global__ void __launch_bounds__(kGuideThreads) k_evolve_guided(Batch B, float dt_f) {
   __shared__ int32_t s_phi[512];
-  __shared__ float s_exp2[64];
   __shared__ float2 s_log[64];
-  __shared__ uint32_t s_q[kMaxL][kGuideThreads];
+  __shared__ int32_t s_k[kMaxL][kGuideThreads];
   __shared__ unsigned long long s_g[kMaxL / kGuideGroup][kGuideThreads];
   __shared__ int s_min, s_max, s_amin, s_amax;
   __shared__ unsigned int s_ev;
@@ -888,7 +880,6 @@ __global__ void __launch_bounds__(kGuideThreads) k_evolve_guided(Batch B, float 
   const int p = B.tile_pop[slot0 / kTile];
   const PopDesc d = B.pops[p];
   for (int i = tid; i < 512; i += kGuideThreads) s_phi[i] = B.phi[(size_t)p * 512 + i];
-  s_exp2[tid] = B.exp2tab[tid];
   s_log[tid] = B.logtab[tid];
   if (tid == 0) {
     s_min = INT_MAX;
@@ -903,11 +894,12 @@ __global__ void __launch_bounds__(kGuideThreads) k_evolve_guided(Batch B, float 
   const int64_t slot = slot0 + tid;
   const int64_t j = slot - d.off;
   const int L = d.L;
+  const unsigned long long* tab = B.gtab;
   if (j < d.nc) {
     unsigned long long x[W];
     load_lat<W>(B.Y, slot, x);
     const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
-    // rates of every bond, group sums, total
+    // exponents and rates of every bond, group sums, total
     unsigned long long a[W];
     active_bonds<W>(x, L, a);
     int r = popc_lat<W>(a);
@@ -915,10 +907,10 @@ __global__ void __launch_bounds__(kGuideThreads) k_evolve_guided(Batch B, float 
     for (int g = 0; g < kMaxL / kGuideGroup; ++g) {
       unsigned long long gs = 0ull;
       for (int b = g * kGuideGroup; b < (g + 1) * kGuideGroup; ++b) {
-        uint32_t q = 0u;
-        if (b < L && ((a[b >> 6] >> (b & 63)) & 1ull)) q = guided_rate<W>(x, L, b, s_phi, d.s_f, s_exp2);
-        s_q[b][tid] = q;
-        gs += q;
+        int k = kGuideOff;
+        if (b < L && ((a[b >> 6] >> (b & 63)) & 1ull)) k = guided_k<W>(x, L, b, s_phi, d.s_q);
+        s_k[b][tid] = k;
+        gs += guided_q(k, tab);
       }
       s_g[g][tid] = gs;
       R += gs;
@@ -931,9 +923,10 @@ __global__ void __launch_bounds__(kGuideThreads) k_evolve_guided(Batch B, float 
         B.st[p].err = kErrRange;
         break;
       }
-      const float rp = __fmul_rn(__fmaf_rn(__uint2float_rn((uint32_t)(R >> 32)), 4294967296.0f,
-                                           __uint2float_rn((uint32_t)R)),
-                                 0x1p-20f);
+      const float Rf = __ull2float_rn(R);
+      const float rp = __fmul_rn(Rf, 0x1p-40f);
+      const long long D = (long long)(__float2ull_rz(Rf) - R);
+      const float eta = __fdiv_rn(__ll2float_rn(D), Rf);
       const float dr = __fsub_rn(__int2float_rn(r), rp);
       const uint4 w = philox4x32_10(make_uint4(e, beta, (uint32_t)j, kTagGuided), k0, k1);
       const float E = neg_ln_u(w.x, s_log);
@@ -946,9 +939,8 @@ __global__ void __launch_bounds__(kGuideThreads) k_evolve_guided(Batch B, float 
       a_r = __fmaf_rn(dr, tau, a_r);
       t = t_new;
       const unsigned long long kk = __umul64hi(((unsigned long long)w.z << 32) | w.y, R);
-      // the first bond whose inclusive cumulative rate exceeds kk
-      // (kk < R = the sum of the group sums, so both loops stop inside the arrays;
-      // the index bounds only make that explicit)
+      // the first bond whose inclusive cumulative rate exceeds kk (kk < R = the sum of
+      // the group sums, so both loops stop inside the arrays; the bounds make it explicit)
       unsigned long long cum = 0ull;
       int g = 0;
       while (g < kMaxL / kGuideGroup - 1 && cum + s_g[g][tid] <= kk) {
@@ -957,27 +949,28 @@ __global__ void __launch_bounds__(kGuideThreads) k_evolve_guided(Batch B, float 
       }
       int b = g * kGuideGroup;
       for (; b < kMaxL - 1; ++b) {
-        cum += s_q[b][tid];
+        cum += guided_q(s_k[b][tid], tab);
         if (cum > kk) break;
       }
-      a_h = __fadd_rn(a_h, __fsub_rn(d.c20s, ln_spec(s_q[b][tid], s_log)));
+      const int kb = s_k[b][tid];
+      a_h = __fadd_rn(a_h, __fsub_rn(__fsub_rn(d.c_s, __fmul_rn(__int2float_rn(kb + d.s_q), 0x1p-17f)),
+                                     eta));
       hop<W>(x, b, L);
       ++h;
       active_bonds<W>(x, L, a);
       r = popc_lat<W>(a);
-      // new rates for the bonds whose windows contain site b or b+1
+      // new exponents for the bonds whose windows contain site b or b+1
       for (int db = -9; db <= 9; ++db) {
         int c = b + db;
         if (c < 0) c += L;
         if (c >= L) c -= L;
-        const uint32_t q = ((a[c >> 6] >> (c & 63)) & 1ull)
-                               ? guided_rate<W>(x, L, c, s_phi, d.s_f, s_exp2) : 0u;
-        const uint32_t old = s_q[c][tid];
-        if (q != old) {
-          s_q[c][tid] = q;
-          const long long diff = (long long)q - (long long)old;
-          s_g[c / kGuideGroup][tid] += (unsigned long long)diff;
-          R += (unsigned long long)diff;
+        const int kn = ((a[c >> 6] >> (c & 63)) & 1ull) ? guided_k<W>(x, L, c, s_phi, d.s_q) : kGuideOff;
+        const int ko = s_k[c][tid];
+        if (kn != ko) {
+          s_k[c][tid] = kn;
+          const unsigned long long qn = guided_q(kn, tab), qo = guided_q(ko, tab);
+          s_g[c / kGuideGroup][tid] += qn - qo;
+          R += qn - qo;
         }
       }
     }
@@ -1162,6 +1155,13 @@ __global__ void __launch_bounds__(kThreads) k_density(Batch B, const float2* cs,
 }
 
 // Sum of the carried activities of each population (for k_hat, eq. khat).
+// Ancestry across the last cloning stage: out[off + j] = in[off + anc_j].
+__global__ void __launch_bounds__(kThreads) k_lineage(Batch B, const int32_t* in, int32_t* out) {
+  const int64_t slot = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  const PopDesc d = B.pops[B.tile_pop[slot / kTile]];
+  if (slot - d.off < d.nc) out[slot] = in[d.off + B.anc[slot]];
+}
+
 __global__ void __launch_bounds__(kThreads) k_ksum(Batch B) {
   __shared__ long long s_part[kWarps];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
