@@ -77,6 +77,7 @@ def parse():
     ap.add_argument("--intervals", type=int, default=None,
                     help="override M (profiling runs only; the bench line then names it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-guided", action="store_true", help="skip the guided-cloning SE measurement")
     ap.add_argument("--kernel-intervals", type=int, default=200)
     return ap.parse_args()
 
@@ -345,6 +346,52 @@ def main():
     sigma = float(np.std(psi_se, ddof=1))
     se_runs, se_seconds = seconds_to_se(sigma, se_batch_s, len(se_pops))
     del ws_se
+
+    # the same target with GUIDED cloning under a learned window potential: the
+    # potential is trained on the GPU from end / ancestral configurations of plain
+    # runs of this population (4 x 8192 clones, 1000 + 1000 intervals), then 64 seeds
+    # at N_c = 4096 run the full t_obs (training time counted separately)
+    guided = None
+    if not args.no_guided:
+        from paper_1711_05095_gb300 import potential as pot
+        q0 = w["pops"][0]
+        g_s = 20.0 / q0["L"] ** 2
+        t_g0 = time.perf_counter()
+        dpops = [dict(q0, n_clones=8192, seed=600000 + 1000 * rank + i) for i in range(4)]
+        end, anc = pot.ancestral_samples(dpops, [g_s] * 4, dt, 1000, 1000, device=dev)
+        cut = 8192 * 3
+        tr, _ = pot.train(end[:cut], anc[:cut], q0["L"], steps=600, batch_size=8192, lr=2e-3, device=dev)
+        held = pot.classifier_loss(tr, end[cut:], anc[cut:], q0["L"], device=dev)
+        phi = tr.potential()
+        tr.close()
+        t_train = time.perf_counter() - t_g0
+        gpops = [dict(q, n_clones=4096, weight_mode=pg.POP_GUIDED) for q in se_pops]
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        g0.record(stream)
+        b = pg.PopulationBatch(gpops, device=dev, stream=stream)
+        for p_ in range(len(gpops)):
+            b.set_potential(p_, phi)
+        b.run(dt, se_w["s"], M)
+        psi_g, _, _ = b.estimate_psi()
+        g1.record(stream)
+        g1.synchronize()
+        ev_g = int(b.events().sum())
+        b.close()
+        g_batch = g0.elapsed_time(g1) / 1e3
+        sig_g = float(np.std(psi_g, ddof=1))
+        g_runs, g_seconds = seconds_to_se(sig_g, g_batch, len(gpops))
+        se_comb = float(np.hypot(sig_g, sigma) / np.sqrt(len(gpops)))
+        guided = {"value": g_seconds, "unit": "s", "target_se": 1e-3,
+                  "workload": "L=50 N=25 lambda=20 N_c=4096 dt=0.1 t_obs=%g, GUIDED with a learned "
+                              "window potential" % w["t_obs"],
+                  "sigma_per_run": sig_g, "runs_needed": g_runs, "batch_runs": len(gpops),
+                  "batch_seconds": g_batch, "clone_events_per_s": ev_g / g_batch,
+                  "mean_psi": float(np.mean(psi_g)),
+                  "z_vs_plain": (float(np.mean(psi_g)) - float(np.mean(psi_se))) / se_comb,
+                  "classifier_heldout_loss": float(held), "classifier_chance_loss": float(np.log(2.0)),
+                  "training_seconds": t_train}
     ops_per_launch = (OPS_HOP * hops_k + (OPS_STOP + OPS_GATHER) * clone_intervals * n_k) / n_k
     peaks, peak_kind = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -377,6 +424,7 @@ def main():
                           "sigma_per_run": sigma, "runs_needed": se_runs,
                           "batch_runs": len(se_pops), "batch_seconds": se_batch_s,
                           "mean_psi": float(np.mean(psi_se)), "method": "plain cloning"},
+        "seconds_to_se_guided": guided,
         "clocks": clocks,
         "wall_s_timed": wall,
         "psi_check": {"lambda=-20": float(psi[0]), "lambda=40": float(psi[-1])},
