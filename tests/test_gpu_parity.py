@@ -123,6 +123,15 @@ RUN_CASES = {
                      dict(L=50, N=25, n_clones=900, seed=16, weight_mode=1)], [0.1, -0.05], [35]),
     # a single interval: the fused run's first and last stages only
     "one_interval": ([dict(L=40, N=20, n_clones=3000, seed=17)], [0.2], [1]),
+    # runs of 1, 2, 3 and 40 intervals; a population of 64 full tiles beside one of a
+    # single ragged tile; s < 0
+    "many_splits": ([dict(L=50, N=25, n_clones=64 * 1024, seed=18), dict(L=20, N=10, n_clones=700, seed=19)],
+                    [0.01, -0.3], [1, 2, 3, 40]),
+    # one population of 65 tiles and a ragged last tile
+    "tiles_65": ([dict(L=30, N=15, n_clones=65 * 1024 + 5, seed=20)], [0.05], [35]),
+    # strong bias: a wide activity range and tiles whose old clones leave no copies
+    "strong_bias": ([dict(L=64, N=32, n_clones=5000, seed=21), dict(L=128, N=64, n_clones=3000, seed=22)],
+                    [2.0, 0.5], [34]),
 }
 
 
