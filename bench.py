@@ -78,6 +78,7 @@ def parse():
                     help="override M (profiling runs only; the bench line then names it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-guided", action="store_true", help="skip the guided-cloning SE measurement")
+    ap.add_argument("--no-others", action="store_true", help="skip the other batch shapes")
     ap.add_argument("--kernel-intervals", type=int, default=200)
     return ap.parse_args()
 
@@ -327,6 +328,34 @@ def main():
     t_k = t_k_us / 1e6
     clone_intervals = sum(q["n_clones"] for q in pops)
 
+    # the other batch shapes of the method, bounded runs (device time of `intervals`
+    # intervals through pop_run after 32 warm-up intervals): two-word lattices at
+    # N_c = 2^20 per population, and 256 uneven populations
+    others = {}
+    if not args.no_others:
+        for name, wl, n_iv in (("large_population", workloads.large_population(), 200),
+                               ("uneven_batch", workloads.uneven_batch(), 200)):
+            b = pg.PopulationBatch(wl["pops"], device=dev, stream=stream)
+            b.run(wl["dt"], wl["s"], 32)
+            ev0 = int(b.events().sum())
+            o0 = torch.cuda.Event(enable_timing=True)
+            o1 = torch.cuda.Event(enable_timing=True)
+            o0.record(stream)
+            b.run(wl["dt"], wl["s"], n_iv)
+            o1.record(stream)
+            o1.synchronize()
+            sec_o = o0.elapsed_time(o1) / 1e3
+            ev_o = int(b.events().sum()) - ev0
+            clones = sum(q["n_clones"] for q in wl["pops"])
+            others[name] = {"value": ev_o / sec_o, "unit": UNIT, "populations": len(wl["pops"]),
+                            "clones": clones, "intervals_timed": n_iv, "ms_per_interval": 1e3 * sec_o / n_iv,
+                            "workload": wl["pops"][0]["L"] if name == "large_population" else "mixed L"}
+            b.close()
+        others["large_population"]["workload"] = ("L=128 N=64 lambda in {5,10,15,20} x 8 seeds, "
+                                                  "N_c=2^20 each, dt=0.05")
+        others["uneven_batch"]["workload"] = ("256 populations, L in {32,64,100,128}, N_c in [2^10, 2^18], "
+                                              "lambda in [-10, 30], dt=0.1")
+
     # seconds to SE(psi_hat) <= 1e-3 at lambda = 20 (s = 0.008): 64 independent seeds
     # of the same population, one batch, full t_obs
     se_w = workloads.seed_replicas(w["pops"][0], 20.0 / 50**2, 64, seed=500000 + 1000 * rank)
@@ -428,6 +457,7 @@ def main():
         "clocks": clocks,
         "wall_s_timed": wall,
         "psi_check": {"lambda=-20": float(psi[0]), "lambda=40": float(psi[-1])},
+        "other_workloads": others,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         idx = list(range(0, 64, 8))
