@@ -350,6 +350,23 @@ def main():
             others[name] = {"value": ev_o / sec_o, "unit": UNIT, "populations": len(wl["pops"]),
                             "clones": clones, "intervals_timed": n_iv, "ms_per_interval": 1e3 * sec_o / n_iv,
                             "workload": wl["pops"][0]["L"] if name == "large_population" else "mixed L"}
+            if name == "large_population":
+                # the separate cloning stage (k_gather) on a working set far above L2:
+                # algorithmic bytes per clone = old lattice 8W + K 4 + dK 4 read, new
+                # lattice 8W + K 4 + ancestor 4 written
+                kt_g = b.kernel_times(wl["dt"], wl["s"], 8, per_step=True)
+                W_g = pg.lattice_words(wl["pops"])
+                bytes_g = clones * (2 * (8 * W_g + 8))
+                t_g = kt_g["gather"][0] / 1e6
+                peaks_g, kind_g = measured_peaks()
+                hbm = float(peaks_g.get("hbm_gbs", 6800.0))
+                others["gather_roofline"] = {
+                    "bound": "hbm", "kernel": "k_gather (separate cloning stage, two-word lattices)",
+                    "achieved": bytes_g / t_g / 1e9, "peak": hbm, "unit": "GB/s",
+                    "frac": bytes_g / t_g / 1e9 / hbm, "bytes_per_launch": bytes_g,
+                    "launch_us": kt_g["gather"][0], "weights_us": kt_g["weights"][0],
+                    "workload": "large_population, 2^25 clones, %d B per clone" % (2 * (8 * W_g + 8)),
+                    "peak_kind": "measured copy bandwidth (%s)" % kind_g}
             b.close()
         others["large_population"]["workload"] = ("L=128 N=64 lambda in {5,10,15,20} x 8 seeds, "
                                                   "N_c=2^20 each, dt=0.05")

@@ -267,8 +267,10 @@ int pop_events(pop_t* pop, uint64_t* h_events);
 
 /*
  * Measurement.  Advances the batch by n_intervals >= 1 intervals with exactly the
- * kernels pop_run uses, in the same order (so with the same results), but launched
- * one by one, each between two CUDA events recorded on the handle's stream.  Any
+ * kernels pop_run uses (per_step = 0) or those of pop_evolve + pop_resample
+ * (per_step = 1: the separate dynamical and cloning stages), in the same order and so
+ * with the same results, but launched one by one, each between two CUDA events
+ * recorded on the handle's stream.  Any
  * output may be NULL; each is a host array of POP_NKINDS:
  *   h_us    mean device time of the launches of each kind, microseconds (0 if none)
  *   h_n     number of launches of each kind
@@ -277,8 +279,8 @@ int pop_events(pop_t* pop, uint64_t* h_events);
  * Fixes s like pop_evolve.  POP_ERR_STATE between pop_evolve and pop_resample.
  * Waits for the stream.
  */
-int pop_kernel_times(pop_t* pop, double dt, const double* s, int64_t n_intervals, double* h_us,
-                     int64_t* h_n, uint64_t* h_hops);
+int pop_kernel_times(pop_t* pop, double dt, const double* s, int64_t n_intervals, int32_t per_step,
+                     double* h_us, int64_t* h_n, uint64_t* h_hops);
 
 /*
  * Kernels launched by this handle since pop_init, by kind (host array of

@@ -120,7 +120,7 @@ def library():
     L.pop_mlp_free.restype = None
     L.pop_events.argtypes = [ctypes.c_void_p, _u64p]
     L.pop_events.restype = ctypes.c_int
-    L.pop_kernel_times.argtypes = [ctypes.c_void_p, ctypes.c_double, _f64p, ctypes.c_int64, _f64p,
+    L.pop_kernel_times.argtypes = [ctypes.c_void_p, ctypes.c_double, _f64p, ctypes.c_int64, ctypes.c_int32, _f64p,
                                    ctypes.POINTER(ctypes.c_int64), _u64p]
     L.pop_kernel_times.restype = ctypes.c_int
     L.pop_launch_count.argtypes = [ctypes.c_void_p, _u64p]
@@ -271,15 +271,16 @@ class PopulationBatch:
         _check(self._lib.pop_set_potential(self._h, int(p), phi.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
                "pop_set_potential")
 
-    def kernel_times(self, dt, s, n):
-        """Advance n intervals as run() does, timing every launch with CUDA events.
+    def kernel_times(self, dt, s, n, per_step=False):
+        """Advance n intervals as run() does (or as evolve() + resample() with
+        per_step), timing every launch with CUDA events.
         Returns {kind: (mean microseconds, launches, hops)}."""
         s, sp = self._s(s)
         k = len(KERNEL_KINDS)
         us = np.zeros(k)
         cnt = np.zeros(k, dtype=np.int64)
         hops = np.zeros(k, dtype=np.uint64)
-        _check(self._lib.pop_kernel_times(self._h, float(dt), sp, int(n), us.ctypes.data_as(_f64p),
+        _check(self._lib.pop_kernel_times(self._h, float(dt), sp, int(n), int(bool(per_step)), us.ctypes.data_as(_f64p),
                                           cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                           hops.ctypes.data_as(_u64p)), "pop_kernel_times")
         return {name: (float(us[i]), int(cnt[i]), int(hops[i])) for i, name in enumerate(KERNEL_KINDS)}

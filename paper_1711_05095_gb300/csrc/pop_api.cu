@@ -649,8 +649,8 @@ int pop_run(pop_t* h, double dt, const double* s, int64_t n_intervals) {
   return POP_OK;
 }
 
-int pop_kernel_times(pop_t* h, double dt, const double* s, int64_t n_intervals, double* h_us,
-                     int64_t* h_n, uint64_t* h_hops) {
+int pop_kernel_times(pop_t* h, double dt, const double* s, int64_t n_intervals, int32_t per_step,
+                     double* h_us, int64_t* h_n, uint64_t* h_hops) {
   if (h == nullptr || !valid_dt(dt) || n_intervals < 1) return POP_ERR_ARG;
   if (h->phase != kReady) return POP_ERR_STATE;
   int rc = fix_biases(h, s);
@@ -672,8 +672,8 @@ int pop_kernel_times(pop_t* h, double dt, const double* s, int64_t n_intervals, 
   h->timer_events = &events;
   h->timer_kinds = &kinds;
   const float dt_f = (float)dt;
-  const bool fuse = fusable(h);
-  // the same launches, in the same order, as pop_run
+  const bool fuse = per_step == 0 && fusable(h);
+  // the same launches, in the same order, as pop_run (or the per-step calls)
   if (fuse) {
     rc = launch_evolve(h, h->stream, dt_f);
     if (rc == POP_OK) rc = total_hops(&hops1);
