@@ -184,6 +184,27 @@ def cpu_oracle_sample(w, pop_idx, M):
     return events, time.perf_counter() - t0
 
 
+def _oracle_one(args):
+    w, p, M = args
+    return cpu_oracle_sample(w, [p], M)[0]
+
+
+def cpu_oracle_parallel(w, pop_idx, M):
+    """The oracle as it stands, one process per population on as many host cores
+    (spawned processes: nothing is forked from a process that has used the GPU).
+    Returns the cpu_baseline-style record over the wall time of the whole pool."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(len(pop_idx)) as pool:
+        pool.map(_oracle_one, [(w, pop_idx[0], 1)] * len(pop_idx))   # start-up and oracle build
+        t0 = time.perf_counter()
+        events = sum(pool.map(_oracle_one, [(w, p, M) for p in pop_idx]))
+        sec = time.perf_counter() - t0
+    return {"value": events / sec, "unit": UNIT, "cores": len(pop_idx), "kind": "oracle",
+            "sample": "populations 0..%d (N_c=16384 each), first %d of the 10000 intervals, one "
+                      "process per population; %.1f s" % (len(pop_idx) - 1, M, sec)}
+
+
 def reference_arm(args, w, world, rank):
     if rank != 0:
         return
@@ -482,6 +503,11 @@ def main():
         line["cpu_baseline"] = {"value": ev_c / sec_c, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": "populations %s (N_c=16384 each), first 40 of the "
                                           "10000 intervals; %.1f s" % (idx, sec_c)}
+        # the same oracle on every host core: one process per population (the
+        # populations are independent, as the paper's OpenMP design splits clones)
+        ncores = os.cpu_count() or 1
+        idx_all = list(range(min(64, ncores)))
+        line["cpu_baseline_all_cores"] = cpu_oracle_parallel(w, idx_all, 40)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
