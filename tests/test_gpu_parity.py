@@ -385,3 +385,32 @@ def test_kernel_times_equals_run_and_counts(pg):
     cnt = c.launch_count()
     assert cnt["evolve"] == 35 and cnt["weights"] == 35 and cnt["gather"] == 70
     assert cnt["gather_evolve"] == 0
+
+
+def test_activity_spread_beyond_the_weight_table_is_reported(pg):
+    # one particle on 128 sites, dt = 2.5e5: about 5e5 hops per clone with a spread of
+    # ~5000 across 4000 clones, beyond the 4096-entry weight table: the cloning stage
+    # reports POP_ERR_RANGE instead of indexing past the table
+    b = pg.PopulationBatch([dict(L=128, N=1, n_clones=4000, seed=3)])
+    b.evolve(2.5e5, [0.001])
+    b.resample()
+    with pytest.raises(pg.PopError) as e:
+        b.events()
+    assert e.value.status == pg.POP_ERR_RANGE
+    b.close()
+    # the device stays usable
+    ok = pg.PopulationBatch([dict(L=20, N=10, n_clones=100, seed=4)])
+    ok.run(0.1, [0.1], 3)
+    assert np.isfinite(ok.estimate_psi()[0][0])
+
+
+def test_an_interval_that_cannot_end_stops_at_the_step_limit(pg):
+    # dt = 1e7 in FP32: once t is near 1e7 a waiting time of ~0.5 no longer changes t,
+    # so only the per-interval step limit (2^24 steps) ends the clone's loop; the
+    # kernel reports POP_ERR_RANGE and returns instead of spinning
+    b = pg.PopulationBatch([dict(L=128, N=1, n_clones=1, seed=5)])
+    b.evolve(1e7, [0.0])
+    with pytest.raises(pg.PopError) as e:
+        b.events()
+    assert e.value.status == pg.POP_ERR_RANGE
+    b.close()
