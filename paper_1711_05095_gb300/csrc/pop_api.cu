@@ -32,6 +32,9 @@ constexpr int kGraphIntervals = 32;
 // the separate cloning stage uses 256-thread blocks above this many tiles (several
 // waves; at one wave, 128-thread blocks finish first)
 constexpr int kGatherWideTiles = 4096;
+#ifndef POP_GATHER_WIDE_THREADS
+#define POP_GATHER_WIDE_THREADS 256
+#endif
 
 struct Layout {
   int32_t P = 0, W = 0, ntiles = 0, nunits = 0;
@@ -276,9 +279,10 @@ int launch_resample(pop_t* h, cudaStream_t st) {
   if (h->lay.ntiles > kGatherWideTiles) {
     // many waves of tiles: 256-thread blocks keep more bytes in flight (measured
     // 4567 against 4379 GB/s on 2^25 two-word clones)
-    if (h->lay.W == 1) k_gather<1, 256><<<grid, 256, 0, st>>>(h->B, 0.0f);
-    else if (h->lay.W == 2) k_gather<2, 256><<<grid, 256, 0, st>>>(h->B, 0.0f);
-    else k_gather<0, 256><<<grid, 256, 0, st>>>(h->B, 0.0f);
+    constexpr int GW = POP_GATHER_WIDE_THREADS;
+    if (h->lay.W == 1) k_gather<1, GW><<<grid, GW, 0, st>>>(h->B, 0.0f);
+    else if (h->lay.W == 2) k_gather<2, GW><<<grid, GW, 0, st>>>(h->B, 0.0f);
+    else k_gather<0, GW><<<grid, GW, 0, st>>>(h->B, 0.0f);
   } else if (h->lay.W == 1) {
     k_gather<1, GT><<<grid, GT, 0, st>>>(h->B, 0.0f);
   } else if (h->lay.W == 2) {

@@ -411,12 +411,13 @@ __global__ void __launch_bounds__(kThreads) k_weights(Batch B) {
 #define POP_FUSE_MIN_BLOCKS 7  // 64 + 8 registers; a wave of 1024 tiles needs 6.7 blocks/SM
 #endif
 template <int W, int NT, bool FUSE = false, bool MOD = false>
-__global__ void __launch_bounds__(NT, FUSE ? POP_FUSE_MIN_BLOCKS : (NT == 128 ? 11 : 6))
+__global__ void __launch_bounds__(NT, FUSE ? POP_FUSE_MIN_BLOCKS : (NT == 128 ? 11 : (NT == 256 ? 6 : 3)))
     k_gather(Batch B, float dt_f) {
   constexpr int NI = kTile / NT;   // old clones per thread
   constexpr int NWARP = NT / 32;
   constexpr int WS = W > 0 ? W : 1;  // W == 0: wide lattices, copied without staging
   static_assert(!FUSE || W > 0, "the fused stage needs staged lattices");
+  static_assert(NI % 4 == 0 && NI * NT == kTile, "whole int4 loads of activities per thread");
   __shared__ unsigned long long s_x[W > 0 ? kTile : 1][WS];
   __shared__ int32_t s_K[kTile];
   __shared__ uint32_t s_jlo[kTile + 1];
