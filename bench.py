@@ -53,10 +53,11 @@ OPS_GATHER = 3 + 2 + 16 + 3                     # 24
 N_SM = 152
 ISSUE_OPS_PER_SM_CLK = 128                      # 4 schedulers x 32 lanes
 
-# DRAM bytes (read + write) of one launch of the dominant kernel on this workload,
-# from one `ncu --set full` capture (profiles/), valid only for the kernel sources it
-# was taken on (hash of the two device headers).
-KERNEL_TRAFFIC = {"bytes": 17162496, "sources": "5f2401df866243e5"}
+# DRAM bytes (read + write) of one whole-batch launch of the dominant kernel on this
+# workload: the sum over the two half-batch launches of one interval (pop_run's two
+# chains read disjoint clones), from one ncu capture (profiles/), valid only for the
+# kernel sources it was taken on (hash of the two device headers).
+KERNEL_TRAFFIC = {"bytes": 17027840, "sources": "86647e78f5eca8fc"}
 
 
 def kernel_sources_digest():
@@ -464,6 +465,10 @@ def main():
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_gops = N_SM * ISSUE_OPS_PER_SM_CLK * sm_max * 1e6 / 1e9
     achieved = ops_per_launch / t_k / 1e9
+    # the same operation count over this rank's timed steps, whose time also holds the
+    # other kernels of each interval and, with pop_run's two chains, their overlap
+    ops_run = OPS_HOP * ev_total + (OPS_STOP + OPS_GATHER) * clone_intervals * M * args.steps
+    achieved_run = ops_run / (sum(ms) / 1e3) / 1e9
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -484,7 +489,9 @@ def main():
                                   % (sm_max, peak_kind),
                      "launch_us": t_k_us, "launches_timed": n_k,
                      "other_kernels_us": {k: v[0] for k, v in kt.items() if k != "gather_evolve" and v[1]},
-                     "ops_per_launch": ops_per_launch},
+                     "ops_per_launch": ops_per_launch,
+                     "launches_from": "pop_kernel_times: whole-batch launches, one chain",
+                     "achieved_in_run": achieved_run, "frac_in_run": achieved_run / peak_gops},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "seconds_to_se": {"value": se_seconds, "unit": "s", "target_se": 1e-3,
                           "workload": "L=50 N=25 lambda=20 N_c=16384 dt=0.1 t_obs=%g" % w["t_obs"],

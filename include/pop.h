@@ -137,6 +137,12 @@ int pop_resample(pop_t* pop);
  * n_intervals full intervals (dynamical stage then cloning stage), identical in
  * result to n_intervals pairs of pop_evolve/pop_resample, launched as captured CUDA
  * graphs.  Same rules for s and dt as pop_evolve.
+ * When the batch fuses the cloning stage with the next dynamical stage (every
+ * population [eq], not GUIDED, L <= 128) and its populations divide into two halves
+ * of whole populations, each at least a quarter of the tiles, the fused intervals of
+ * each half run as their own chain of kernels on an internal stream forked from and
+ * joined back into the handle's stream (the halves share no data; results are the
+ * same bit for bit).
  */
 int pop_run(pop_t* pop, double dt, const double* s, int64_t n_intervals);
 
@@ -266,8 +272,9 @@ int pop_events(pop_t* pop, uint64_t* h_events);
 #define POP_NKINDS 5
 
 /*
- * Measurement.  Advances the batch by n_intervals >= 1 intervals with exactly the
- * kernels pop_run uses (per_step = 0) or those of pop_evolve + pop_resample
+ * Measurement.  Advances the batch by n_intervals >= 1 intervals with the kernels
+ * pop_run uses, over the whole batch (per_step = 0: never split into halves), or those
+ * of pop_evolve + pop_resample
  * (per_step = 1: the separate dynamical and cloning stages), in the same order and so
  * with the same results, but launched one by one, each between two CUDA events
  * recorded on the handle's stream.  Any

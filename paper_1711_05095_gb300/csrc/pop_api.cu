@@ -17,6 +17,7 @@
 // population its cloning stage is still reading.
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -92,7 +93,7 @@ bool make_layout(const pop_params* params, int32_t n_pops, Layout* lay) {
   l.o_exp2 = take(64 * sizeof(float));
   l.o_hist = take(P * kKcap * sizeof(unsigned int));
   l.o_tile_sum = take(nt * sizeof(unsigned long long));
-  l.o_beta = take(sizeof(unsigned int));
+  l.o_beta = take(3 * sizeof(unsigned int));   // the interval counter, and one per half
   l.o_ksum = take(P * sizeof(long long));
   l.o_phi = take(P * 512 * sizeof(int32_t));
   l.o_gtab = take((kGuideTabA + kGuideTabB) * sizeof(unsigned long long));
@@ -128,6 +129,12 @@ struct pop_batch {
   int device = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t capture_stream = nullptr;
+  // pop_run's fused loop in two halves of whole populations on two streams, so the
+  // latency-bound phases of one half overlap the dynamical stage of the other
+  int32_t split = 0;                 // first tile of the second half (0: no split)
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  Batch half[2]{};                   // the batch with each half's own interval counter
   cudaGraphExec_t graph = nullptr;
   float graph_dt = 0.0f;
   unsigned char* ws = nullptr;
@@ -267,7 +274,7 @@ int launch_evolve(pop_t* h, cudaStream_t st, float dt_f) {
 
 void launch_weights(pop_t* h, cudaStream_t st) {
   kernel_begin(h, st, POP_K_WEIGHTS);
-  k_weights<<<(unsigned)h->lay.ntiles, kThreads, 0, st>>>(h->B);
+  k_weights<<<(unsigned)h->lay.ntiles, kThreads, 0, st>>>(h->B, 0);
   kernel_end(h, st);
 }
 
@@ -280,15 +287,15 @@ int launch_resample(pop_t* h, cudaStream_t st) {
     // many waves of tiles: 256-thread blocks keep more bytes in flight (measured
     // 4567 against 4379 GB/s on 2^25 two-word clones)
     constexpr int GW = POP_GATHER_WIDE_THREADS;
-    if (h->lay.W == 1) k_gather<1, GW><<<grid, GW, 0, st>>>(h->B, 0.0f);
-    else if (h->lay.W == 2) k_gather<2, GW><<<grid, GW, 0, st>>>(h->B, 0.0f);
-    else k_gather<0, GW><<<grid, GW, 0, st>>>(h->B, 0.0f);
+    if (h->lay.W == 1) k_gather<1, GW><<<grid, GW, 0, st>>>(h->B, 0.0f, 0);
+    else if (h->lay.W == 2) k_gather<2, GW><<<grid, GW, 0, st>>>(h->B, 0.0f, 0);
+    else k_gather<0, GW><<<grid, GW, 0, st>>>(h->B, 0.0f, 0);
   } else if (h->lay.W == 1) {
-    k_gather<1, GT><<<grid, GT, 0, st>>>(h->B, 0.0f);
+    k_gather<1, GT><<<grid, GT, 0, st>>>(h->B, 0.0f, 0);
   } else if (h->lay.W == 2) {
-    k_gather<2, GT><<<grid, GT, 0, st>>>(h->B, 0.0f);
+    k_gather<2, GT><<<grid, GT, 0, st>>>(h->B, 0.0f, 0);
   } else {
-    k_gather<0, GT><<<grid, GT, 0, st>>>(h->B, 0.0f);
+    k_gather<0, GT><<<grid, GT, 0, st>>>(h->B, 0.0f, 0);
   }
   kernel_end(h, st);
   if (h->B.any_iid) {
@@ -307,21 +314,29 @@ bool fusable(const pop_t* h) {
   return h->lay.W >= 1 && h->lay.W <= 2 && !h->B.any_iid && !h->guided;
 }
 
-// Cloning stage of the current interval and dynamical stage of the next one.
-int launch_resample_evolve(pop_t* h, cudaStream_t st, float dt_f) {
-  const unsigned grid = (unsigned)h->lay.ntiles;
-  launch_weights(h, st);
+// Cloning stage of the current interval and dynamical stage of the next one, for
+// the tiles [tile0, tile0 + ntiles) (whole populations) with the batch view Bx.
+int launch_resample_evolve_range(pop_t* h, cudaStream_t st, float dt_f, const Batch& Bx,
+                                 int tile0, int ntiles) {
+  const unsigned grid = (unsigned)ntiles;
+  kernel_begin(h, st, POP_K_WEIGHTS);
+  k_weights<<<grid, kThreads, 0, st>>>(Bx, tile0);
+  kernel_end(h, st);
   constexpr int GT = POP_FUSE_THREADS;
   kernel_begin(h, st, POP_K_GATHER_EVOLVE);
   if (h->any_mod) {
-    if (h->lay.W == 1) k_gather<1, GT, true, true><<<grid, GT, 0, st>>>(h->B, dt_f);
-    else k_gather<2, GT, true, true><<<grid, GT, 0, st>>>(h->B, dt_f);
+    if (h->lay.W == 1) k_gather<1, GT, true, true><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
+    else k_gather<2, GT, true, true><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
   } else {
-    if (h->lay.W == 1) k_gather<1, GT, true, false><<<grid, GT, 0, st>>>(h->B, dt_f);
-    else k_gather<2, GT, true, false><<<grid, GT, 0, st>>>(h->B, dt_f);
+    if (h->lay.W == 1) k_gather<1, GT, true, false><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
+    else k_gather<2, GT, true, false><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
   }
   kernel_end(h, st);
   return cuda_status(cudaGetLastError());
+}
+
+int launch_resample_evolve(pop_t* h, cudaStream_t st, float dt_f) {
+  return launch_resample_evolve_range(h, st, dt_f, h->B, 0, h->lay.ntiles);
 }
 
 // Persistent evolve grid: as many blocks as fit on the device at once, each
@@ -412,7 +427,10 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
   h->ws = (unsigned char*)d_workspace;
   auto fail = [&](int rc) { pop_free(h); return rc; };
   if (cudaGetDevice(&h->device) != cudaSuccess) return fail(POP_ERR_CUDA);
-  if (cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+  if (cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess)
     return fail(POP_ERR_CUDA);
 
   // per-population descriptors and the tile map
@@ -526,6 +544,20 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
   B.dKb[1] = B.dKb[0] + lay.nslots;
   B.anc = (int32_t*)(ws + lay.o_anc);
   B.ntiles = lay.ntiles;
+  // two-stream split: the population boundary nearest half the tiles, each half at
+  // least a quarter of the batch
+  {
+    int32_t best = 0;
+    for (int32_t p = 1; p < n_pops; ++p) {
+      const int32_t t = h->desc[p].first_tile;
+      if (std::abs(2 * t - lay.ntiles) < std::abs(2 * best - lay.ntiles)) best = t;
+    }
+    if (4 * best >= lay.ntiles && 4 * (lay.ntiles - best) >= lay.ntiles) h->split = best;
+    for (int k = 0; k < 2; ++k) {
+      h->half[k] = B;
+      h->half[k].beta = B.beta + 1 + k;
+    }
+  }
   B.nunits = lay.nunits;
   B.nslots = lay.nslots;
   B.W = lay.W;
@@ -619,11 +651,37 @@ int pop_run(pop_t* h, double dt, const double* s, int64_t n_intervals) {
   const int64_t n_rep = fuse ? n_intervals - 1 : n_intervals;
   const int64_t n_graph = n_rep / kGraphIntervals;
   const int64_t n_rest = n_rep % kGraphIntervals;
+  // split: each half of the batch runs its own chain on st and the auxiliary stream
+  // (forked from and joined back into st), with its own interval counter
+  const bool split = fuse && h->split > 0;
   auto one = [&](cudaStream_t st) {
     if (fuse) return launch_resample_evolve(h, st, dt_f);
     const int lr = launch_evolve(h, st, dt_f);
     return lr == POP_OK ? launch_resample(h, st) : lr;
   };
+  auto halves = [&](cudaStream_t st, int64_t n) {
+    if (cudaEventRecord(h->ev_fork, st) != cudaSuccess ||
+        cudaStreamWaitEvent(h->aux_stream, h->ev_fork, 0) != cudaSuccess)
+      return (int)POP_ERR_CUDA;
+    int lr = POP_OK;
+    for (int64_t i = 0; i < n && lr == POP_OK; ++i) {
+      lr = launch_resample_evolve_range(h, st, dt_f, h->half[0], 0, h->split);
+      if (lr == POP_OK)
+        lr = launch_resample_evolve_range(h, h->aux_stream, dt_f, h->half[1], h->split,
+                                          h->lay.ntiles - h->split);
+    }
+    // the join is made even after a failed launch, so a capture can end cleanly
+    if (cudaEventRecord(h->ev_join, h->aux_stream) != cudaSuccess ||
+        cudaStreamWaitEvent(st, h->ev_join, 0) != cudaSuccess)
+      return (int)POP_ERR_CUDA;
+    return lr;
+  };
+  if (split) {
+    POP_CUDA(cudaMemcpyAsync(h->half[0].beta, h->B.beta, sizeof(unsigned int),
+                             cudaMemcpyDeviceToDevice, h->stream));
+    POP_CUDA(cudaMemcpyAsync(h->half[1].beta, h->B.beta, sizeof(unsigned int),
+                             cudaMemcpyDeviceToDevice, h->stream));
+  }
   if (n_graph > 0 && (h->graph == nullptr || h->graph_dt != dt_f)) {
     if (h->graph != nullptr) {
       cudaGraphExecDestroy(h->graph);
@@ -634,7 +692,9 @@ int pop_run(pop_t* h, double dt, const double* s, int64_t n_intervals) {
     int lr = POP_OK;
     for (uint64_t& c : h->graph_counts) c = 0;
     h->count = h->graph_counts;
-    for (int i = 0; i < kGraphIntervals && lr == POP_OK; ++i) lr = one(h->capture_stream);
+    if (split) lr = halves(h->capture_stream, kGraphIntervals);
+    else
+      for (int i = 0; i < kGraphIntervals && lr == POP_OK; ++i) lr = one(h->capture_stream);
     h->count = h->launches;
     const cudaError_t ec = cudaStreamEndCapture(h->capture_stream, &g);
     if (lr != POP_OK || ec != cudaSuccess) {
@@ -653,9 +713,18 @@ int pop_run(pop_t* h, double dt, const double* s, int64_t n_intervals) {
     POP_CUDA(cudaGraphLaunch(h->graph, h->stream));
     for (int k = 0; k < POP_NKINDS; ++k) h->launches[k] += h->graph_counts[k];
   }
-  for (int64_t i = 0; i < n_rest; ++i) {
-    rc = one(h->stream);
+  if (split && n_rest > 0) {
+    rc = halves(h->stream, n_rest);
     if (rc != POP_OK) return rc;
+  } else {
+    for (int64_t i = 0; i < n_rest; ++i) {
+      rc = one(h->stream);
+      if (rc != POP_OK) return rc;
+    }
+  }
+  if (split) {
+    POP_CUDA(cudaMemcpyAsync(h->B.beta, h->half[0].beta, sizeof(unsigned int),
+                             cudaMemcpyDeviceToDevice, h->stream));
   }
   if (fuse) {
     rc = launch_resample(h, h->stream);
@@ -929,6 +998,9 @@ void pop_free(pop_t* h) {
   if (h == nullptr) return;
   if (h->graph) cudaGraphExecDestroy(h->graph);
   if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+  if (h->aux_stream) cudaStreamDestroy(h->aux_stream);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   delete h;
 }
 

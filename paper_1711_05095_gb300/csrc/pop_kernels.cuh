@@ -318,11 +318,11 @@ __global__ void __launch_bounds__(kThreads, POP_EVOLVE_MIN_BLOCKS) k_evolve(Batc
 // Per tile: the weight sum and the histogram of |dK - k_ref|.  The first tile of a
 // population also records k_ref and the [eq] offset word U of the interval.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_weights(Batch B) {
+__global__ void __launch_bounds__(kThreads) k_weights(Batch B, int tile0) {
   __shared__ unsigned int s_hist[kHistSmem];
   __shared__ unsigned long long s_red[kWarps];
   const int tid = threadIdx.x;
-  const int tile = blockIdx.x;
+  const int tile = tile0 + (int)blockIdx.x;
   const int p = B.tile_pop[tile];
   const PopDesc d = B.pops[p];
   PopState* st = B.st + p;
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(kThreads) k_weights(Batch B) {
 #endif
 template <int W, int NT, bool FUSE = false, bool MOD = false>
 __global__ void __launch_bounds__(NT, FUSE ? POP_FUSE_MIN_BLOCKS : (NT == 128 ? 11 : (NT == 256 ? 6 : 3)))
-    k_gather(Batch B, float dt_f) {
+    k_gather(Batch B, float dt_f, int tile0) {
   constexpr int NI = kTile / NT;   // old clones per thread
   constexpr int NWARP = NT / 32;
   constexpr int WS = W > 0 ? W : 1;  // W == 0: wide lattices, copied without staging
@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(NT, FUSE ? POP_FUSE_MIN_BLOCKS : (NT == 128 ? 
   __shared__ int s_nmin, s_nmax, s_namin, s_namax;
   __shared__ unsigned int s_nev;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int tile = blockIdx.x;
+  const int tile = tile0 + (int)blockIdx.x;
   const int p = B.tile_pop[tile];
   const PopDesc d = B.pops[p];
   PopState* st = B.st + p;

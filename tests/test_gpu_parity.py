@@ -129,6 +129,12 @@ RUN_CASES = {
                     [0.01, -0.3], [1, 2, 3, 40]),
     # one population of 65 tiles and a ragged last tile
     "tiles_65": ([dict(L=30, N=15, n_clones=65 * 1024 + 5, seed=20)], [0.05], [35]),
+    # five populations of 1, 4, 2, 3 and 2 tiles: pop_run's two chains split them after
+    # the second (5 and 7 tiles); a graph replay, then direct launches of both chains
+    "halves_of_five": ([dict(L=30, N=15, n_clones=1000, seed=30), dict(L=50, N=25, n_clones=4000, seed=31),
+                        dict(L=70, N=30, n_clones=1900, seed=32, weight_mode=1),
+                        dict(L=128, N=64, n_clones=3072, seed=33), dict(L=9, N=4, n_clones=1500, seed=34)],
+                       [0.2, -0.01, 0.1, 0.004, -0.5], [33, 5]),
     # strong bias: a wide activity range and tiles whose old clones leave no copies
     "strong_bias": ([dict(L=64, N=32, n_clones=5000, seed=21), dict(L=128, N=64, n_clones=3000, seed=22)],
                     [2.0, 0.5], [34]),
@@ -375,10 +381,20 @@ def test_kernel_times_equals_run_and_counts(pg):
     assert kt["evolve"][2] + kt["gather_evolve"][2] == int(b.events().sum())
     for name in ("evolve", "weights", "gather", "gather_evolve"):
         assert kt[name][0] > 0.0
-    for batch in (a, b):
+    # pop_run splits this batch (3 + 2 tiles, each half at least a quarter) into two
+    # chains, each with its own [weights, fused stage] per interval; kernel_times never
+    for batch, halves in ((a, 2), (b, 1)):
         c = batch.launch_count()
-        assert c["evolve"] == 1 and c["gather_evolve"] == n - 1 and c["weights"] == n
+        assert c["evolve"] == 1 and c["gather_evolve"] == halves * (n - 1)
+        assert c["weights"] == halves * (n - 1) + 1
         assert c["gather"] == 1 and c["other"] == 1       # the initial state
+    # one population, or a split that would leave less than a quarter: one chain
+    for pops1 in ([dict(L=50, N=25, n_clones=3000, seed=24)],
+                  [dict(L=50, N=25, n_clones=9000, seed=25), dict(L=40, N=20, n_clones=2000, seed=26)]):
+        d = pg.PopulationBatch(pops1)
+        d.run(0.1, [0.02] * len(pops1), n)
+        c = d.launch_count()
+        assert c["gather_evolve"] == n - 1 and c["weights"] == n, pops1
     # [iid] batches keep the three separate kernels (and the [iid] selection) per interval
     c = pg.PopulationBatch([dict(L=30, N=15, n_clones=1500, seed=23, selection=1)])
     c.run(0.1, [0.1], 35)
