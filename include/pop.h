@@ -138,13 +138,24 @@ int pop_resample(pop_t* pop);
  * result to n_intervals pairs of pop_evolve/pop_resample, launched as captured CUDA
  * graphs.  Same rules for s and dt as pop_evolve.
  * When the batch fuses the cloning stage with the next dynamical stage (every
- * population [eq], not GUIDED, L <= 128) and its populations divide into two halves
- * of whole populations, each at least a quarter of the tiles, the fused intervals of
- * each half run as their own chain of kernels on an internal stream forked from and
- * joined back into the handle's stream (the halves share no data; results are the
- * same bit for bit).
+ * population [eq], not GUIDED, L <= 128), the fused intervals run as 1 to 8 chains of
+ * kernels, each over a run of whole populations, on internal streams forked from and
+ * joined back into the handle's stream (the chains share no data; results are the
+ * same bit for bit); pop_run_chains gives the split.
  */
 int pop_run(pop_t* pop, double dt, const double* s, int64_t n_intervals);
+
+/*
+ * The chains of pop_run: returns their number K (0 when the batch does not fuse, so
+ * pop_run launches one sequence; -1 for a NULL handle) and, when h_first_tiles is not
+ * NULL and K > 0, writes K + 1 entries: chain c runs the 1024-slot tiles
+ * [h_first_tiles[c], h_first_tiles[c + 1]), whole populations, the last entry the
+ * batch's tile count.  K is the largest number up to 8 (for a batch that fits in two
+ * waves of the fused kernel on this device; up to 2 for a larger one) for which the
+ * population starts nearest k/K of the tiles (k = 1 .. K-1) leave every chain at least
+ * half of its equal share.
+ */
+int32_t pop_run_chains(pop_t* pop, int32_t* h_first_tiles);
 
 /*
  * Estimates after the intervals run so far (host arrays of n_pops each; any may be

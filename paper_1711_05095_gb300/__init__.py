@@ -36,7 +36,7 @@ EXPORTS = ("pop_workspace_bytes", "pop_init", "pop_set_state", "pop_evolve", "po
            "pop_set_potential", "pop_lineage", "pop_slots", "pop_first_slot",
            "pop_mlp_workspace_bytes", "pop_mlp_init", "pop_mlp_grad", "pop_mlp_step",
            "pop_mlp_params", "pop_mlp_potential", "pop_mlp_free",
-           "pop_launch_count", "pop_strerror", "pop_free")
+           "pop_launch_count", "pop_run_chains", "pop_strerror", "pop_free")
 KERNEL_KINDS = ("evolve", "weights", "gather", "gather_evolve", "other")
 POP_NOALLOC_MAX_CLONES = 1 << 20
 
@@ -125,6 +125,8 @@ def library():
     L.pop_kernel_times.restype = ctypes.c_int
     L.pop_launch_count.argtypes = [ctypes.c_void_p, _u64p]
     L.pop_launch_count.restype = ctypes.c_int
+    L.pop_run_chains.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]
+    L.pop_run_chains.restype = ctypes.c_int32
     L.pop_select_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_uint64,
                                      ctypes.c_uint32, ctypes.c_void_p, _f64p, ctypes.c_void_p]
     L.pop_select_noalloc.restype = ctypes.c_int
@@ -247,6 +249,15 @@ class PopulationBatch:
         g = ctypes.c_int32(0)
         _check(self._lib.pop_autotune(self._h, float(dt), sp, int(trials), ctypes.byref(g)), "pop_autotune")
         return int(g.value)
+
+    def run_chains(self):
+        """First tile of each chain of run() and the tile count (K + 1 entries; [] when
+        the batch does not fuse)."""
+        t = np.zeros(9, dtype=np.int32)
+        k = int(self._lib.pop_run_chains(self._h, t.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+        if k < 0:
+            raise PopError(POP_ERR_ARG, "pop_run_chains")
+        return [int(x) for x in t[:k + 1]] if k > 0 else []
 
     @property
     def slots(self):

@@ -27,6 +27,19 @@
 
 using namespace popgpu;
 
+// pop_run's chains (see pop_batch::nch): at most POP_RUN_CHAINS for a batch that fits
+// in two waves of the fused kernel, at most POP_RUN_CHAINS_LARGE for a larger one
+#ifndef POP_RUN_CHAINS
+#define POP_RUN_CHAINS 8
+#endif
+#ifndef POP_RUN_CHAINS_LARGE
+#define POP_RUN_CHAINS_LARGE 2
+#endif
+constexpr int kMaxChains = 8;
+static_assert(POP_RUN_CHAINS >= 1 && POP_RUN_CHAINS <= kMaxChains &&
+              POP_RUN_CHAINS_LARGE >= 1 && POP_RUN_CHAINS_LARGE <= kMaxChains, "1 to 8 chains");
+
+
 namespace {
 
 constexpr int kGraphIntervals = 32;
@@ -93,7 +106,7 @@ bool make_layout(const pop_params* params, int32_t n_pops, Layout* lay) {
   l.o_exp2 = take(64 * sizeof(float));
   l.o_hist = take(P * kKcap * sizeof(unsigned int));
   l.o_tile_sum = take(nt * sizeof(unsigned long long));
-  l.o_beta = take(3 * sizeof(unsigned int));   // the interval counter, and one per half
+  l.o_beta = take((1 + kMaxChains) * sizeof(unsigned int));   // the interval counter, one per chain
   l.o_ksum = take(P * sizeof(long long));
   l.o_phi = take(P * 512 * sizeof(int32_t));
   l.o_gtab = take((kGuideTabA + kGuideTabB) * sizeof(unsigned long long));
@@ -122,6 +135,35 @@ enum Phase { kReady = 0, kEvolved = 1 };
 
 }  // namespace
 
+namespace {
+// Split ntiles into K chains of whole populations, K the largest number up to want for
+// which each chain holds at least half of its equal share: boundary k is the population
+// start nearest k ntiles / K.  Returns K; bounds[0..K] are the chains' first tiles and
+// ntiles.
+int choose_chains(const std::vector<PopDesc>& desc, int32_t ntiles, int want, int32_t* bounds) {
+  for (int K = want; K >= 2; --K) {
+    bool ok = true;
+    bounds[0] = 0;
+    for (int k = 1; k < K && ok; ++k) {
+      int32_t best = -1;
+      for (size_t p = 1; p < desc.size(); ++p) {
+        const int64_t t = desc[p].first_tile;
+        if (best < 0 || std::llabs(K * t - (int64_t)k * ntiles) < std::llabs((int64_t)K * best - (int64_t)k * ntiles))
+          best = (int32_t)t;
+      }
+      ok = best >= 0;
+      bounds[k] = best;
+    }
+    bounds[K] = ntiles;
+    for (int k = 0; k < K && ok; ++k) ok = 2 * (int64_t)K * (bounds[k + 1] - bounds[k]) >= ntiles;
+    if (ok) return K;
+  }
+  bounds[0] = 0;
+  bounds[1] = ntiles;
+  return 1;
+}
+}  // namespace
+
 struct pop_batch {
   Layout lay;
   std::vector<pop_params> params;
@@ -129,12 +171,14 @@ struct pop_batch {
   int device = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t capture_stream = nullptr;
-  // pop_run's fused loop in two halves of whole populations on two streams, so the
-  // latency-bound phases of one half overlap the dynamical stage of the other
-  int32_t split = 0;                 // first tile of the second half (0: no split)
-  cudaStream_t aux_stream = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  Batch half[2]{};                   // the batch with each half's own interval counter
+  // pop_run's fused loop as nch chains of whole populations, each on its own stream,
+  // so the latency-bound phases of one chain overlap the dynamical stage of another
+  int32_t nch = 1;
+  int32_t chain_tile[kMaxChains + 1] = {};   // chain c: tiles [chain_tile[c], chain_tile[c + 1])
+  cudaStream_t aux_stream[kMaxChains - 1] = {};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[kMaxChains - 1] = {};
+  Batch chain[kMaxChains]{};                 // the batch with each chain's own interval counter
   cudaGraphExec_t graph = nullptr;
   float graph_dt = 0.0f;
   unsigned char* ws = nullptr;
@@ -339,6 +383,27 @@ int launch_resample_evolve(pop_t* h, cudaStream_t st, float dt_f) {
   return launch_resample_evolve_range(h, st, dt_f, h->B, 0, h->lay.ntiles);
 }
 
+// pop_run's chains.  In a batch of at most two waves of the fused kernel the drain at
+// the end of each launch and the k_weights between launches are a large part of an
+// interval, and more chains fill them; in a larger batch more chains only compete.
+int size_chains(pop_t* h) {
+  h->nch = 1;
+  h->chain_tile[0] = 0;
+  h->chain_tile[1] = h->lay.ntiles;
+  if (!fusable(h)) return POP_OK;
+  constexpr int GT = POP_FUSE_THREADS;
+  const void* f = h->lay.W == 1
+                      ? (h->any_mod ? (const void*)k_gather<1, GT, true, true> : (const void*)k_gather<1, GT, true, false>)
+                      : (h->any_mod ? (const void*)k_gather<2, GT, true, true> : (const void*)k_gather<2, GT, true, false>);
+  int per_sm = 0, sms = 0;
+  POP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, GT, 0));
+  POP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+  const long long wave = (long long)(per_sm < 1 ? 1 : per_sm) * sms;
+  const int want = h->lay.ntiles <= 2 * wave ? POP_RUN_CHAINS : POP_RUN_CHAINS_LARGE;
+  h->nch = choose_chains(h->desc, h->lay.ntiles, want, h->chain_tile);
+  return POP_OK;
+}
+
 // Persistent evolve grid: as many blocks as fit on the device at once, each
 // owning an equal share of the 256-slot units.
 template <int W, bool MOD>
@@ -428,9 +493,7 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
   auto fail = [&](int rc) { pop_free(h); return rc; };
   if (cudaGetDevice(&h->device) != cudaSuccess) return fail(POP_ERR_CUDA);
   if (cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess)
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess)
     return fail(POP_ERR_CUDA);
 
   // per-population descriptors and the tile map
@@ -544,20 +607,15 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
   B.dKb[1] = B.dKb[0] + lay.nslots;
   B.anc = (int32_t*)(ws + lay.o_anc);
   B.ntiles = lay.ntiles;
-  // two-stream split: the population boundary nearest half the tiles, each half at
-  // least a quarter of the batch
-  {
-    int32_t best = 0;
-    for (int32_t p = 1; p < n_pops; ++p) {
-      const int32_t t = h->desc[p].first_tile;
-      if (std::abs(2 * t - lay.ntiles) < std::abs(2 * best - lay.ntiles)) best = t;
-    }
-    if (4 * best >= lay.ntiles && 4 * (lay.ntiles - best) >= lay.ntiles) h->split = best;
-    for (int k = 0; k < 2; ++k) {
-      h->half[k] = B;
-      h->half[k].beta = B.beta + 1 + k;
-    }
+  if (size_chains(h) != POP_OK) return fail(POP_ERR_CUDA);
+  for (int c = 0; c < h->nch; ++c) {
+    h->chain[c] = B;
+    h->chain[c].beta = B.beta + 1 + c;
   }
+  for (int c = 0; c + 1 < h->nch; ++c)
+    if (cudaStreamCreateWithFlags(&h->aux_stream[c], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_join[c], cudaEventDisableTiming) != cudaSuccess)
+      return fail(POP_ERR_CUDA);
   B.nunits = lay.nunits;
   B.nslots = lay.nslots;
   B.W = lay.W;
@@ -651,37 +709,35 @@ int pop_run(pop_t* h, double dt, const double* s, int64_t n_intervals) {
   const int64_t n_rep = fuse ? n_intervals - 1 : n_intervals;
   const int64_t n_graph = n_rep / kGraphIntervals;
   const int64_t n_rest = n_rep % kGraphIntervals;
-  // split: each half of the batch runs its own chain on st and the auxiliary stream
-  // (forked from and joined back into st), with its own interval counter
-  const bool split = fuse && h->split > 0;
+  // chains: each part of the batch runs its own sequence, chain 0 on st and the others
+  // on the auxiliary streams (forked from and joined back into st), each with its own
+  // interval counter
+  const bool split = fuse && h->nch > 1;
   auto one = [&](cudaStream_t st) {
     if (fuse) return launch_resample_evolve(h, st, dt_f);
     const int lr = launch_evolve(h, st, dt_f);
     return lr == POP_OK ? launch_resample(h, st) : lr;
   };
-  auto halves = [&](cudaStream_t st, int64_t n) {
-    if (cudaEventRecord(h->ev_fork, st) != cudaSuccess ||
-        cudaStreamWaitEvent(h->aux_stream, h->ev_fork, 0) != cudaSuccess)
-      return (int)POP_ERR_CUDA;
+  auto chains = [&](cudaStream_t st, int64_t n) {
+    if (cudaEventRecord(h->ev_fork, st) != cudaSuccess) return (int)POP_ERR_CUDA;
+    for (int c = 0; c + 1 < h->nch; ++c)
+      if (cudaStreamWaitEvent(h->aux_stream[c], h->ev_fork, 0) != cudaSuccess) return (int)POP_ERR_CUDA;
     int lr = POP_OK;
-    for (int64_t i = 0; i < n && lr == POP_OK; ++i) {
-      lr = launch_resample_evolve_range(h, st, dt_f, h->half[0], 0, h->split);
-      if (lr == POP_OK)
-        lr = launch_resample_evolve_range(h, h->aux_stream, dt_f, h->half[1], h->split,
-                                          h->lay.ntiles - h->split);
-    }
-    // the join is made even after a failed launch, so a capture can end cleanly
-    if (cudaEventRecord(h->ev_join, h->aux_stream) != cudaSuccess ||
-        cudaStreamWaitEvent(st, h->ev_join, 0) != cudaSuccess)
-      return (int)POP_ERR_CUDA;
+    for (int64_t i = 0; i < n && lr == POP_OK; ++i)
+      for (int c = 0; c < h->nch && lr == POP_OK; ++c)
+        lr = launch_resample_evolve_range(h, c == 0 ? st : h->aux_stream[c - 1], dt_f, h->chain[c],
+                                          h->chain_tile[c], h->chain_tile[c + 1] - h->chain_tile[c]);
+    // the joins are made even after a failed launch, so a capture can end cleanly
+    for (int c = 0; c + 1 < h->nch; ++c)
+      if (cudaEventRecord(h->ev_join[c], h->aux_stream[c]) != cudaSuccess ||
+          cudaStreamWaitEvent(st, h->ev_join[c], 0) != cudaSuccess)
+        return (int)POP_ERR_CUDA;
     return lr;
   };
-  if (split) {
-    POP_CUDA(cudaMemcpyAsync(h->half[0].beta, h->B.beta, sizeof(unsigned int),
-                             cudaMemcpyDeviceToDevice, h->stream));
-    POP_CUDA(cudaMemcpyAsync(h->half[1].beta, h->B.beta, sizeof(unsigned int),
-                             cudaMemcpyDeviceToDevice, h->stream));
-  }
+  if (split)
+    for (int c = 0; c < h->nch; ++c)
+      POP_CUDA(cudaMemcpyAsync(h->chain[c].beta, h->B.beta, sizeof(unsigned int),
+                               cudaMemcpyDeviceToDevice, h->stream));
   if (n_graph > 0 && (h->graph == nullptr || h->graph_dt != dt_f)) {
     if (h->graph != nullptr) {
       cudaGraphExecDestroy(h->graph);
@@ -692,7 +748,7 @@ int pop_run(pop_t* h, double dt, const double* s, int64_t n_intervals) {
     int lr = POP_OK;
     for (uint64_t& c : h->graph_counts) c = 0;
     h->count = h->graph_counts;
-    if (split) lr = halves(h->capture_stream, kGraphIntervals);
+    if (split) lr = chains(h->capture_stream, kGraphIntervals);
     else
       for (int i = 0; i < kGraphIntervals && lr == POP_OK; ++i) lr = one(h->capture_stream);
     h->count = h->launches;
@@ -714,7 +770,7 @@ int pop_run(pop_t* h, double dt, const double* s, int64_t n_intervals) {
     for (int k = 0; k < POP_NKINDS; ++k) h->launches[k] += h->graph_counts[k];
   }
   if (split && n_rest > 0) {
-    rc = halves(h->stream, n_rest);
+    rc = chains(h->stream, n_rest);
     if (rc != POP_OK) return rc;
   } else {
     for (int64_t i = 0; i < n_rest; ++i) {
@@ -723,7 +779,7 @@ int pop_run(pop_t* h, double dt, const double* s, int64_t n_intervals) {
     }
   }
   if (split) {
-    POP_CUDA(cudaMemcpyAsync(h->B.beta, h->half[0].beta, sizeof(unsigned int),
+    POP_CUDA(cudaMemcpyAsync(h->B.beta, h->chain[0].beta, sizeof(unsigned int),
                              cudaMemcpyDeviceToDevice, h->stream));
   }
   if (fuse) {
@@ -802,6 +858,14 @@ int pop_kernel_times(pop_t* h, double dt, const double* s, int64_t n_intervals, 
     }
   }
   return POP_OK;
+}
+
+int32_t pop_run_chains(pop_t* h, int32_t* h_first_tiles) {
+  if (h == nullptr) return -1;
+  const int32_t n = fusable(h) ? h->nch : 0;
+  if (h_first_tiles != nullptr && n > 0)
+    for (int c = 0; c <= n; ++c) h_first_tiles[c] = h->chain_tile[c];
+  return n;
 }
 
 int pop_launch_count(pop_t* h, uint64_t* h_n) {
@@ -998,9 +1062,11 @@ void pop_free(pop_t* h) {
   if (h == nullptr) return;
   if (h->graph) cudaGraphExecDestroy(h->graph);
   if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
-  if (h->aux_stream) cudaStreamDestroy(h->aux_stream);
+  for (int c = 0; c + 1 < kMaxChains; ++c) {
+    if (h->aux_stream[c]) cudaStreamDestroy(h->aux_stream[c]);
+    if (h->ev_join[c]) cudaEventDestroy(h->ev_join[c]);
+  }
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
-  if (h->ev_join) cudaEventDestroy(h->ev_join);
   delete h;
 }
 

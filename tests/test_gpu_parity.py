@@ -129,8 +129,8 @@ RUN_CASES = {
                     [0.01, -0.3], [1, 2, 3, 40]),
     # one population of 65 tiles and a ragged last tile
     "tiles_65": ([dict(L=30, N=15, n_clones=65 * 1024 + 5, seed=20)], [0.05], [35]),
-    # five populations of 1, 4, 2, 3 and 2 tiles: pop_run's two chains split them after
-    # the second (5 and 7 tiles); a graph replay, then direct launches of both chains
+    # five populations of 1, 4, 2, 3 and 2 tiles: pop_run runs three chains of 5, 2 and
+    # 5 tiles; a graph replay, then direct launches of the chains
     "halves_of_five": ([dict(L=30, N=15, n_clones=1000, seed=30), dict(L=50, N=25, n_clones=4000, seed=31),
                         dict(L=70, N=30, n_clones=1900, seed=32, weight_mode=1),
                         dict(L=128, N=64, n_clones=3072, seed=33), dict(L=9, N=4, n_clones=1500, seed=34)],
@@ -139,6 +139,25 @@ RUN_CASES = {
     "strong_bias": ([dict(L=64, N=32, n_clones=5000, seed=21), dict(L=128, N=64, n_clones=3000, seed=22)],
                     [2.0, 0.5], [34]),
 }
+
+
+def test_run_chains(pg):
+    # the split rule: population starts nearest k/K of the tiles, every chain at least
+    # half its share; up to 8 chains within two waves of the fused kernel, else 2
+    five = pg.PopulationBatch(RUN_CASES["halves_of_five"][0])
+    assert five.run_chains() == [0, 5, 7, 12]
+    w = workloads.s_sweep()
+    sweep = pg.PopulationBatch(w["pops"])                 # 64 x 16 tiles
+    assert sweep.run_chains() == [128 * c for c in range(9)]
+    sweep.close()
+    big = pg.PopulationBatch([dict(L=50, N=25, n_clones=4096 * 1024, seed=40 + i) for i in range(3)])
+    assert big.run_chains() == [0, 4096, 12288]            # 3 x 4096 tiles: two chains
+    big.close()
+    # batches that do not fuse run one sequence
+    assert pg.PopulationBatch([dict(L=30, N=15, n_clones=1200, seed=15, selection=1),
+                               dict(L=30, N=15, n_clones=1200, seed=16)]).run_chains() == []
+    assert pg.PopulationBatch([dict(L=200, N=100, n_clones=1200, seed=17),
+                               dict(L=30, N=15, n_clones=1200, seed=18)]).run_chains() == []
 
 
 @pytest.mark.parametrize("case", sorted(RUN_CASES))
@@ -381,17 +400,19 @@ def test_kernel_times_equals_run_and_counts(pg):
     assert kt["evolve"][2] + kt["gather_evolve"][2] == int(b.events().sum())
     for name in ("evolve", "weights", "gather", "gather_evolve"):
         assert kt[name][0] > 0.0
-    # pop_run splits this batch (3 + 2 tiles, each half at least a quarter) into two
-    # chains, each with its own [weights, fused stage] per interval; kernel_times never
-    for batch, halves in ((a, 2), (b, 1)):
+    # pop_run splits this batch (3 + 2 tiles, each at least a quarter) into two chains,
+    # each with its own [weights, fused stage] per interval; kernel_times never does
+    assert a.run_chains() == [0, 3, 5]
+    for batch, chains in ((a, 2), (b, 1)):
         c = batch.launch_count()
-        assert c["evolve"] == 1 and c["gather_evolve"] == halves * (n - 1)
-        assert c["weights"] == halves * (n - 1) + 1
+        assert c["evolve"] == 1 and c["gather_evolve"] == chains * (n - 1)
+        assert c["weights"] == chains * (n - 1) + 1
         assert c["gather"] == 1 and c["other"] == 1       # the initial state
     # one population, or a split that would leave less than a quarter: one chain
     for pops1 in ([dict(L=50, N=25, n_clones=3000, seed=24)],
                   [dict(L=50, N=25, n_clones=9000, seed=25), dict(L=40, N=20, n_clones=2000, seed=26)]):
         d = pg.PopulationBatch(pops1)
+        assert d.run_chains() == [0, d.slots // 1024]
         d.run(0.1, [0.02] * len(pops1), n)
         c = d.launch_count()
         assert c["gather_evolve"] == n - 1 and c["weights"] == n, pops1
