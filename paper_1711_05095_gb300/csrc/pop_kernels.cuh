@@ -408,7 +408,7 @@ __global__ void __launch_bounds__(kThreads) k_weights(Batch B, int tile0) {
 #define POP_FUSE_THREADS 128
 #endif
 #ifndef POP_FUSE_MIN_BLOCKS
-#define POP_FUSE_MIN_BLOCKS 7  // 64 + 8 registers; a wave of 1024 tiles needs 6.7 blocks/SM
+#define POP_FUSE_MIN_BLOCKS 8  // 64 registers, no spills; pop_run's chains keep more than one launch resident
 #endif
 template <int W, int NT, bool FUSE = false, bool MOD = false>
 __global__ void __launch_bounds__(NT, FUSE ? POP_FUSE_MIN_BLOCKS : (NT == 128 ? 11 : (NT == 256 ? 6 : 3)))
