@@ -360,6 +360,51 @@ def test_full_size_uneven_batch_sampled(pg):
         assert np.all(np.isfinite(psi))
 
 
+@pytest.mark.parametrize("case", ["one_word", "two_words_modified"])
+def test_cloning_stage_beyond_4096_tiles(pg, case):
+    # batches of more than 4096 tiles take the 256-thread cloning stage: small
+    # populations before, between and after the large ones checked bit for bit
+    # against the oracle every interval; in the large ones every new clone is its
+    # ancestor's evolved clone, and [eq] ancestors never decrease
+    if case == "one_word":
+        pops = [dict(L=20, N=10, n_clones=1500, seed=41), dict(L=30, N=15, n_clones=2100 * 1024, seed=42),
+                dict(L=64, N=31, n_clones=777, seed=43, selection=1), dict(L=50, N=25, n_clones=2048 * 1024, seed=44),
+                dict(L=40, N=20, n_clones=3000, seed=45, weight_mode=1)]
+        s = [0.05, 0.01, -0.2, 0.02, 0.3]
+    else:
+        pops = [dict(L=100, N=50, n_clones=1100, seed=46, weight_mode=1),
+                dict(L=128, N=64, n_clones=4096 * 1024, seed=47),
+                dict(L=65, N=30, n_clones=2500, seed=48, weight_mode=1)]
+        s = [0.1, 0.003, -0.1]
+    batch = pg.PopulationBatch(pops)
+    assert batch.slots // 1024 > 4096
+    small = [p for p, q in enumerate(pops) if q["n_clones"] < 10000]
+    big = [p for p in range(len(pops)) if p not in small]
+    orcs = {p: oracle.Population(pops[p]["L"], pops[p]["N"], pops[p]["n_clones"], pops[p]["seed"],
+                                 modified=pops[p].get("weight_mode", 0) == 1,
+                                 iid=pops[p].get("selection", 0) == 1) for p in small}
+    for beta in range(1, 4):
+        batch.evolve(0.1, s)
+        evolved = {p: batch.copy_state(p) for p in big}
+        batch.resample()
+        for p, o in orcs.items():
+            o.evolve(0.1, s[p])
+            o.resample(s[p])
+            g = batch.copy_state(p)
+            assert np.array_equal(g["anc"], o.anc), "anc beta=%d pop %d" % (beta, p)
+            assert_state_equal(g, o, batch.W, "beta=%d pop %d" % (beta, p))
+        for p in big:
+            g, e = batch.copy_state(p), evolved[p]
+            anc = g["anc"]
+            assert np.all(np.diff(anc) >= 0) and anc.min() >= 0 and anc.max() < pops[p]["n_clones"]
+            assert np.array_equal(g["lattice"], e["lattice"][anc]), "lattice beta=%d pop %d" % (beta, p)
+            assert np.array_equal(g["K"], e["K"][anc]), "K beta=%d pop %d" % (beta, p)
+    psi, _, _ = batch.estimate_psi()
+    for p, o in orcs.items():
+        np.testing.assert_allclose(psi[p], o.estimates()[0], rtol=PSI_RTOL, atol=0.0)
+    assert np.all(np.isfinite(psi))
+
+
 def test_autotune_changes_no_result(pg):
     pops = [dict(L=50, N=25, n_clones=5000, seed=9), dict(L=128, N=64, n_clones=3000, seed=10)]
     s = [0.01, -0.002]
