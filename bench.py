@@ -380,17 +380,22 @@ def main():
                 # the separate cloning stage (k_gather) on a working set far above L2:
                 # algorithmic bytes per clone = old lattice 8W + K 4 + dK 4 read, new
                 # lattice 8W + K 4 + ancestor 4 written
+                torch.cuda.nvtx.range_push("gather_timing")
                 kt_g = b.kernel_times(wl["dt"], wl["s"], 8, per_step=True)
+                torch.cuda.nvtx.range_pop()
                 W_g = pg.lattice_words(wl["pops"])
                 bytes_g = clones * (2 * (8 * W_g + 8))
                 t_g = kt_g["gather"][0] / 1e6
                 peaks_g, kind_g = measured_peaks()
                 hbm = float(peaks_g.get("hbm_gbs", 6800.0))
+                t_scan = kt_g["other"][0] / 1e6   # k_tile_scan, launched before each gather
                 others["gather_roofline"] = {
                     "bound": "hbm", "kernel": "k_gather (separate cloning stage, two-word lattices)",
                     "achieved": bytes_g / t_g / 1e9, "peak": hbm, "unit": "GB/s",
                     "frac": bytes_g / t_g / 1e9 / hbm, "bytes_per_launch": bytes_g,
                     "launch_us": kt_g["gather"][0], "weights_us": kt_g["weights"][0],
+                    "tile_scan_us": kt_g["other"][0],
+                    "frac_with_tile_scan": bytes_g / (t_g + t_scan) / 1e9 / hbm,
                     "workload": "large_population, 2^25 clones, %d B per clone" % (2 * (8 * W_g + 8)),
                     "peak_kind": "measured copy bandwidth (%s)" % kind_g}
             b.close()

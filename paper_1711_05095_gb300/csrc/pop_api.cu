@@ -3,7 +3,8 @@
 // A handle owns only host state; every device buffer is carved out of the
 // caller's workspace.  Layout of the workspace (each region 256-byte aligned):
 //   PopDesc[P]  PopState[P]  tile_pop[ntiles]  wtab[P][4096] u64  qtab, qm1tab[P][4096] f64
-//   inv_rate[P][129] f32  logtab[64] f32x2  hist[P][4096] u32  tile_sum[ntiles] u64  beta  ksum[P]
+//   inv_rate[P][129] f32  logtab[64] f32x2  hist[P][4096] u32  tile_sum, tile_excl[ntiles] u64
+//   beta  ksum[P]
 //   X[2], Y lattices [nslots][W] u64   KX[2], KY, dK[2], anc [nslots] i32   A[2] [nslots] f32
 // where every population starts on a 1024-slot tile and nslots is the padded total.
 //
@@ -53,7 +54,7 @@ constexpr int kGatherWideTiles = 4096;
 struct Layout {
   int32_t P = 0, W = 0, ntiles = 0, nunits = 0;
   int64_t nslots = 0;
-  size_t o_pops, o_st, o_tile_pop, o_wtab, o_qtab, o_qm1tab, o_inv, o_logtab, o_exp2, o_A, o_S, o_cs, o_tacc, o_hist, o_tile_sum, o_beta, o_phi, o_gtab,
+  size_t o_pops, o_st, o_tile_pop, o_wtab, o_qtab, o_qm1tab, o_inv, o_logtab, o_exp2, o_A, o_S, o_cs, o_tacc, o_hist, o_tile_sum, o_tile_excl, o_beta, o_phi, o_gtab,
       o_ksum, o_X, o_Y, o_KX, o_KY, o_dK, o_anc, total;
 };
 
@@ -106,6 +107,7 @@ bool make_layout(const pop_params* params, int32_t n_pops, Layout* lay) {
   l.o_exp2 = take(64 * sizeof(float));
   l.o_hist = take(P * kKcap * sizeof(unsigned int));
   l.o_tile_sum = take(nt * sizeof(unsigned long long));
+  l.o_tile_excl = take(nt * sizeof(unsigned long long));
   l.o_beta = take((1 + kMaxChains) * sizeof(unsigned int));   // the interval counter, one per chain
   l.o_ksum = take(P * sizeof(long long));
   l.o_phi = take(P * 512 * sizeof(int32_t));
@@ -175,6 +177,7 @@ struct pop_batch {
   // so the latency-bound phases of one chain overlap the dynamical stage of another
   int32_t nch = 1;
   int32_t chain_tile[kMaxChains + 1] = {};   // chain c: tiles [chain_tile[c], chain_tile[c + 1])
+  int32_t chain_pop[kMaxChains + 1] = {};    // and populations [chain_pop[c], chain_pop[c + 1])
   cudaStream_t aux_stream[kMaxChains - 1] = {};
   cudaEvent_t ev_fork = nullptr;
   cudaEvent_t ev_join[kMaxChains - 1] = {};
@@ -316,10 +319,18 @@ int launch_evolve(pop_t* h, cudaStream_t st, float dt_f) {
   return cuda_status(cudaGetLastError());
 }
 
+// The tile prefixes and totals of the populations [pop0, pop1).
+void launch_tile_scan(pop_t* h, cudaStream_t st, const Batch& Bx, int pop0, int pop1) {
+  kernel_begin(h, st, POP_K_OTHER);
+  k_tile_scan<<<(unsigned)(pop1 - pop0), kScanThreads, 0, st>>>(Bx, pop0);
+  kernel_end(h, st);
+}
+
 void launch_weights(pop_t* h, cudaStream_t st) {
   kernel_begin(h, st, POP_K_WEIGHTS);
   k_weights<<<(unsigned)h->lay.ntiles, kThreads, 0, st>>>(h->B, 0);
   kernel_end(h, st);
+  launch_tile_scan(h, st, h->B, 0, h->lay.P);
 }
 
 int launch_resample(pop_t* h, cudaStream_t st) {
@@ -361,26 +372,42 @@ bool fusable(const pop_t* h) {
 // Cloning stage of the current interval and dynamical stage of the next one, for
 // the tiles [tile0, tile0 + ntiles) (whole populations) with the batch view Bx.
 int launch_resample_evolve_range(pop_t* h, cudaStream_t st, float dt_f, const Batch& Bx,
-                                 int tile0, int ntiles) {
+                                 int tile0, int ntiles, int pop0, int pop1) {
   const unsigned grid = (unsigned)ntiles;
   kernel_begin(h, st, POP_K_WEIGHTS);
   k_weights<<<grid, kThreads, 0, st>>>(Bx, tile0);
   kernel_end(h, st);
+  // the tile prefixes from k_tile_scan when every population here has many tiles; a
+  // population of a few tiles is cheaper to sum inside the fused kernel than to scan in
+  // one more launch per interval
+  bool scan = true;
+  for (int p = pop0; p < pop1; ++p) scan = scan && h->desc[p].ntiles > kScanTiles;
+  if (scan) launch_tile_scan(h, st, Bx, pop0, pop1);
   constexpr int GT = POP_FUSE_THREADS;
   kernel_begin(h, st, POP_K_GATHER_EVOLVE);
-  if (h->any_mod) {
-    if (h->lay.W == 1) k_gather<1, GT, true, true><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
-    else k_gather<2, GT, true, true><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
+  if (h->lay.W == 1) {
+    if (h->any_mod) {
+      if (scan) k_gather<1, GT, true, true, true><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
+      else k_gather<1, GT, true, true, false><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
+    } else {
+      if (scan) k_gather<1, GT, true, false, true><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
+      else k_gather<1, GT, true, false, false><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
+    }
   } else {
-    if (h->lay.W == 1) k_gather<1, GT, true, false><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
-    else k_gather<2, GT, true, false><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
+    if (h->any_mod) {
+      if (scan) k_gather<2, GT, true, true, true><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
+      else k_gather<2, GT, true, true, false><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
+    } else {
+      if (scan) k_gather<2, GT, true, false, true><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
+      else k_gather<2, GT, true, false, false><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
+    }
   }
   kernel_end(h, st);
   return cuda_status(cudaGetLastError());
 }
 
 int launch_resample_evolve(pop_t* h, cudaStream_t st, float dt_f) {
-  return launch_resample_evolve_range(h, st, dt_f, h->B, 0, h->lay.ntiles);
+  return launch_resample_evolve_range(h, st, dt_f, h->B, 0, h->lay.ntiles, 0, h->lay.P);
 }
 
 // pop_run's chains.  In a batch of at most two waves of the fused kernel the drain at
@@ -390,17 +417,25 @@ int size_chains(pop_t* h) {
   h->nch = 1;
   h->chain_tile[0] = 0;
   h->chain_tile[1] = h->lay.ntiles;
+  h->chain_pop[0] = 0;
+  h->chain_pop[1] = h->lay.P;
   if (!fusable(h)) return POP_OK;
   constexpr int GT = POP_FUSE_THREADS;
   const void* f = h->lay.W == 1
-                      ? (h->any_mod ? (const void*)k_gather<1, GT, true, true> : (const void*)k_gather<1, GT, true, false>)
-                      : (h->any_mod ? (const void*)k_gather<2, GT, true, true> : (const void*)k_gather<2, GT, true, false>);
+                      ? (h->any_mod ? (const void*)k_gather<1, GT, true, true, false>
+                                    : (const void*)k_gather<1, GT, true, false, false>)
+                      : (h->any_mod ? (const void*)k_gather<2, GT, true, true, false>
+                                    : (const void*)k_gather<2, GT, true, false, false>);
   int per_sm = 0, sms = 0;
   POP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, GT, 0));
   POP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
   const long long wave = (long long)(per_sm < 1 ? 1 : per_sm) * sms;
   const int want = h->lay.ntiles <= 2 * wave ? POP_RUN_CHAINS : POP_RUN_CHAINS_LARGE;
   h->nch = choose_chains(h->desc, h->lay.ntiles, want, h->chain_tile);
+  for (int c = 0, p = 0; c <= h->nch; ++c) {  // chains hold whole populations
+    while (p < h->lay.P && h->desc[p].first_tile < h->chain_tile[c]) ++p;
+    h->chain_pop[c] = p;
+  }
   return POP_OK;
 }
 
@@ -593,6 +628,7 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
   B.S = (unsigned long long*)(ws + lay.o_S);
   B.hist = (unsigned int*)(ws + lay.o_hist);
   B.tile_sum = (unsigned long long*)(ws + lay.o_tile_sum);
+  B.tile_excl = (unsigned long long*)(ws + lay.o_tile_excl);
   B.beta = (unsigned int*)(ws + lay.o_beta);
   B.phi = (const int32_t*)(ws + lay.o_phi);
   B.gtab = (const unsigned long long*)(ws + lay.o_gtab);
@@ -726,7 +762,8 @@ int pop_run(pop_t* h, double dt, const double* s, int64_t n_intervals) {
     for (int64_t i = 0; i < n && lr == POP_OK; ++i)
       for (int c = 0; c < h->nch && lr == POP_OK; ++c)
         lr = launch_resample_evolve_range(h, c == 0 ? st : h->aux_stream[c - 1], dt_f, h->chain[c],
-                                          h->chain_tile[c], h->chain_tile[c + 1] - h->chain_tile[c]);
+                                          h->chain_tile[c], h->chain_tile[c + 1] - h->chain_tile[c],
+                                          h->chain_pop[c], h->chain_pop[c + 1]);
     // the joins are made even after a failed launch, so a capture can end cleanly
     for (int c = 0; c + 1 < h->nch; ++c)
       if (cudaEventRecord(h->ev_join[c], h->aux_stream[c]) != cudaSuccess ||

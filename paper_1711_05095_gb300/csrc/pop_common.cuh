@@ -41,6 +41,11 @@ constexpr int kChunk = kUnit * kChunkUnits;
 constexpr int kKcap = 4096;               // fixed-point weight table size
 constexpr int kHistSmem = 512;            // activity bins kept in shared memory
 constexpr int kMap = 2048;                // new slots of one tile mapped in shared memory
+#ifndef POP_SCAN_TILES
+#define POP_SCAN_TILES 64
+#endif
+constexpr int kScanTiles = POP_SCAN_TILES; // fused stage: k_tile_scan when every population
+                                           // of the launch has more tiles
 constexpr int kMaxL = 128;                // one clone per lane: W <= 2 words
 constexpr int kMaxLWide = 4096;           // one clone per warp: 2 words per lane
 constexpr int kInvStride = kMaxLWide + 1; // per-population 1/r table stride
@@ -86,7 +91,7 @@ struct PopState {
   float a_ref;                 // MODIFIED: reference A of this interval (k_weights)
   uint32_t beta;               // interval being resampled (k_weights)
   int32_t pad;
-  unsigned long long T;        // total weight of this interval ([iid] selection)
+  unsigned long long T;        // total weight of this interval (k_tile_scan or k_gather)
 };
 
 struct Batch {
@@ -105,6 +110,8 @@ struct Batch {
   unsigned long long* S;                // [iid]: exclusive prefix sums of the weights
   unsigned int* hist;                   // [P][kKcap] activity histogram (zero between intervals)
   unsigned long long* tile_sum;         // [ntiles] weight sum of each tile
+  unsigned long long* tile_excl;        // [ntiles] sum of the population's earlier tiles
+                                        // (k_tile_scan)
   unsigned int* beta;                   // interval being evolved (1-based)
   unsigned long long* Xb[2];            // evolved lattices [slots][W], by interval parity
   unsigned long long* Y;                // population lattices between intervals [slots][W]

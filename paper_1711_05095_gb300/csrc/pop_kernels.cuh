@@ -386,8 +386,47 @@ __global__ void __launch_bounds__(kThreads) k_weights(Batch B, int tile0) {
 }
 
 // ---------------------------------------------------------------------------
-// Cloning stage for one tile of old clones.  The tile's exclusive prefix comes from
-// the tile sums; a block scan gives S_k for its clones; old clone k owns the new
+// One block per population scans its tile sums once (each tile's exclusive prefix and
+// the total T), so each block of the cloning stage reads two numbers instead of summing
+// all the population's tile sums, work that grows with the square of its tile count
+// (integer sums: the order of addition is immaterial).
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 1024;
+__global__ void __launch_bounds__(kScanThreads) k_tile_scan(Batch B, int pop0) {
+  __shared__ unsigned long long s_part[kScanThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int p = pop0 + (int)blockIdx.x;
+  const PopDesc d = B.pops[p];
+  unsigned long long run = 0ull;
+  for (int i0 = 0; i0 < d.ntiles; i0 += kScanThreads) {
+    const int i = i0 + tid;
+    const unsigned long long v = (i < d.ntiles) ? B.tile_sum[d.first_tile + i] : 0ull;
+    unsigned long long xs = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, xs, o);
+      if (lane >= o) xs += y;
+    }
+    if (lane == 31) s_part[wid] = xs;
+    __syncthreads();
+    unsigned long long before = run + xs - v, chunk = 0ull;
+#pragma unroll
+    for (int q = 0; q < kScanThreads / 32; ++q) {
+      const unsigned long long t = s_part[q];
+      if (q < wid) before += t;
+      chunk += t;
+    }
+    if (i < d.ntiles) B.tile_excl[d.first_tile + i] = before;
+    run += chunk;
+    __syncthreads();
+  }
+  if (tid == 0) B.st[p].T = run;
+}
+
+// ---------------------------------------------------------------------------
+// Cloning stage for one tile of old clones.  The tile's exclusive prefix and the
+// population total come from k_tile_scan (or the tile sums); a block scan gives S_k
+// for its clones; old clone k owns the new
 // slots [j_lo(S_k), j_lo(S_{k+1})).  The old clones are staged in shared memory, a
 // map from new slot to old clone is scattered there, and every new slot of the
 // tile's range is written once, coalesced.  The first tile of each population adds
@@ -410,7 +449,10 @@ __global__ void __launch_bounds__(kThreads) k_weights(Batch B, int tile0) {
 #ifndef POP_FUSE_MIN_BLOCKS
 #define POP_FUSE_MIN_BLOCKS 8  // 64 registers, no spills; pop_run's chains keep more than one launch resident
 #endif
-template <int W, int NT, bool FUSE = false, bool MOD = false>
+// SCAN: the population totals and tile prefixes come from k_tile_scan; otherwise each
+// block sums its population's tile sums (cheaper for a few tiles per population, but
+// the extra path costs registers and scheduling when compiled into the same kernel).
+template <int W, int NT, bool FUSE = false, bool MOD = false, bool SCAN = true>
 __global__ void __launch_bounds__(NT, FUSE ? POP_FUSE_MIN_BLOCKS : (NT == 128 ? 11 : (NT == 256 ? 6 : 3)))
     k_gather(Batch B, float dt_f, int tile0) {
   constexpr int NI = kTile / NT;   // old clones per thread
@@ -422,7 +464,7 @@ __global__ void __launch_bounds__(NT, FUSE ? POP_FUSE_MIN_BLOCKS : (NT == 128 ? 
   __shared__ int32_t s_K[kTile];
   __shared__ uint32_t s_jlo[kTile + 1];
   __shared__ uint16_t s_src[kMap];
-  __shared__ unsigned long long s_red[NWARP];
+  __shared__ unsigned long long s_red[SCAN ? 1 : NWARP];
   __shared__ unsigned long long s_wsum[NWARP];
   // FUSE only: the population's waiting-time factors, the log table, the slot
   // counter and the block's activity range of the next interval
@@ -495,11 +537,16 @@ __global__ void __launch_bounds__(NT, FUSE ? POP_FUSE_MIN_BLOCKS : (NT == 128 ? 
   const unsigned long long c = 2ull * (unsigned long long)st->U + 1ull;
 
   // population total T and this tile's exclusive prefix
-  unsigned long long tT = 0ull, tE = 0ull;
-  for (int i = tid; i < d.ntiles; i += NT) {
-    const unsigned long long v = B.tile_sum[d.first_tile + i];
-    tT += v;
-    if (i < lt) tE += v;
+  unsigned long long T = 0ull, excl = 0ull, tT = 0ull, tE = 0ull;
+  if constexpr (SCAN) {
+    T = st->T;
+    excl = B.tile_excl[tile];
+  } else {
+    for (int i = tid; i < d.ntiles; i += NT) {
+      const unsigned long long v = B.tile_sum[d.first_tile + i];
+      tT += v;
+      if (i < lt) tE += v;
+    }
   }
 
   // weights of this tile's clones and their scan within each warp
@@ -522,8 +569,12 @@ __global__ void __launch_bounds__(NT, FUSE ? POP_FUSE_MIN_BLOCKS : (NT == 128 ? 
     if (lane >= o) xs += y;
   }
   if (lane == 31) s_wsum[wid] = xs;
-  const unsigned long long T = block_sum_u64_n<NWARP>(tT, s_red);
-  const unsigned long long excl = block_sum_u64_n<NWARP>(tE, s_red);
+  if constexpr (SCAN) {
+    __syncthreads();
+  } else {
+    T = block_sum_u64_n<NWARP>(tT, s_red);
+    excl = block_sum_u64_n<NWARP>(tE, s_red);
+  }
 
   const int sh = max(0, 64 - __clzll((long long)T) - 24);
   const float ratio = __fdiv_rn((float)nc, __uint2float_rn((uint32_t)(T >> sh)));
