@@ -923,8 +923,11 @@ template <int W>
 __global__ void __launch_bounds__(kGuideThreads) k_evolve_guided(Batch B, float dt_f) {
   __shared__ int32_t s_phi[512];
   __shared__ float2 s_log[64];
-  __shared__ int32_t s_k[kMaxL][kGuideThreads];
-  __shared__ unsigned long long s_g[kMaxL / kGuideGroup][kGuideThreads];
+  // exponents and group sums of nb = 64 W bonds, the bonds a lattice of W words holds
+  // (a one-word batch keeps half the shared memory per block, so twice the warps)
+  constexpr int nb = 64 * W, ng = nb / kGuideGroup;
+  __shared__ int32_t s_k[nb][kGuideThreads];
+  __shared__ unsigned long long s_g[ng][kGuideThreads];
   __shared__ int s_min, s_max, s_amin, s_amax;
   __shared__ unsigned int s_ev;
   const int tid = threadIdx.x;
@@ -956,7 +959,7 @@ __global__ void __launch_bounds__(kGuideThreads) k_evolve_guided(Batch B, float 
     active_bonds<W>(x, L, a);
     int r = popc_lat<W>(a);
     unsigned long long R = 0ull;
-    for (int g = 0; g < kMaxL / kGuideGroup; ++g) {
+    for (int g = 0; g < ng; ++g) {
       unsigned long long gs = 0ull;
       for (int b = g * kGuideGroup; b < (g + 1) * kGuideGroup; ++b) {
         int k = kGuideOff;
@@ -995,12 +998,12 @@ __global__ void __launch_bounds__(kGuideThreads) k_evolve_guided(Batch B, float 
       // the group sums, so both loops stop inside the arrays; the bounds make it explicit)
       unsigned long long cum = 0ull;
       int g = 0;
-      while (g < kMaxL / kGuideGroup - 1 && cum + s_g[g][tid] <= kk) {
+      while (g < ng - 1 && cum + s_g[g][tid] <= kk) {
         cum += s_g[g][tid];
         ++g;
       }
       int b = g * kGuideGroup;
-      for (; b < kMaxL - 1; ++b) {
+      for (; b < nb - 1; ++b) {
         cum += guided_q(s_k[b][tid], tab);
         if (cum > kk) break;
       }
