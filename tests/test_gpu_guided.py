@@ -82,6 +82,13 @@ def test_guided_parity_batch(pg):
     guided_parity(pg, pops, [0.05, -0.01, 0.1], 0.1, 4, [potential(1, 0.3), potential(2, 0.2), potential(3, 0.5)])
 
 
+def test_guided_parity_batch_one_word(pg):
+    # one-word lattices (L <= 64): the kernel keeps exponent rows for 64 bonds
+    pops = [dict(L=18, N=7, n_clones=1300, seed=11), dict(L=64, N=32, n_clones=2049, seed=12),
+            dict(L=41, N=20, n_clones=600, seed=13)]
+    guided_parity(pg, pops, [0.2, 0.004, -0.05], 0.1, 4, [potential(7, 0.4), potential(8, 0.1), potential(9, 0.3)])
+
+
 def test_guided_run_equals_steps(pg):
     pops = [dict(L=50, N=25, n_clones=2000, seed=7, weight_mode=GUIDED),
             dict(L=100, N=40, n_clones=1300, seed=8, weight_mode=GUIDED)]
