@@ -207,18 +207,8 @@ __device__ __forceinline__ int popc_lat(const unsigned long long (&a)[W]) {
   else return __popcll(a[0]) + __popcll(a[1]);
 }
 
-// Position of the k-th (0-based) set bit of a, k < popc(a).
-#ifdef POP_KTH_FNS
-__device__ __forceinline__ int kth_set_bit64(unsigned long long a, uint32_t k) {
-  const uint32_t lo = (uint32_t)a;
-  const uint32_t c0 = (uint32_t)__popc(lo);
-  const bool in_lo = k < c0;
-  const uint32_t word = in_lo ? lo : (uint32_t)(a >> 32);
-  const uint32_t kk = in_lo ? k : k - c0;
-  return (int)__fns(word, 0u, (int)kk + 1) + (in_lo ? 0 : 32);
-}
-#else
-// binary descent on population counts of halves
+// Position of the k-th (0-based) set bit of a, k < popc(a): binary descent on the
+// population counts of halves.
 __device__ __forceinline__ int kth_set_bit64(unsigned long long a, uint32_t k) {
   uint32_t x = (uint32_t)a;
   int pos = 0;
@@ -236,7 +226,6 @@ __device__ __forceinline__ int kth_set_bit64(unsigned long long a, uint32_t k) {
   if (k >= c) { pos += 1; }
   return pos;
 }
-#endif
 
 template <int W>
 __device__ __forceinline__ int kth_bond(const unsigned long long (&a)[W], uint32_t k) {
@@ -295,16 +284,6 @@ __device__ __forceinline__ void store_lat(unsigned long long* base, int64_t slot
   } else {
     reinterpret_cast<ulonglong2*>(base)[slot] = make_ulonglong2(x[0], x[1]);
   }
-}
-
-__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
