@@ -512,6 +512,8 @@ def main():
         "seconds_to_se_guided": guided,
         "clocks": clocks,
         "wall_s_timed": wall,
+        # the same steps counted in clone-intervals (one clone through one interval)
+        "clone_intervals_per_s": clone_intervals * M * args.steps * world / t_dev,
         "psi_check": {"lambda=-20": float(psi[0]), "lambda=40": float(psi[-1])},
         "other_workloads": others,
     }
