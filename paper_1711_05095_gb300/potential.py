@@ -12,7 +12,7 @@ window network phi is trained as that classifier on the GPU and compiled to the
 Typical use::
 
     end, anc = ancestral_samples(pops, s, dt, burn, lag)        # plain cloning runs
-    tr = train(end, anc, L, steps=2000)                         # Adam on the GPU
+    tr, losses = train(end, anc, L, steps=2000)                 # Adam on the GPU
     phi = tr.potential()                                        # 512 floats
     guided = PopulationBatch([dict(q, weight_mode=POP_GUIDED) ...]); guided.set_potential(p, phi)
 """
