@@ -126,3 +126,13 @@ def test_iid_copy_counts_are_multinomial():
     heavy, light = counts[:n // 2].sum() / R, counts[n // 2:].sum() / R
     assert abs(heavy - 0.75 * n) <= 5 * math.sqrt(n * 0.75 * 0.25 / R)
     assert abs(heavy + light - n) < 1e-9
+
+
+def test_eq_selection_has_smaller_variance_than_iid():
+    # Sec. 4.4: at the same N_c, equally spaced points ([eq]) give a smaller variance of
+    # k-hat than independent ones ([iid]), which delete clones that [eq] keeps; with 40
+    # runs each, equal variances would give a ratio above 1.9 with probability < 2.5 %
+    L, N, s = 12, 6, 0.1
+    eq = [oracle.run(L, N, 128, seed, s, 0.1, 500)["k_hat"] for seed in range(40)]
+    iid = [oracle.run(L, N, 128, seed, s, 0.1, 500, iid=True)["k_hat"] for seed in range(40)]
+    assert np.var(iid, ddof=1) > 2.5 * np.var(eq, ddof=1)
