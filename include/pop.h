@@ -279,7 +279,9 @@ int pop_events(pop_t* pop, uint64_t* h_events);
 #define POP_K_GATHER 2         /* cloning stage: [eq] copies, [iid] selection */
 #define POP_K_GATHER_EVOLVE 3  /* cloning stage of one interval fused with the
                                   dynamical stage of the next (pop_run, [eq], L <= 128) */
-#define POP_K_OTHER 4          /* initial state, estimates, density mode */
+#define POP_K_OTHER 4          /* initial state, estimates, density mode, ancestry
+                                  (pop_lineage), and the scan of each population's tile
+                                  sums before a cloning stage */
 #define POP_NKINDS 5
 
 /*
