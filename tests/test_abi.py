@@ -76,6 +76,24 @@ def test_init_rejects_bad_arguments_without_device(lib):
     lib.pop_free(None)
 
 
+def test_every_handle_call_rejects_a_null_handle(lib):
+    # host-side checks made before any device work, so they run without a GPU
+    E = pg.POP_ERR_ARG
+    assert lib.pop_set_state(None, 0, None, None) == E
+    assert lib.pop_run(None, 0.1, None, 1) == E
+    assert lib.pop_estimate_psi(None, None, None, None) == E
+    assert lib.pop_copy_state(None, 0, None, None, None, None) == E
+    assert lib.pop_events(None, None) == E
+    assert lib.pop_launch_count(None, None) == E
+    assert lib.pop_kernel_times(None, 0.1, None, 1, 0, None, None, None) == E
+    assert lib.pop_autotune(None, 0.1, None, 1, None) == E
+    assert lib.pop_lineage(None, None, None) == E
+    assert lib.pop_density_mode(None, 1, None) == E
+    assert lib.pop_run_chains(None, None) == -1
+    assert lib.pop_slots(None) == -1
+    assert lib.pop_first_slot(None, 0) == -1
+
+
 def test_strerror(lib):
     for code in (0, -1, -2, -3, -4, -5):
         assert lib.pop_strerror(code)
