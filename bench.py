@@ -54,7 +54,7 @@ N_SM = 152
 ISSUE_OPS_PER_SM_CLK = 128                      # 4 schedulers x 32 lanes
 
 # Counters of one whole-batch launch of the dominant kernel on this workload, from ncu
-# captures (profiles/): DRAM bytes (read + write), and issue slots busy, ALU pipe and
+# captures: DRAM bytes (read + write), and issue slots busy, ALU pipe and
 # active lanes per instruction; valid only for the kernel sources they were taken on
 # (hash of the two device headers).
 KERNEL_TRAFFIC = {"bytes": 17178624, "issue_slots_busy": 0.6165, "alu_pipe": 0.5161,

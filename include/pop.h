@@ -20,9 +20,9 @@
  *   - Work is enqueued on the CUDA stream given to pop_init.  pop_evolve,
  *     pop_resample and pop_run return once their kernels are enqueued; the
  *     host-reading calls (pop_estimate_psi, pop_copy_state, pop_events) wait for
- *     the stream.  Kernel-side errors (an activity outside the weight table, a
- *     spin-wait that gave up) are sticky in device memory and are returned by the
- *     next host-reading call.
+ *     the stream.  Kernel-side errors (an activity outside the weight table, an
+ *     interval that needed more than 2^24 BKL steps) are sticky in device memory and
+ *     are returned by the next host-reading call.
  *   - A handle is not thread-safe; distinct handles are independent.
  *   - Lattices: site i of a clone is bit (i mod 64) of 64-bit word (i div 64); a
  *     clone occupies W = ceil(max_p L_p / 64) consecutive words (bits >= L zero).
@@ -49,8 +49,9 @@ extern "C" {
 #define POP_OK 0
 #define POP_ERR_ARG (-1)     /* an argument is out of its documented range */
 #define POP_ERR_CUDA (-2)    /* a CUDA runtime call failed (no device, launch failure) */
-#define POP_ERR_RANGE (-3)   /* an interval activity differed from the reference by >= POP_KCAP */
-#define POP_ERR_TIMEOUT (-4) /* a device-side wait gave up after its iteration limit */
+#define POP_ERR_RANGE (-3)   /* an interval activity differed from the reference by >= POP_KCAP,
+                                or a clone's interval needed more than 2^24 BKL steps */
+/* (-4) is not used: no kernel of this library waits on the device */
 #define POP_ERR_STATE (-5)   /* call out of order, or s changed during a run */
 
 /* weight modes (eq. upsdef) */
@@ -324,10 +325,13 @@ int pop_launch_count(pop_t* pop, uint64_t* h_n);
  * Results equal those of pop_resample for the same activities.  Scratch lives in
  * a static device array of 120 KiB that every GPU which loads the library holds
  * until the process exits; each call clears what must start at zero, the array
- * keeps the last call's contents, and calls that overlap on the GPU race on it.
- * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  Waits for
- * the stream.  No cudaMalloc, cudaFree or allocating library routine is called.
+ * keeps the last call's contents (the weight tables are re-sent only when s or the
+ * weight scale of N_c changes), and calls that overlap on the GPU race on it.  The
+ * array of the CURRENT device is used: the stream must belong to that device.  The
+ * first call on a device looks up the array's device address (with that device
+ * current).  Every call synchronises the stream and copies from pageable host
+ * memory, so it must not be called on a stream that is being captured.  No
+ * cudaMalloc, cudaFree or allocating library routine is called.
  */
 #define POP_NOALLOC_MAX_CLONES (1LL << 20)
 int pop_select_noalloc(const int32_t* d_dK, int64_t n_clones, double s, uint64_t seed,

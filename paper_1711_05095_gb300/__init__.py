@@ -19,7 +19,6 @@ POP_OK = 0
 POP_ERR_ARG = -1
 POP_ERR_CUDA = -2
 POP_ERR_RANGE = -3
-POP_ERR_TIMEOUT = -4
 POP_ERR_STATE = -5
 POP_PLAIN = 0
 POP_MODIFIED = 1
@@ -331,12 +330,15 @@ def select_noalloc(d_dK, s, seed, interval, d_anc, stream=None):
     callers that cannot allocate device memory; nothing is allocated here."""
     import torch
     n = int(d_dK.numel())
-    if d_anc.numel() != n or d_dK.dtype != torch.int32 or d_anc.dtype != torch.int32:
+    if (d_anc.numel() != n or d_dK.dtype != torch.int32 or d_anc.dtype != torch.int32
+            or not d_dK.is_cuda or d_anc.device != d_dK.device):
         raise PopError(POP_ERR_ARG, "pop_select_noalloc")
-    st = stream if stream is not None else torch.cuda.current_stream(d_dK.device)
-    term = ctypes.c_double(0.0)
-    rc = library().pop_select_noalloc(ctypes.c_void_p(d_dK.data_ptr()), n, float(s), int(seed),
-                                      int(interval), ctypes.c_void_p(d_anc.data_ptr()),
-                                      ctypes.byref(term), ctypes.c_void_p(st.cuda_stream))
+    # the library uses the scratch array of the current device: make it the tensors' one
+    with torch.cuda.device(d_dK.device):
+        st = stream if stream is not None else torch.cuda.current_stream(d_dK.device)
+        term = ctypes.c_double(0.0)
+        rc = library().pop_select_noalloc(ctypes.c_void_p(d_dK.data_ptr()), n, float(s), int(seed),
+                                          int(interval), ctypes.c_void_p(d_anc.data_ptr()),
+                                          ctypes.byref(term), ctypes.c_void_p(st.cuda_stream))
     _check(rc, "pop_select_noalloc")
     return term.value

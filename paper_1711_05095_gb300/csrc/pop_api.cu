@@ -1088,8 +1088,7 @@ const char* pop_strerror(int status) {
     case POP_OK: return "ok";
     case POP_ERR_ARG: return "invalid argument";
     case POP_ERR_CUDA: return "CUDA runtime error";
-    case POP_ERR_RANGE: return "interval activity outside the weight table";
-    case POP_ERR_TIMEOUT: return "device-side wait gave up";
+    case POP_ERR_RANGE: return "interval activity outside the weight table, or step limit reached";
     case POP_ERR_STATE: return "call out of order or bias changed during a run";
     default: return "unknown status";
   }

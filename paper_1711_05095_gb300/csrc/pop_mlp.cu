@@ -50,14 +50,17 @@ struct Work {
 
 __device__ __forceinline__ float bf(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
+// GELU(x) = x Phi(x) with Phi(x) = erfc(-x / sqrt 2) / 2: the complementary error
+// function keeps the relative accuracy for negative x, where 1 + erf would cancel.
 __device__ __forceinline__ float gelu(float x) {
-  return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f));
+  return 0.5f * x * erfcf(x * -0.70710678118654752f);
 }
 __device__ __forceinline__ float gelu_grad(float x) {
-  return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
+  return 0.5f * erfcf(x * -0.70710678118654752f) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
 }
 
-// Layer 1 (9 binary inputs): Z1 = X bf16(W1)^T + b1, H1 = GELU(Z1).
+// Layer 1 (9 binary inputs): Z1 = X bf16(W1)^T + b1 in FP32, b1 first and then the set
+// inputs in increasing k (a fixed order, so Z1 is reproducible bit for bit), H1 = GELU(Z1).
 __global__ void k_layer1(Work w) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;  // p * 128 + h
   if (i >= kPat * kH) return;

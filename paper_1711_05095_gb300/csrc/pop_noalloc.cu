@@ -11,8 +11,11 @@
 // histogram, per-tile weight sums and a few scalars) lives in one file-scope
 // static __device__ array of kScratchBytes (120 KiB), held by every GPU that loads
 // the library until the process exits.  Every call shares that array: the
-// histogram and scalars are cleared at the start of each call, and calls that
-// overlap on the GPU (two streams, or two host threads) race on it.
+// histogram and scalars are cleared at the start of each call, the tables are uploaded
+// only when the bias or the weight scale differs from the last upload on that device,
+// and calls that overlap on the GPU (two streams, or two host threads) race on it.
+// A call synchronises its stream and copies from pageable host memory, so it cannot
+// be made on a stream that is being captured into a CUDA graph.
 //
 // The same arithmetic as k_weights / k_gather of the batch path (pop_kernels.cuh),
 // restricted to one population and without the lattice copy, so its ancestors and
@@ -51,6 +54,22 @@ static __device__ __align__(256) unsigned char g_select_scratch[kScratchBytes];
 
 // device address of g_select_scratch per device, set on the first call on that device
 static unsigned char* g_scratch_ptr[kMaxDevices];
+
+// the bias and weight scale whose tables the array of each device holds (the tables
+// depend on nothing else), so a call with the same s and N_c skips their upload
+struct TableKey {
+  bool valid;
+  double s;
+  int F;
+};
+static TableKey g_tables[kMaxDevices];
+
+// host copies of the tables, built per thread outside the stack (96 KiB)
+struct HostTables {
+  unsigned long long wtab[kKcap];
+  double qtab[kKcap], qm1tab[kKcap];
+};
+static thread_local HostTables t_host;
 
 struct SelArgs {
   const int32_t* dK;
@@ -225,17 +244,19 @@ extern "C" int pop_select_noalloc(const int32_t* d_dK, int64_t n_clones, double 
   unsigned char* scratch = g_scratch_ptr[dev];
   cudaStream_t stream = (cudaStream_t)cuda_stream;
 
-  // tables of this bias (the same definitions as the batch path), on the host stack
-  unsigned long long wtab[kKcap];
-  double qtab[kKcap], qm1tab[kKcap];
+  // tables of this bias (the same definitions as the batch path); uploaded only when
+  // the array does not already hold those of this (s, F)
   const int F = 61 - ceil_log2(n_clones);
-  const double a = std::fabs(s);
-  for (int k = 0; k < kKcap; ++k) {
-    const double x = -a * (double)k;
-    const double q = std::exp(x);
-    wtab[k] = (unsigned long long)std::nearbyint(std::ldexp(q, F));
-    qtab[k] = q;
-    qm1tab[k] = std::expm1(x);
+  const bool upload = !(g_tables[dev].valid && g_tables[dev].s == s && g_tables[dev].F == F);
+  if (upload) {
+    const double a = std::fabs(s);
+    for (int k = 0; k < kKcap; ++k) {
+      const double x = -a * (double)k;
+      const double q = std::exp(x);
+      t_host.wtab[k] = (unsigned long long)std::nearbyint(std::ldexp(q, F));
+      t_host.qtab[k] = q;
+      t_host.qm1tab[k] = std::expm1(x);
+    }
   }
   SelState st0;
   std::memset(&st0, 0, sizeof st0);
@@ -258,10 +279,17 @@ extern "C" int pop_select_noalloc(const int32_t* d_dK, int64_t n_clones, double 
   A.seed = seed;
   A.s = s;
 
-  if (cudaMemcpyAsync(A.wtab, wtab, sizeof wtab, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
-      cudaMemcpyAsync(A.qtab, qtab, sizeof qtab, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
-      cudaMemcpyAsync(A.qm1tab, qm1tab, sizeof qm1tab, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
-      cudaMemsetAsync(A.hist, 0, (size_t)kKcap * 4, stream) != cudaSuccess ||
+  if (upload) {
+    // pageable sources: each copy has read its source when it returns
+    g_tables[dev].valid = false;
+    if (cudaMemcpyAsync(A.wtab, t_host.wtab, sizeof t_host.wtab, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+        cudaMemcpyAsync(A.qtab, t_host.qtab, sizeof t_host.qtab, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+        cudaMemcpyAsync(A.qm1tab, t_host.qm1tab, sizeof t_host.qm1tab, cudaMemcpyHostToDevice,
+                        stream) != cudaSuccess)
+      return POP_ERR_CUDA;
+    g_tables[dev] = TableKey{true, s, F};
+  }
+  if (cudaMemsetAsync(A.hist, 0, (size_t)kKcap * 4, stream) != cudaSuccess ||
       cudaMemcpyAsync(A.st, &st0, sizeof st0, cudaMemcpyHostToDevice, stream) != cudaSuccess)
     return POP_ERR_CUDA;
   k_sel_range<<<A.ntiles, kThreads, 0, stream>>>(A);

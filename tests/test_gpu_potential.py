@@ -32,36 +32,40 @@ def batch(n, L, seed):
     return words, g.integers(0, 2, n).astype(np.uint8)
 
 
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
-
-
-@pytest.mark.parametrize("L,n", [(20, 300), (70, 200), (128, 150)])
+@pytest.mark.parametrize("L,n", [(20, 300), (70, 200), (128, 150), (50, 4096)])
 def test_loss_and_gradient_match_oracle(env, L, n):
+    # every element of the gradient against the FP64 oracle with BF16 operands, within
+    # the element-wise tolerance oracle/mlp.py derives for an FP32 / BF16 evaluation:
+    # twice the first-order running error bound of FP32 sums (n u / (1 - n u) times the
+    # magnitudes summed, the tensor-core products as K/16 accumulation steps), FP32
+    # GELU / exp to a few ulp, and one BF16 ulp wherever an operand lies within its
+    # error of a rounding tie (tests/test_oracle_mlp.py pins that bound against an
+    # independent FP32 evaluation and against planted mistakes)
     torch, pg, potential = env
     theta = potential.init_params(7) + np.random.default_rng(L).normal(0, 0.05, potential.N_PARAMS).astype(np.float32)
     words, labels = batch(n, L, L)
     tr = potential.Trainer(theta=theta)
     loss, g = tr.grad(torch.from_numpy(words.view(np.int64)).cuda(), torch.from_numpy(labels).cuda(), L)
     want_loss, want_g = mlp.loss_and_grad(theta, words, labels, L, bf=True)
-    assert abs(loss - want_loss) <= 1e-4 * abs(want_loss)
+    tol_loss, tol = mlp.grad_tolerance(theta, words, labels, L)
+    assert abs(loss - want_loss) <= tol_loss, (loss, want_loss, tol_loss)
     k = 0
     for name, shape in mlp.SIZES:
         m = int(np.prod(shape))
-        # BF16 operands: a rounding that lands on the other side of a tie in FP32 against
-        # FP64 moves single products by 2^-8 relative; the sums stay within 1e-2
-        assert rel(g[k:k + m], want_g[k:k + m]) < 2e-2, name
+        np.testing.assert_array_less(np.abs(g[k:k + m] - want_g[k:k + m]), tol[k:k + m] + 1e-30,
+                                     err_msg=name)
         k += m
-    assert rel(g, want_g) < 1e-2
 
 
 def test_compiled_table_matches_oracle(env):
+    # the 512 potential values against the oracle's forward pass, element-wise within
+    # twice the running error bound of the FP32 / BF16 evaluation
     torch, pg, potential = env
     theta = potential.init_params(3) + np.random.default_rng(1).normal(0, 0.1, potential.N_PARAMS).astype(np.float32)
     tr = potential.Trainer(theta=theta)
     phi = tr.potential()
     want, _ = mlp.forward(theta, bf=True)
-    np.testing.assert_allclose(phi, want, atol=2e-3 * max(1.0, np.abs(want).max()))
+    np.testing.assert_array_less(np.abs(phi - want), mlp.phi_tolerance(theta) + 1e-30)
 
 
 def test_adam_step_matches_oracle(env):

@@ -95,3 +95,94 @@ def test_adam_step_written_out():
     # first step: m_hat = g, v_hat = g^2, so the update is lr * g / (|g| + eps)
     assert abs(float(th[0]) - (0.5 - 0.01 * 0.2 / (0.2 + 1e-8))) < 1e-7
     assert abs(float(m[0]) - 0.02) < 1e-8 and abs(float(v[0]) - 0.001 * 0.04) < 1e-11   # float32 state
+
+
+def _f32_evaluation(theta, words, labels, L, seed):
+    """The network evaluated in FP32 the way a GPU may: FP32 activations (correctly
+    rounded GELU), BF16 operands rounded from them, FP32 matrix products and FP32 sums in
+    a shuffled order.  Independent of loss_and_grad except for the shared definitions."""
+    f = np.float32
+    P = mlp.unpack(theta)
+    X = mlp.patterns().astype(f)
+    bf = lambda a: mlp.bf16(np.asarray(a, dtype=f)).astype(f)
+    Z1 = mlp.layer1_f32(theta).astype(f)
+    H1 = mlp.gelu(Z1.astype(np.float64)).astype(f)
+    Z2 = (bf(H1) @ bf(P["W2"]).T).astype(f) + P["b2"].astype(f)
+    H2 = mlp.gelu(Z2.astype(np.float64)).astype(f)
+    Phi = (bf(H2) @ bf(P["W3"])).astype(f) + f(P["b3"])
+    counts = mlp.window_counts(words, L).astype(f)
+    y = np.asarray(labels, dtype=f)
+    n = y.size
+    z = f(0.5) * (counts @ Phi) + f(P["c"])
+    loss = float(np.mean((np.logaddexp(0.0, z.astype(np.float64)) - y * z).astype(f)))
+    dz = ((f(1) / (f(1) + np.exp(-z))) - y) / f(n)
+    order = np.random.default_rng(seed).permutation(n)
+    dPhi = f(0.5) * (counts[order].T @ dz[order])
+    g = {}
+    g["c"] = np.array(dz[order].sum(dtype=f))
+    g["b3"] = np.array(dPhi[::-1].sum(dtype=f))
+    g["W3"] = bf(H2).T @ dPhi
+    dZ2 = (np.outer(dPhi, bf(P["W3"])) * mlp.gelu_grad(Z2.astype(np.float64)).astype(f)).astype(f)
+    g["W2"] = bf(dZ2).T @ bf(H1)
+    g["b2"] = dZ2[::-1].sum(axis=0, dtype=f)
+    dH1 = bf(dZ2) @ bf(P["W2"])
+    dZ1 = (dH1 * mlp.gelu_grad(Z1.astype(np.float64)).astype(f)).astype(f)
+    g["W1"] = dZ1.T @ X
+    g["b1"] = dZ1.sum(axis=0, dtype=f)
+    return loss, mlp.pack(g)
+
+
+@pytest.mark.parametrize("L,n,seed", [(20, 300, 1), (70, 200, 2), (128, 150, 3)])
+def test_grad_tolerance_covers_an_fp32_evaluation(L, n, seed):
+    # the element-wise parity tolerance (twice the first-order running error bound of an
+    # FP32 / BF16 evaluation) holds for an FP32 evaluation with its own rounding, order
+    # and BF16 decisions
+    theta = (mlp.init_params(7) + np.random.default_rng(L).normal(0, 0.05, mlp.N_PARAMS)).astype(np.float32)
+    words, labels = random_batch(n, L, seed)
+    loss, g = mlp.loss_and_grad(theta, words, labels, L, bf=True)
+    tol_loss, tol = mlp.grad_tolerance(theta, words, labels, L)
+    l32, g32 = _f32_evaluation(theta, words, labels, L, seed)
+    assert abs(l32 - loss) <= tol_loss
+    bad = np.abs(g32 - g) > tol
+    assert not bad.any(), (np.flatnonzero(bad)[:10], (np.abs(g32 - g) / tol).max())
+    # the FP32 evaluation really does differ (it is not the oracle itself)
+    assert np.abs(g32 - g).max() > 0
+
+
+def test_grad_tolerance_rejects_planted_mistakes():
+    # mistakes a kernel could make fail the element-wise check: a sign in one W1 or b1
+    # element, a transposed W2 gradient, a dropped b3 term, a missing 1/2 in dPhi
+    L, n = 40, 200
+    theta = (mlp.init_params(11) + np.random.default_rng(4).normal(0, 0.05, mlp.N_PARAMS)).astype(np.float32)
+    words, labels = random_batch(n, L, 9)
+    _, g = mlp.loss_and_grad(theta, words, labels, L, bf=True)
+    _, tol = mlp.grad_tolerance(theta, words, labels, L)
+    off = {}
+    k = 0
+    for name, shape in mlp.SIZES:
+        off[name] = (k, int(np.prod(shape)))
+        k += int(np.prod(shape))
+
+    def rejected(h):
+        return bool((np.abs(h - g) > tol).any())
+
+    for name in ("W1", "b1", "W3"):
+        k0, m = off[name]
+        i = k0 + int(np.argmax(np.abs(g[k0:k0 + m])))
+        h = g.copy()
+        h[i] = -h[i]
+        assert rejected(h), name
+    # W1: most elements are far above their tolerance, so a sign error anywhere is seen
+    k0, m = off["W1"]
+    assert np.mean(np.abs(g[k0:k0 + m]) > tol[k0:k0 + m]) > 0.8
+    h = g.copy()
+    k0, m = off["W2"]
+    h[k0:k0 + m] = g[k0:k0 + m].reshape(128, 128).T.reshape(-1)
+    assert rejected(h)
+    h = g.copy()
+    h[off["b3"][0]] = 0.0
+    assert rejected(h)
+    h = g.copy()
+    k0, m = off["W3"]
+    h[k0:k0 + m] *= 2.0
+    assert rejected(h)
