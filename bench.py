@@ -1,19 +1,28 @@
 #!/usr/bin/env python3
 """Benchmark of the SSEP cloning estimator on GB300: clone-events per second.
 
-Workload (the batched s-sweep): 64 populations of the SSEP on a ring of L = 50 sites
-with N = 25 particles, biases lambda = s L^2 evenly spaced in [-20, 40], N_c = 16384
-clones each (2^20 clones), cloning interval dt = 0.1, t_obs = 1000 (M = 10000
-intervals).  One step is one whole run: pop_init (initial configurations), pop_autotune
-(launch configuration), M intervals of dynamical + cloning stages (pop_run,
-captured CUDA graphs), and pop_estimate_psi.  clone-events = BKL hops executed by all clones (arXiv:1711.05095
-measures the serial and parallel cost of exactly this loop, Sec. 6).
+Workload (the large-population batch): 32 populations of the SSEP on a ring of L = 128
+sites with N = 64 particles, biases lambda = s L^2 in {5, 10, 15, 20} x 8 seeds,
+N_c = 2^20 clones each (2^25 clones), cloning interval dt = 0.05, t_obs = 2000
+(M = 40000 intervals per run).  One step is one block of `--block` (default 1000)
+consecutive intervals of one continuing run: dynamical + cloning stages through
+pop_run (captured CUDA graphs); a run that has reached M intervals is replaced by a
+fresh one between steps (its initial state is not part of a step).  clone-events =
+BKL hops executed by all clones (arXiv:1711.05095 measures the serial and parallel
+cost of exactly this loop, Sec. 6).
+
+Beside the headline the line carries: the dominant kernel's roofline from the launches
+of the timed configuration, the end-to-end figure from host configurations, the other
+batch shapes (s-sweep, uneven batch, the separate cloning stage against HBM), a
+guided-against-plain comparison at L = 128, and the CPU oracle's throughput.
 
 Prints one JSON line.  --impl reference times the CPU oracle on a bounded sample of
-the same workload instead.
+the same workload instead.  --config5 runs the learned-potential study at its full
+size (a separate, longer measurement that prints its own JSON).
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -50,15 +59,13 @@ OPS_STOP = OPS_HOP - 25 - 7 - 1                 # the step that ends the interva
 # its prefix sum (2), the inverse j_lo of the prefix by 128-bit products and compares
 # (16), and for the new clone the ancestor lookup and its lattice and K (3)
 OPS_GATHER = 3 + 2 + 16 + 3                     # 24
-N_SM = 152
 ISSUE_OPS_PER_SM_CLK = 128                      # 4 schedulers x 32 lanes
 
-# Counters of one whole-batch launch of the dominant kernel on this workload, from ncu
-# captures: DRAM bytes (read + write), and issue slots busy, ALU pipe and
-# active lanes per instruction; valid only for the kernel sources they were taken on
-# (hash of the two device headers).
-KERNEL_TRAFFIC = {"bytes": 17178624, "issue_slots_busy": 0.6165, "alu_pipe": 0.5161,
-                  "lanes_per_instruction": 24.11, "sources": "9eaf7124658b13ee"}
+# Counters of one launch of the dominant kernel on this workload, from an ncu capture
+# of a smaller batch of the same shape scaled to a full launch: DRAM bytes (read +
+# write), issue slots busy, ALU pipe and active lanes per instruction; valid only for
+# the kernel sources they were taken on (hash of the two device headers).
+KERNEL_TRAFFIC = None
 
 
 def kernel_sources_digest():
@@ -76,12 +83,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--intervals", type=int, default=None,
-                    help="override M (profiling runs only; the bench line then names it)")
+    ap.add_argument("--block", type=int, default=1000, help="intervals per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-guided", action="store_true", help="skip the guided-cloning SE measurement")
+    ap.add_argument("--no-guided", action="store_true", help="skip the guided-against-plain comparison")
     ap.add_argument("--no-others", action="store_true", help="skip the other batch shapes")
-    ap.add_argument("--kernel-intervals", type=int, default=200)
+    ap.add_argument("--kernel-intervals", type=int, default=100)
+    ap.add_argument("--config5", action="store_true",
+                    help="the learned-potential study at full size instead of the bench line")
     return ap.parse_args()
 
 
@@ -140,7 +148,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def dist_setup(args):
+def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -165,84 +173,187 @@ def reduce_over_ranks(dist, device, seconds, units):
     return float(t.item()), float(e.item())
 
 
-def seconds_to_se(sigma, batch_seconds, batch_runs, target=1e-3):
-    """Device seconds to bring the standard error of psi_hat over independent runs to
-    `target`: R = ceil((sigma / target)^2) runs at the measured time per run."""
-    import math
-    runs = max(2, int(math.ceil((sigma / target) ** 2)))
-    return runs, batch_seconds * runs / batch_runs
+def seconds_to_se(sigma, seconds_per_run, target):
+    """Seconds of device time to bring the standard error of psi_hat to `target`: the
+    variance of psi_hat over independent runs times the cost of one run, divided by
+    target^2 (R = (sigma / target)^2 runs of this length, or one run R times as long:
+    the variance of psi_hat falls as 1/t_obs once t_obs is many correlation times)."""
+    return sigma * sigma * seconds_per_run / (target * target)
 
 
-def cpu_oracle_sample(w, pop_idx, M):
-    """The oracle as it stands, single-threaded, on the listed populations for M
-    intervals.  Returns (events, seconds)."""
+# ---------------------------------------------------------------------------
+# CPU oracle (bench's cpu_baseline leg and the reference arm only)
+# ---------------------------------------------------------------------------
+def cpu_oracle_intervals(w, pop_idx, n_intervals):
+    """The oracle as it stands, single-threaded: the listed populations are initialised
+    (not timed) and then run n_intervals intervals (dynamical + cloning stage), timed.
+    Returns (events, seconds)."""
     import oracle
     oracle.lib()
-    events, t0 = 0, time.perf_counter()
+    events, sec = 0, 0.0
     for p in pop_idx:
         q = w["pops"][p]
-        r = oracle.run(q["L"], q["N"], q["n_clones"], q["seed"], w["s"][p], w["dt"], M)
-        events += r["events"]
-    return events, time.perf_counter() - t0
+        o = oracle.Population(q["L"], q["N"], q["n_clones"], q["seed"])
+        t0 = time.perf_counter()
+        for _ in range(n_intervals):
+            o.evolve(w["dt"])
+            o.resample(w["s"][p])
+        sec += time.perf_counter() - t0
+        events += o.events
+    return events, sec
 
 
 def _oracle_one(args):
-    w, p, M = args
-    return cpu_oracle_sample(w, [p], M)[0]
+    w, p, n = args
+    return cpu_oracle_intervals(w, [p], n)
 
 
-def cpu_oracle_parallel(w, pop_idx, M):
-    """The oracle as it stands, one process per population on as many host cores
-    (spawned processes: nothing is forked from a process that has used the GPU).
-    Returns the cpu_baseline-style record over the wall time of the whole pool."""
+def cpu_oracle_parallel(w, pop_idx, n_intervals):
+    """The same oracle on as many host cores, one spawned process per population
+    (nothing is forked from a process that has used the GPU); the rate is the events of
+    all processes over the longest process's interval time."""
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
     with ctx.Pool(len(pop_idx)) as pool:
-        pool.map(_oracle_one, [(w, pop_idx[0], 1)] * len(pop_idx))   # start-up and oracle build
-        t0 = time.perf_counter()
-        events = sum(pool.map(_oracle_one, [(w, p, M) for p in pop_idx]))
-        sec = time.perf_counter() - t0
+        res = pool.map(_oracle_one, [(w, p, n_intervals) for p in pop_idx])
+    events = sum(r[0] for r in res)
+    sec = max(r[1] for r in res)
     return {"value": events / sec, "unit": UNIT, "cores": len(pop_idx), "kind": "oracle",
-            "sample": "populations 0..%d (N_c=16384 each), first %d of the 10000 intervals, one "
-                      "process per population; %.1f s" % (len(pop_idx) - 1, M, sec)}
+            "sample": "populations 0..%d of the large-population batch (N_c=2^20 each), %d intervals "
+                      "each after an untimed initial state, one process per population; %.1f s"
+                      % (len(pop_idx) - 1, n_intervals, sec)}
 
 
-def reference_arm(args, w, world, rank):
+def workload_name(w, block):
+    return ("large_population L=128 N=64 lambda in {5,10,15,20} x 8 seeds N_c=2^20 each dt=%g t_obs=%g "
+            "(M=%d); one step = %d consecutive intervals of one continuing run"
+            % (w["dt"], w["t_obs"], w["M"], block))
+
+
+def reference_arm(args, w, rank):
+    """The oracle on a bounded sample of the same workload: per step, one interval of
+    one population (N_c = 2^20, L = 128), the population initialised before the steps."""
     if rank != 0:
         return
-    pops = [0, 32]
-    M = 40
+    import oracle
+    oracle.lib()
+    p = 0
+    q = w["pops"][p]
+    o = oracle.Population(q["L"], q["N"], q["n_clones"], q["seed"])
     steps = []
     for i in range(args.warmup + args.steps):
-        ev, sec = cpu_oracle_sample(w, pops, M)
+        ev0 = o.events
+        t0 = time.perf_counter()
+        o.evolve(w["dt"])
+        o.resample(w["s"][p])
+        sec = time.perf_counter() - t0
         if i >= args.warmup:
-            steps.append((ev, sec))
+            steps.append((o.events - ev0, sec))
     ev = sum(e for e, _ in steps)
     sec = sum(s for _, s in steps)
     value = ev / sec
-    sample = "populations %s of the 64 (N_c=16384 each), first %d of 10000 intervals, per step" % (pops, M)
+    sample = ("population 0 of the 32 (L=128, N_c=2^20), one interval per step (dynamical + cloning "
+              "stage), consecutive intervals of one run; initial state not timed")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * sec / len(steps), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": "s_sweep L=50 N=25 64 biases N_c=16384 dt=0.1 t_obs=1000",
-                   "sample": sample},
+        "config": {"workload": workload_name(w, args.block), "sample": sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# guided against plain cloning at L = 128
+# ---------------------------------------------------------------------------
+def guided_vs_plain(dev, L, lam, dt, M, burn, seeds, nc_list, nc_plain_ref, data_pops, data_nc,
+                    data_burn, data_lag, train_steps, batch, lr, target, seed0=700000):
+    """Train the window potential from plain populations, then psi_hat over `seeds`
+    independent runs of each method (steady state: `burn` intervals dropped).  Each
+    row: mean, spread, device seconds per run, variance x cost, seconds to SE(psi) <=
+    target, and z against plain cloning at the same N_c and against the reference."""
+    from paper_1711_05095_gb300 import potential as pot
+    from paper_1711_05095_gb300.study_guided import run_batch
+    N = L // 2
+    s = lam / L ** 2
+    t0 = time.perf_counter()
+    pops = [dict(L=L, N=N, n_clones=data_nc, seed=900000 + i) for i in range(data_pops)]
+    end, anc = pot.ancestral_samples(pops, [s] * data_pops, dt, data_burn, data_lag, device=dev)
+    t_data = time.perf_counter() - t0
+    cut = data_nc * (data_pops - 1)
+    t0 = time.perf_counter()
+    tr, losses = pot.train(end[:cut], anc[:cut], L, steps=train_steps, batch_size=batch, lr=lr, device=dev)
+    held = pot.classifier_loss(tr, end[cut:], anc[cut:], L, device=dev)
+    phi = tr.potential()
+    tr.close()
+    t_train = time.perf_counter() - t0
+    rows = {}
+    plan = [("plain", n) for n in nc_list] + [("guided", n) for n in nc_list]
+    if nc_plain_ref is not None and nc_plain_ref not in nc_list:
+        plan.append(("plain", nc_plain_ref))
+    for k, (mode, nc) in enumerate(plan):
+        psi, sec, ev = run_batch(L, N, s, dt, M, nc, seeds, seed0 + 1000 * k, mode, phi, burn=burn)
+        sd = float(np.std(psi, ddof=1))
+        per_run = sec / seeds
+        rows["%s_%d" % (mode, nc)] = dict(
+            method=mode, n_clones=nc, psi_mean=float(np.mean(psi)), psi_std=sd, se=sd / math.sqrt(seeds),
+            seconds_per_run=per_run, variance_x_cost=sd * sd * per_run,
+            seconds_to_se=seconds_to_se(sd, per_run, target), clone_events_per_s=ev / sec)
+    for nc in nc_list:
+        g, p = rows["guided_%d" % nc], rows["plain_%d" % nc]
+        g["z_vs_plain_same_nc"] = (g["psi_mean"] - p["psi_mean"]) / math.hypot(g["se"], p["se"])
+        g["seconds_to_se_ratio_vs_plain_same_nc"] = g["seconds_to_se"] / p["seconds_to_se"]
+    if nc_plain_ref is not None:
+        ref = rows["plain_%d" % nc_plain_ref]
+        for r in rows.values():
+            if r is not ref:
+                r["z_vs_plain_reference"] = (r["psi_mean"] - ref["psi_mean"]) / math.hypot(r["se"], ref["se"])
+    best_g = min((r for r in rows.values() if r["method"] == "guided"), key=lambda r: r["seconds_to_se"])
+    best_p = min((r for r in rows.values() if r["method"] == "plain"), key=lambda r: r["seconds_to_se"])
+    return {
+        "workload": "L=%d N=%d lambda=%g dt=%g t_obs=%g after %d intervals dropped, %d seeds per method"
+                    % (L, N, lam, dt, M * dt, burn, seeds),
+        "target_se": target, "rows": rows,
+        "best_guided_over_best_plain_seconds_to_se": best_g["seconds_to_se"] / best_p["seconds_to_se"],
+        "training": {"data": "%d plain populations x %d clones, burn %d and lag %d intervals"
+                             % (data_pops, data_nc, data_burn, data_lag),
+                     "configurations": int(2 * len(end)), "steps": train_steps, "batch": batch,
+                     "heldout_loss": float(held), "chance_loss": float(np.log(2.0)),
+                     "phi_range": [float(phi.min()), float(phi.max())],
+                     "seconds_data": t_data, "seconds_train": t_train},
+    }
+
+
+def config5(args):
+    """The learned-potential workload at full size: the window potential trained on
+    2^22 end / ancestral configurations of L = 128, lambda = 15 populations; guided
+    cloning at N_c in {2^12, 2^14, 2^16} against plain cloning at N_c = 2^20, 32 seeds
+    each, dt = 0.05, t_obs = 2000 (plain at 2^12 .. 2^16 too, for z at equal N_c)."""
+    import torch
+    from paper_1711_05095_gb300 import build as pbuild
+    pbuild.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    out = guided_vs_plain(dev, L=128, lam=15.0, dt=0.05, M=40000, burn=2000, seeds=32,
+                          nc_list=[2 ** 12, 2 ** 14, 2 ** 16], nc_plain_ref=2 ** 20,
+                          data_pops=9, data_nc=2 ** 18, data_burn=20000, data_lag=2000,
+                          train_steps=4000, batch=16384, lr=2e-3, target=1e-3)
+    out["kind"] = "config5 learned guiding potential, full size"
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
 def main():
     args = parse()
-    world, rank, local = dist_setup(args)
-    w = workloads.s_sweep()
-    if args.intervals is not None:
-        w["M"] = int(args.intervals)
-        w["t_obs"] = w["M"] * w["dt"]
+    world, rank, local = dist_setup()
+    if args.config5:
+        return config5(args)
+    w = workloads.large_population()
     if args.impl == "reference":
-        return reference_arm(args, w, world, rank)
+        return reference_arm(args, w, rank)
 
     import torch
     import paper_1711_05095_gb300 as pg
@@ -257,277 +368,230 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     pops = rank_populations(w["pops"], rank)
-    s, dt, M = w["s"], w["dt"], w["M"]
+    s, dt, M, block = w["s"], w["dt"], w["M"], int(args.block)
     P = len(pops)
+    clones = sum(q["n_clones"] for q in pops)
     nbytes = pg.workspace_bytes(pops)
     ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
     flush = torch.empty(512 * 2**20, dtype=torch.uint8, device=dev)   # > 129 MB L2
-
-    def one_step():
-        b = pg.PopulationBatch(pops, device=dev, stream=stream, workspace=ws)
-        b.autotune(dt, s, trials=3)
-        b.run(dt, s, M)
-        psi, kh, t = b.estimate_psi()
-        ev = int(b.events().sum())
-        launches.append(sum(b.launch_count().values()))
-        b.close()
-        return ev, psi
-
-    launches = []
 
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    # one continuing run; a run that has reached M intervals is replaced between steps
+    state = {"b": None, "done": 0, "tuned": None}
+    runs_closed = {"events": 0, "launches": 0}
+
+    def fresh_run():
+        if state["b"] is not None:
+            runs_closed["events"] += int(state["b"].events().sum())
+            runs_closed["launches"] += sum(state["b"].launch_count().values())
+            state["b"].close()
+        b = pg.PopulationBatch(pops, device=dev, stream=stream, workspace=ws)
+        state["tuned"] = b.autotune(dt, s, trials=3)
+        state["b"], state["done"] = b, 0
+
+    def totals():
+        b = state["b"]
+        return (runs_closed["events"] + int(b.events().sum()),
+                runs_closed["launches"] + sum(b.launch_count().values()))
+
+    fresh_run()
     for _ in range(args.warmup):
-        one_step()
-    launches.clear()
-    sampler = ClockSampler(local)
+        if state["done"] + block > M:
+            fresh_run()
+        state["b"].run(dt, s, block)
+        state["done"] += block
     barrier()
+    ev_start, launches_start = totals()
+    sampler = ClockSampler(local)
     sampler.start()
     t_wall0 = time.perf_counter()
-    ev_total, ms = 0, []
+    ms = []
     for _ in range(args.steps):
+        if state["done"] + block > M:
+            fresh_run()
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        ev, psi = one_step()
+        state["b"].run(dt, s, block)
         e1.record(stream)
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
-        ev_total += ev
+        state["done"] += block
     barrier()
     wall = time.perf_counter() - t_wall0
     clocks = sampler.stop()
+    ev_end, launches_end = totals()
+    ev_total = ev_end - ev_start
     t_dev, ev_all = reduce_over_ranks(dist, dev, sum(ms) / 1e3, ev_total)
     value = ev_all / t_dev
+    b = state["b"]
+    psi_run, _, t_run = b.estimate_psi()
+    chains = b.run_chains()
 
-    # end to end through the C ABI with host buffers: initial configurations from
-    # pinned host memory (pop_set_state), the run, estimates back to the host
-    host_lat = []
-    for q in pops:
-        arr = workloads.random_subsets(q["L"], q["N"], q["n_clones"], seed=q["seed"])
-        pinned = torch.empty(arr.shape, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
-        pinned[...] = arr
-        kz = torch.zeros(q["n_clones"], dtype=torch.int32, pin_memory=True).numpy()
-        host_lat.append((pinned, kz))
+    # dominant kernel: the launches pop_run makes for this batch in the tuned
+    # configuration, each between CUDA events recorded by the library on the stream it
+    # launches on (pop_kernel_times), continuing the same run
+    R = args.kernel_intervals
+    torch.cuda.nvtx.range_push("fused_kernel_timing")
+    kt = b.kernel_times(dt, s, R + 1)
+    torch.cuda.nvtx.range_pop()
+    t_k_us, n_k, hops_k = kt["gather_evolve"]
+    t_k = t_k_us / 1e6
+    ops_per_launch = (OPS_HOP * hops_k + (OPS_STOP + OPS_GATHER) * clones * n_k) / n_k
+    peaks, peak_kind = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_gops = n_sm * ISSUE_OPS_PER_SM_CLK * sm_max * 1e6 / 1e9
+    achieved = ops_per_launch / t_k / 1e9
+    ops_run = OPS_HOP * ev_total + (OPS_STOP + OPS_GATHER) * clones * block * args.steps
+    achieved_run = ops_run / (sum(ms) / 1e3) / 1e9
+    per_interval_us = {k: v[0] for k, v in kt.items() if v[1]}
+    counters_valid = KERNEL_TRAFFIC is not None and kernel_sources_digest() == KERNEL_TRAFFIC["sources"]
+
+    # end to end through the C ABI from host memory: a fresh run from pinned host
+    # configurations (pop_set_state: lattices and K), one block of intervals, the
+    # estimates read back (pop_estimate_psi); wall clock, pop_init included
     W = pg.lattice_words(pops)
+    host = workloads.random_subsets(pops[0]["L"], pops[0]["N"], pops[0]["n_clones"], seed=77)
+    lat_pin = torch.empty(host.shape, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+    lat_pin[...] = host
+    k_pin = torch.zeros(pops[0]["n_clones"], dtype=torch.int32, pin_memory=True).numpy()
     h2d = sum(q["n_clones"] * (8 * W + 4) for q in pops)
-    d2h = P * (40 + 8)      # per-population state record and K sum read by pop_estimate_psi
+    d2h = P * (64 + 8)      # per-population state record and K sum read by pop_estimate_psi
+    b.close()
+    state["b"] = None
 
     def e2e_step():
-        b = pg.PopulationBatch(pops, device=dev, stream=stream, workspace=ws)
+        bb = pg.PopulationBatch(pops, device=dev, stream=stream, workspace=ws)
         for p in range(P):
-            b.set_state(p, host_lat[p][0], host_lat[p][1])
-        b.run(dt, s, M)
-        psi, kh, t = b.estimate_psi()
-        ev = int(b.events().sum())
-        b.close()
+            bb.set_state(p, lat_pin, k_pin)
+        bb.run(dt, s, block)
+        bb.estimate_psi()
+        ev = int(bb.events().sum())
+        bb.close()
         return ev
 
     e2e_step()
     barrier()
     e2e_ev, e2e_t = 0, 0.0
-    for _ in range(max(1, min(args.steps, 2))):
-        flush.zero_()
+    n_e2e = max(1, min(args.steps, 2))
+    for _ in range(n_e2e):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         e2e_ev += e2e_step()
         e2e_t += time.perf_counter() - t0
     e2e_t_all, e2e_ev_all = reduce_over_ranks(dist, dev, e2e_t, e2e_ev)
     e2e_value = e2e_ev_all / e2e_t_all
+    del ws
 
-    # dominant kernel: the cloning stage fused with the next dynamical stage
-    # (k_gather<FUSE>), every launch between CUDA events recorded by the library on
-    # the stream it launches on (pop_kernel_times), after 64 warm-up intervals
-    R = args.kernel_intervals
-    b = pg.PopulationBatch(pops, device=dev, stream=stream, workspace=ws)
-    b.run(dt, s, 64)
-    # an NVTX range, so that a profiler can select these whole-batch launches
-    torch.cuda.nvtx.range_push("fused_kernel_timing")
-    kt = b.kernel_times(dt, s, R + 1)
-    torch.cuda.nvtx.range_pop()
-    b.close()
-    t_k_us, n_k, hops_k = kt["gather_evolve"]
-    t_k = t_k_us / 1e6
-    clone_intervals = sum(q["n_clones"] for q in pops)
-
-    # the other batch shapes of the method, bounded runs (device time of `intervals`
-    # intervals through pop_run after 32 warm-up intervals): two-word lattices at
-    # N_c = 2^20 per population, and 256 uneven populations
     others = {}
     if not args.no_others:
-        for name, wl, n_iv in (("large_population", workloads.large_population(), 200),
-                               ("uneven_batch", workloads.uneven_batch(), 200)):
-            b = pg.PopulationBatch(wl["pops"], device=dev, stream=stream)
-            b.run(wl["dt"], wl["s"], 32)
-            ev0 = int(b.events().sum())
+        # the other batch shapes: whole runs (device time, pop_init to the estimates)
+        for name, wl in (("s_sweep", workloads.s_sweep()), ("uneven_batch", workloads.uneven_batch())):
             o0 = torch.cuda.Event(enable_timing=True)
             o1 = torch.cuda.Event(enable_timing=True)
+            flush.zero_()
             o0.record(stream)
-            b.run(wl["dt"], wl["s"], n_iv)
+            bo = pg.PopulationBatch(wl["pops"], device=dev, stream=stream)
+            tuned_o = bo.autotune(wl["dt"], wl["s"], trials=3)
+            bo.run(wl["dt"], wl["s"], wl["M"])
+            bo.estimate_psi()
             o1.record(stream)
             o1.synchronize()
             sec_o = o0.elapsed_time(o1) / 1e3
-            ev_o = int(b.events().sum()) - ev0
-            clones = sum(q["n_clones"] for q in wl["pops"])
+            ev_o = int(bo.events().sum())
+            cl = sum(q["n_clones"] for q in wl["pops"])
+            ch = bo.run_chains()
             others[name] = {"value": ev_o / sec_o, "unit": UNIT, "populations": len(wl["pops"]),
-                            "clones": clones, "intervals_timed": n_iv, "ms_per_interval": 1e3 * sec_o / n_iv,
-                            "workload": wl["pops"][0]["L"] if name == "large_population" else "mixed L"}
-            if name == "large_population":
-                # the separate cloning stage (k_gather) on a working set far above L2:
-                # algorithmic bytes per clone = old lattice 8W + K 4 + dK 4 read, new
-                # lattice 8W + K 4 + ancestor 4 written
-                torch.cuda.nvtx.range_push("gather_timing")
-                kt_g = b.kernel_times(wl["dt"], wl["s"], 8, per_step=True)
-                torch.cuda.nvtx.range_pop()
-                W_g = pg.lattice_words(wl["pops"])
-                bytes_g = clones * (2 * (8 * W_g + 8))
-                t_g = kt_g["gather"][0] / 1e6
-                peaks_g, kind_g = measured_peaks()
-                hbm = float(peaks_g.get("hbm_gbs", 6800.0))
-                t_scan = kt_g["other"][0] / 1e6   # k_tile_scan, launched before each gather
-                others["gather_roofline"] = {
-                    "bound": "hbm", "kernel": "k_gather (separate cloning stage, two-word lattices)",
-                    "achieved": bytes_g / t_g / 1e9, "peak": hbm, "unit": "GB/s",
-                    "frac": bytes_g / t_g / 1e9 / hbm, "bytes_per_launch": bytes_g,
-                    "launch_us": kt_g["gather"][0], "weights_us": kt_g["weights"][0],
-                    "tile_scan_us": kt_g["other"][0],
-                    "frac_with_tile_scan": bytes_g / (t_g + t_scan) / 1e9 / hbm,
-                    "workload": "large_population, 2^25 clones, %d B per clone" % (2 * (8 * W_g + 8)),
-                    "peak_kind": "measured copy bandwidth (%s)" % kind_g}
-            b.close()
-        others["large_population"]["workload"] = ("L=128 N=64 lambda in {5,10,15,20} x 8 seeds, "
-                                                  "N_c=2^20 each, dt=0.05")
+                            "clones": cl, "intervals": wl["M"], "seconds": sec_o,
+                            "chains": len(ch) - 1 if ch else 0, "tuned": tuned_o}
+            bo.close()
+        others["s_sweep"]["workload"] = ("64 populations L=50 N=25 lambda in [-20,40] N_c=16384 dt=0.1 t_obs=1000, "
+                                         "whole run")
         others["uneven_batch"]["workload"] = ("256 populations, L in {32,64,100,128}, N_c in [2^10, 2^18], "
-                                              "lambda in [-10, 30], dt=0.1")
+                                              "lambda in [-10, 30], dt=0.1, t_obs=500, whole run")
+        # the separate cloning stage (k_gather) on the 2^25-clone batch, far above L2:
+        # algorithmic bytes per clone = old lattice 8W + K 4 + dK 4 read, new lattice
+        # 8W + K 4 + ancestor 4 written
+        bg = pg.PopulationBatch(pops, device=dev, stream=stream)
+        bg.run(dt, s, 16)
+        torch.cuda.nvtx.range_push("gather_timing")
+        kt_g = bg.kernel_times(dt, s, 8, per_step=True)
+        torch.cuda.nvtx.range_pop()
+        bg.close()
+        bytes_g = clones * (2 * (8 * W + 8))
+        t_g = kt_g["gather"][0] / 1e6
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        t_scan = kt_g["other"][0] / 1e6   # k_tile_scan, launched before each gather
+        others["gather_roofline"] = {
+            "bound": "hbm", "kernel": "k_gather (separate cloning stage, two-word lattices)",
+            "achieved": bytes_g / t_g / 1e9, "peak": hbm, "unit": "GB/s",
+            "frac": bytes_g / t_g / 1e9 / hbm, "bytes_per_launch": bytes_g,
+            "launch_us": kt_g["gather"][0], "weights_us": kt_g["weights"][0],
+            "tile_scan_us": kt_g["other"][0],
+            "frac_with_tile_scan": bytes_g / (t_g + t_scan) / 1e9 / hbm,
+            "workload": "large_population, 2^25 clones, %d B per clone" % (2 * (8 * W + 8)),
+            "peak_kind": "measured copy bandwidth (%s)" % peak_kind}
 
-    # seconds to SE(psi_hat) <= 1e-3 at lambda = 20 (s = 0.008): 64 independent seeds
-    # of the same population, one batch, full t_obs
-    se_w = workloads.seed_replicas(w["pops"][0], 20.0 / 50**2, 64, seed=500000 + 1000 * rank)
-    se_pops = se_w["pops"]
-    ws_se = torch.empty(pg.workspace_bytes(se_pops), dtype=torch.uint8, device=dev)
-    flush.zero_()
-    s0 = torch.cuda.Event(enable_timing=True)
-    s1 = torch.cuda.Event(enable_timing=True)
-    s0.record(stream)
-    b = pg.PopulationBatch(se_pops, device=dev, stream=stream, workspace=ws_se)
-    b.run(dt, se_w["s"], M)
-    psi_se, _, _ = b.estimate_psi()
-    s1.record(stream)
-    s1.synchronize()
-    b.close()
-    se_batch_s = s0.elapsed_time(s1) / 1e3
-    sigma = float(np.std(psi_se, ddof=1))
-    se_runs, se_seconds = seconds_to_se(sigma, se_batch_s, len(se_pops))
-    del ws_se
-
-    # the same target with GUIDED cloning under a learned window potential: the
-    # potential is trained on the GPU from end / ancestral configurations of plain
-    # runs of this population (4 x 8192 clones, 1000 + 1000 intervals), then 64 seeds
-    # at N_c = 4096 run the full t_obs (training time counted separately)
+    # guided against plain cloning at L = 128, lambda = 15 (a bounded version of the
+    # learned-potential workload; --config5 runs it at full size)
     guided = None
     if not args.no_guided:
-        from paper_1711_05095_gb300 import potential as pot
-        q0 = w["pops"][0]
-        g_s = 20.0 / q0["L"] ** 2
-        t_g0 = time.perf_counter()
-        dpops = [dict(q0, n_clones=8192, seed=600000 + 1000 * rank + i) for i in range(4)]
-        end, anc = pot.ancestral_samples(dpops, [g_s] * 4, dt, 1000, 1000, device=dev)
-        cut = 8192 * 3
-        tr, _ = pot.train(end[:cut], anc[:cut], q0["L"], steps=600, batch_size=8192, lr=2e-3, device=dev)
-        held = pot.classifier_loss(tr, end[cut:], anc[cut:], q0["L"], device=dev)
-        phi = tr.potential()
-        tr.close()
-        t_train = time.perf_counter() - t_g0
-        gpops = [dict(q, n_clones=4096, weight_mode=pg.POP_GUIDED) for q in se_pops]
-        g0 = torch.cuda.Event(enable_timing=True)
-        g1 = torch.cuda.Event(enable_timing=True)
-        flush.zero_()
-        g0.record(stream)
-        b = pg.PopulationBatch(gpops, device=dev, stream=stream)
-        for p_ in range(len(gpops)):
-            b.set_potential(p_, phi)
-        b.run(dt, se_w["s"], M)
-        psi_g, _, _ = b.estimate_psi()
-        g1.record(stream)
-        g1.synchronize()
-        ev_g = int(b.events().sum())
-        b.close()
-        g_batch = g0.elapsed_time(g1) / 1e3
-        sig_g = float(np.std(psi_g, ddof=1))
-        g_runs, g_seconds = seconds_to_se(sig_g, g_batch, len(gpops))
-        se_comb = float(np.hypot(sig_g, sigma) / np.sqrt(len(gpops)))
-        guided = {"value": g_seconds, "unit": "s", "target_se": 1e-3,
-                  "workload": "L=50 N=25 lambda=20 N_c=4096 dt=0.1 t_obs=%g, GUIDED with a learned "
-                              "window potential" % w["t_obs"],
-                  "sigma_per_run": sig_g, "runs_needed": g_runs, "batch_runs": len(gpops),
-                  "batch_seconds": g_batch, "clone_events_per_s": ev_g / g_batch,
-                  "mean_psi": float(np.mean(psi_g)),
-                  "z_vs_plain": (float(np.mean(psi_g)) - float(np.mean(psi_se))) / se_comb,
-                  "classifier_heldout_loss": float(held), "classifier_chance_loss": float(np.log(2.0)),
-                  "training_seconds": t_train}
-    ops_per_launch = (OPS_HOP * hops_k + (OPS_STOP + OPS_GATHER) * clone_intervals * n_k) / n_k
-    counters_valid = kernel_sources_digest() == KERNEL_TRAFFIC["sources"]
-    peaks, peak_kind = measured_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_gops = N_SM * ISSUE_OPS_PER_SM_CLK * sm_max * 1e6 / 1e9
-    achieved = ops_per_launch / t_k / 1e9
-    # the same operation count over this rank's timed steps, whose time also holds the
-    # other kernels of each interval and, with pop_run's two chains, their overlap
-    ops_run = OPS_HOP * ev_total + (OPS_STOP + OPS_GATHER) * clone_intervals * M * args.steps
-    achieved_run = ops_run / (sum(ms) / 1e3) / 1e9
+        guided = guided_vs_plain(dev, L=128, lam=15.0, dt=0.05, M=4000, burn=1000, seeds=32,
+                                 nc_list=[2 ** 14], nc_plain_ref=None, data_pops=4, data_nc=2 ** 16,
+                                 data_burn=2000, data_lag=400, train_steps=600, batch=8192, lr=2e-3,
+                                 target=1e-4)
+        guided["bounded"] = ("t_obs 200 (config: 2000), one N_c (2^14) per method, 2^19 training "
+                             "configurations (config: 2^22); full size: bench.py --config5")
 
+    n_chains = len(chains) - 1 if chains else 1
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": "s_sweep L=50 N=25 64 biases lambda in [-20,40] N_c=16384 each "
-                               "dt=0.1 t_obs=%g (M=%d)" % (w["t_obs"], M),
-                   "populations": P, "clones": clone_intervals, "intervals": M,
-                   "l2": "flushed (512 MB write) between timed steps",
-                   "parallelism": "replicas%d" % world},
-        "gpu_launches": int(sum(launches)),
+        "config": {"workload": workload_name(w, block),
+                   "populations": P, "clones": clones, "intervals_per_step": block,
+                   "l2": "inputs larger than L2 (2 GB of clone state) and a 512 MB write between steps",
+                   "parallelism": "replicas%d" % world, "chains": n_chains, "tuned": state["tuned"]},
+        "gpu_launches": int(launches_end - launches_start),
         "roofline": {"bound": "alu", "kernel": "k_gather<fused> (cloning stage + next dynamical stage)",
-                     "achieved": achieved, "peak": peak_gops,
-                     "unit": "Gop/s", "frac": achieved / peak_gops,
+                     "achieved": achieved, "peak": peak_gops, "unit": "Gop/s", "frac": achieved / peak_gops,
                      "traffic": KERNEL_TRAFFIC["bytes"] if counters_valid else None,
                      "ncu": ({k: KERNEL_TRAFFIC[k] for k in ("issue_slots_busy", "alu_pipe", "lanes_per_instruction")}
                              if counters_valid else None),
-                     "peak_kind": "issue rate 152 SM x 128 lanes x %.0f MHz (%s max clock)"
-                                  % (sm_max, peak_kind),
-                     "launch_us": t_k_us, "launches_timed": n_k,
-                     "other_kernels_us": {k: v[0] for k, v in kt.items() if k != "gather_evolve" and v[1]},
-                     "ops_per_launch": ops_per_launch,
-                     "launches_from": "pop_kernel_times: whole-batch launches, one chain",
+                     "peak_kind": "issue rate %d SM x 128 lanes x %.0f MHz (%s max clock)"
+                                  % (n_sm, sm_max, peak_kind),
+                     "launch_us": t_k_us, "launches_timed": n_k, "ops_per_launch": ops_per_launch,
+                     "per_interval_us": per_interval_us,
+                     "launches_from": "pop_kernel_times: the launch sequence of pop_run for this batch "
+                                      "(%d chain%s), continuing the timed run" % (n_chains, "s" if n_chains > 1 else ""),
+                     "dominant_ms_per_step": t_k_us * block / 1e3,
                      "achieved_in_run": achieved_run, "frac_in_run": achieved_run / peak_gops},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "seconds_to_se": {"value": se_seconds, "unit": "s", "target_se": 1e-3,
-                          "workload": "L=50 N=25 lambda=20 N_c=16384 dt=0.1 t_obs=%g" % w["t_obs"],
-                          "sigma_per_run": sigma, "runs_needed": se_runs,
-                          "batch_runs": len(se_pops), "batch_seconds": se_batch_s,
-                          "mean_psi": float(np.mean(psi_se)), "method": "plain cloning"},
-        "seconds_to_se_guided": guided,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "step": "pop_init + pop_set_state of every population from pinned host memory + %d intervals "
+                        "+ pop_estimate_psi (wall clock; the 32 populations start from the same host "
+                        "configurations)" % block},
+        "guided_vs_plain_L128": guided,
         "clocks": clocks,
         "wall_s_timed": wall,
-        # the same steps counted in clone-intervals (one clone through one interval)
-        "clone_intervals_per_s": clone_intervals * M * args.steps * world / t_dev,
-        "psi_check": {"lambda=-20": float(psi[0]), "lambda=40": float(psi[-1])},
+        "clone_intervals_per_s": clones * block * args.steps * world / t_dev,
+        "psi_check": {"lambda=5": float(psi_run[0]), "lambda=20": float(psi_run[-1]), "t_obs": t_run},
         "other_workloads": others,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        idx = list(range(0, 64, 8))
-        ev_c, sec_c = cpu_oracle_sample(w, idx, 40)
+        idx = [0, 8, 16, 24]
+        ev_c, sec_c = cpu_oracle_intervals(w, idx, 2)
         line["cpu_baseline"] = {"value": ev_c / sec_c, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": "populations %s (N_c=16384 each), first 40 of the "
-                                          "10000 intervals; %.1f s" % (idx, sec_c)}
-        # the same oracle on every host core: one process per population (the
-        # populations are independent, as the paper's OpenMP design splits clones)
+                                "sample": "populations %s (L=128, N_c=2^20 each), the first 2 intervals after "
+                                          "an untimed initial state; %.1f s" % (idx, sec_c)}
         ncores = os.cpu_count() or 1
-        idx_all = list(range(min(64, ncores)))
-        line["cpu_baseline_all_cores"] = cpu_oracle_parallel(w, idx_all, 40)
+        idx_all = list(range(min(32, ncores)))
+        line["cpu_baseline_all_cores"] = cpu_oracle_parallel(w, idx_all, 2)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -52,5 +52,9 @@ def test_two_cpu_ranks():
 
 
 def test_seconds_to_se():
-    runs, sec = bench.seconds_to_se(sigma=0.004, batch_seconds=2.0, batch_runs=64)
-    assert runs == 16 and sec == pytest.approx(0.5)
+    # SE = sigma / sqrt(R) reaches the target after R = (sigma / target)^2 runs of
+    # this cost: 16 runs of 2/64 s each
+    assert bench.seconds_to_se(sigma=0.004, seconds_per_run=2.0 / 64, target=1e-3) == pytest.approx(0.5)
+    # below one run's spread the time is a fraction of a run (the same SE from a run
+    # that much shorter), not rounded up
+    assert bench.seconds_to_se(sigma=5e-4, seconds_per_run=1.0, target=1e-3) == pytest.approx(0.25)

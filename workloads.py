@@ -66,15 +66,13 @@ def seed_replicas(pop, s, n_runs, seed, dt=0.1, t_obs=1000.0):
 
 def random_subsets(L, N, n_clones, seed):
     """Host-side uniform N-subsets packed as uint64 words (n_clones, ceil(L/64)):
-    initial configurations supplied from host memory (pop_set_state)."""
+    initial configurations supplied from host memory (pop_set_state).  Each row is an
+    independent uniform shuffle of N ones and L - N zeros; site i is bit (i mod 64) of
+    word (i div 64)."""
     g = np.random.default_rng(seed)
     W = (L + 63) // 64
-    words = np.zeros((n_clones, W), dtype=np.uint64)
-    keys = g.random((n_clones, L))
-    occ = np.argsort(keys, axis=1)[:, :N]
-    for q in range(W):
-        sel = (occ >= 64 * q) & (occ < 64 * (q + 1))
-        bits = np.where(sel, np.left_shift(np.uint64(1), (occ - 64 * q).clip(0, 63).astype(np.uint64)),
-                        np.uint64(0))
-        words[:, q] = np.bitwise_or.reduce(bits, axis=1) if N > 0 else 0
-    return words
+    rows = np.zeros((n_clones, 64 * W), dtype=np.uint8)
+    rows[:, :N] = 1
+    rows[:, :L] = g.permuted(rows[:, :L], axis=1)
+    packed = np.packbits(rows, axis=1, bitorder="little")          # 8 W bytes per row
+    return np.ascontiguousarray(packed).view("<u8").reshape(n_clones, W).astype(np.uint64)
