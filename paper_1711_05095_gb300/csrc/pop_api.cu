@@ -37,6 +37,11 @@ using namespace popgpu;
 #define POP_RUN_CHAINS_LARGE 2
 #endif
 constexpr int kMaxChains = 8;
+// clones each lane of the fused kernel advances together (1 or 2)
+#ifndef POP_FUSE_CLONES
+#define POP_FUSE_CLONES 1
+#endif
+constexpr int kFuseClones = POP_FUSE_CLONES;
 static_assert(POP_RUN_CHAINS >= 1 && POP_RUN_CHAINS <= kMaxChains &&
               POP_RUN_CHAINS_LARGE >= 1 && POP_RUN_CHAINS_LARGE <= kMaxChains, "1 to 8 chains");
 
@@ -326,10 +331,15 @@ void launch_tile_scan(pop_t* h, cudaStream_t st, const Batch& Bx, int pop0, int 
   kernel_end(h, st);
 }
 
-void launch_weights(pop_t* h, cudaStream_t st) {
+// k_weights over the tiles [tile0, tile0 + ntiles), one block per tile
+void launch_weights_range(pop_t* h, cudaStream_t st, const Batch& Bx, int tile0, int ntiles) {
   kernel_begin(h, st, POP_K_WEIGHTS);
-  k_weights<<<(unsigned)h->lay.ntiles, kThreads, 0, st>>>(h->B, 0);
+  k_weights<<<(unsigned)ntiles, kThreads, 0, st>>>(Bx, tile0);
   kernel_end(h, st);
+}
+
+void launch_weights(pop_t* h, cudaStream_t st) {
+  launch_weights_range(h, st, h->B, 0, h->lay.ntiles);
   launch_tile_scan(h, st, h->B, 0, h->lay.P);
 }
 
@@ -374,9 +384,7 @@ bool fusable(const pop_t* h) {
 int launch_resample_evolve_range(pop_t* h, cudaStream_t st, float dt_f, const Batch& Bx,
                                  int tile0, int ntiles, int pop0, int pop1) {
   const unsigned grid = (unsigned)ntiles;
-  kernel_begin(h, st, POP_K_WEIGHTS);
-  k_weights<<<grid, kThreads, 0, st>>>(Bx, tile0);
-  kernel_end(h, st);
+  launch_weights_range(h, st, Bx, tile0, ntiles);
   // the tile prefixes from k_tile_scan when every population here has many tiles; a
   // population of a few tiles is cheaper to sum inside the fused kernel than to scan in
   // one more launch per interval
@@ -387,19 +395,19 @@ int launch_resample_evolve_range(pop_t* h, cudaStream_t st, float dt_f, const Ba
   kernel_begin(h, st, POP_K_GATHER_EVOLVE);
   if (h->lay.W == 1) {
     if (h->any_mod) {
-      if (scan) k_gather<1, GT, true, true, true><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
-      else k_gather<1, GT, true, true, false><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
+      if (scan) k_gather<1, GT, true, true, true, kFuseClones><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
+      else k_gather<1, GT, true, true, false, kFuseClones><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
     } else {
-      if (scan) k_gather<1, GT, true, false, true><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
-      else k_gather<1, GT, true, false, false><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
+      if (scan) k_gather<1, GT, true, false, true, kFuseClones><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
+      else k_gather<1, GT, true, false, false, kFuseClones><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
     }
   } else {
     if (h->any_mod) {
-      if (scan) k_gather<2, GT, true, true, true><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
-      else k_gather<2, GT, true, true, false><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
+      if (scan) k_gather<2, GT, true, true, true, kFuseClones><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
+      else k_gather<2, GT, true, true, false, kFuseClones><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
     } else {
-      if (scan) k_gather<2, GT, true, false, true><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
-      else k_gather<2, GT, true, false, false><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
+      if (scan) k_gather<2, GT, true, false, true, kFuseClones><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
+      else k_gather<2, GT, true, false, false, kFuseClones><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
     }
   }
   kernel_end(h, st);
@@ -422,10 +430,10 @@ int size_chains(pop_t* h) {
   if (!fusable(h)) return POP_OK;
   constexpr int GT = POP_FUSE_THREADS;
   const void* f = h->lay.W == 1
-                      ? (h->any_mod ? (const void*)k_gather<1, GT, true, true, false>
-                                    : (const void*)k_gather<1, GT, true, false, false>)
-                      : (h->any_mod ? (const void*)k_gather<2, GT, true, true, false>
-                                    : (const void*)k_gather<2, GT, true, false, false>);
+                      ? (h->any_mod ? (const void*)k_gather<1, GT, true, true, false, kFuseClones>
+                                    : (const void*)k_gather<1, GT, true, false, false, kFuseClones>)
+                      : (h->any_mod ? (const void*)k_gather<2, GT, true, true, false, kFuseClones>
+                                    : (const void*)k_gather<2, GT, true, false, false, kFuseClones>);
   int per_sm = 0, sms = 0;
   POP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, GT, 0));
   POP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));

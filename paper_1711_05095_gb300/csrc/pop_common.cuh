@@ -149,6 +149,22 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
+// The same generator with the key schedule given: rk[r] = (k0 + r 0x9E3779B9,
+// k1 + r 0xBB67AE85) mod 2^32, the key of round r.  A block whose clones share one
+// key (one population per tile) computes the schedule once instead of per draw.
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint2* rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint2 k = rk[r];
+    const uint32_t lo0 = c.x * 0xD2511F53u;
+    const uint32_t hi0 = __umulhi(c.x, 0xD2511F53u);
+    const uint32_t lo1 = c.z * 0xCD9E8D57u;
+    const uint32_t hi1 = __umulhi(c.z, 0xCD9E8D57u);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
 // ---------------------------------------------------------------------------
 // E = -ln(u), u = (2w+1)/2^33, in FP32 with a fixed sequence of operations:
 // v = 2w+1 truncated to its 24 leading bits, v' = m 2^p with m in [1, 2) and p the

@@ -109,6 +109,37 @@ __device__ __forceinline__ bool bkl_step(unsigned long long (&x)[W], float& t, f
   return true;
 }
 
+// The same step without branches, for a clone that is `live` (else nothing changes):
+// the rate, waiting time and bond are computed in any case and applied under the
+// step's predicate, so the lanes of a warp stay together and two steps of different
+// clones can be interleaved.  r = 0 or t_new >= dt ends the interval as in bkl_step
+// (MOD: the last segment r (dt - t) is added when r > 0; for r = 0 it adds nothing).
+template <int W, bool MOD>
+__device__ __forceinline__ bool bkl_step_pred(unsigned long long (&x)[W], float& t, float& acc, int L,
+                                              const float* inv, float E, uint32_t wb, float dt_f,
+                                              bool live) {
+  unsigned long long a[W];
+  active_bonds<W>(x, L, a);
+  const int r = popc_lat<W>(a);
+  const float tau = __fmul_rn(E, inv[r]);
+  const float t_new = __fadd_rn(t, tau);
+  const bool moving = live && r != 0;
+  const bool hopped = moving && t_new < dt_f;
+  if (MOD) {
+    const float seg = hopped ? tau : __fsub_rn(dt_f, t);
+    acc = moving ? __fmaf_rn((float)r, seg, acc) : acc;
+  }
+  t = hopped ? t_new : t;
+  const int b = kth_bond<W>(a, __umulhi(wb, (uint32_t)r));
+  unsigned long long y[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) y[w] = x[w];
+  hop<W>(y, b, L);
+#pragma unroll
+  for (int w = 0; w < W; ++w) x[w] = hopped ? y[w] : x[w];
+  return hopped;
+}
+
 // ---------------------------------------------------------------------------
 // Dynamical stage.  A persistent grid; each block stages an equal share of the
 // clones in shared memory.  Every lane holds one clone in registers and advances
@@ -449,27 +480,43 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(Batch B, int pop0) {
 #ifndef POP_FUSE_MIN_BLOCKS
 #define POP_FUSE_MIN_BLOCKS 8  // 64 registers, no spills; pop_run's chains keep more than one launch resident
 #endif
+#ifndef POP_FUSE2_MIN_BLOCKS
+#define POP_FUSE2_MIN_BLOCKS 6  // two clones per lane: up to 80 registers
+#endif
 // SCAN: the population totals and tile prefixes come from k_tile_scan; otherwise each
 // block sums its population's tile sums (cheaper for a few tiles per population, but
 // the extra path costs registers and scheduling when compiled into the same kernel).
-template <int W, int NT, bool FUSE = false, bool MOD = false, bool SCAN = true>
-__global__ void __launch_bounds__(NT, FUSE ? POP_FUSE_MIN_BLOCKS : (NT == 128 ? 11 : (NT == 256 ? 6 : 3)))
+// NCL (FUSE only): clones each lane advances together in the dynamical stage, 1 or 2
+// (two independent Philox and bit-select chains in flight per lane).
+template <int W, int NT, bool FUSE = false, bool MOD = false, bool SCAN = true, int NCL = 1>
+__global__ void __launch_bounds__(NT, FUSE ? (NCL == 1 ? POP_FUSE_MIN_BLOCKS : POP_FUSE2_MIN_BLOCKS)
+                                           : (NT == 128 ? 11 : (NT == 256 ? 6 : 3)))
     k_gather(Batch B, float dt_f, int tile0) {
   constexpr int NI = kTile / NT;   // old clones per thread
   constexpr int NWARP = NT / 32;
   constexpr int WS = W > 0 ? W : 1;  // W == 0: wide lattices, copied without staging
   static_assert(!FUSE || W > 0, "the fused stage needs staged lattices");
   static_assert(NI % 4 == 0 && NI * NT == kTile, "whole int4 loads of activities per thread");
+  static_assert(NCL == 1 || NCL == 2, "one or two clones per lane");
   __shared__ unsigned long long s_x[W > 0 ? kTile : 1][WS];
-  __shared__ int32_t s_K[kTile];
-  __shared__ uint32_t s_jlo[kTile + 1];
-  __shared__ uint16_t s_src[kMap];
+  // the old clones' cumulative activities (the fused stage reads each new clone's from
+  // global memory when the clone is taken, keeping shared memory for more blocks)
+  __shared__ int32_t s_K[FUSE ? 1 : kTile];
+  // the new slots of the tile's old clones: the map from new slot to old clone
+  // (uint16, kMap entries) or, when one old clone has more copies than the map holds,
+  // the ranges j_lo (uint32, kTile + 1 entries) searched instead; one buffer
+  static_assert(kMap * sizeof(uint16_t) <= (kTile + 1) * sizeof(uint32_t), "map fits the range buffer");
+  __shared__ __align__(16) uint32_t s_rng[kTile + 1];
+  uint32_t* const s_jlo = s_rng;
+  uint16_t* const s_src = reinterpret_cast<uint16_t*>(s_rng);
+  __shared__ uint32_t s_J[2];
   __shared__ unsigned long long s_red[SCAN ? 1 : NWARP];
   __shared__ unsigned long long s_wsum[NWARP];
-  // FUSE only: the population's waiting-time factors, the log table, the slot
-  // counter and the block's activity range of the next interval
+  // FUSE only: the population's waiting-time factors, the log table, the Philox key
+  // schedule, the slot counter and the block's activity range of the next interval
   __shared__ float s_inv[FUSE ? kMaxL + 1 : 1];
   __shared__ float2 s_logtab[FUSE ? 64 : 1];
+  __shared__ uint2 s_keys[FUSE ? 10 : 1];
   __shared__ int s_take;
   __shared__ int s_nmin, s_nmax, s_namin, s_namax;
   __shared__ unsigned int s_nev;
@@ -492,6 +539,9 @@ __global__ void __launch_bounds__(NT, FUSE ? POP_FUSE_MIN_BLOCKS : (NT == 128 ? 
     const float* src = B.inv_rate + (size_t)p * kInvStride;
     for (int r = tid; r <= kMaxL; r += NT) s_inv[r] = (r <= d.L) ? src[r] : 0.0f;
     if (tid < 64) s_logtab[tid] = B.logtab[tid];
+    if (tid < 10)
+      s_keys[tid] = make_uint2((uint32_t)d.seed + (uint32_t)tid * 0x9E3779B9u,
+                               (uint32_t)(d.seed >> 32) + (uint32_t)tid * 0xBB67AE85u);
     if (tid == 0) {
       s_take = 0;
       s_nmin = INT_MAX;
@@ -519,7 +569,7 @@ __global__ void __launch_bounds__(NT, FUSE ? POP_FUSE_MIN_BLOCKS : (NT == 128 ? 
 #pragma unroll
         for (int q = 0; q < W; ++q) s_x[i][q] = x[q];
       }
-      s_K[i] = KXo[base + i];
+      if constexpr (!FUSE) s_K[i] = KXo[base + i];
     }
   }
   float av[NI];
@@ -591,21 +641,23 @@ __global__ void __launch_bounds__(NT, FUSE ? POP_FUSE_MIN_BLOCKS : (NT == 128 ? 
   } else {
   uint32_t jl[NI + 1];
   j_lo_run<NI>(run, w, T, c, nc, sh, ratio, jl);
-#pragma unroll
-  for (int i = 0; i < NI; ++i) s_jlo[tid * NI + i] = jl[i];
-  if (tid == NT - 1) s_jlo[kTile] = jl[NI];
+  if (tid == 0) s_J[0] = jl[0];
+  if (tid == NT - 1) s_J[1] = jl[NI];
   __syncthreads();
 
-  const uint32_t J0 = s_jlo[0], J1 = s_jlo[kTile];
+  const uint32_t J0 = s_J[0], J1 = s_J[1];
   const bool mapped = (J1 - J0) <= (uint32_t)kMap;
   if (mapped) {
+    // the thread's old clones own the new slots [jl[0], jl[NI]), held in its registers
 #pragma unroll
-    for (int i = 0; i < NI; ++i) {
-      const int k = tid * NI + i;
-      for (uint32_t jj = s_jlo[k]; jj < s_jlo[k + 1]; ++jj) s_src[jj - J0] = (uint16_t)k;
-    }
-    __syncthreads();
+    for (int i = 0; i < NI; ++i)
+      for (uint32_t jj = jl[i]; jj < jl[i + 1]; ++jj) s_src[jj - J0] = (uint16_t)(tid * NI + i);
+  } else {
+#pragma unroll
+    for (int i = 0; i < NI; ++i) s_jlo[tid * NI + i] = jl[i];
+    if (tid == NT - 1) s_jlo[kTile] = jl[NI];
   }
+  __syncthreads();
   auto source = [&](uint32_t jj) -> int {
     if (mapped) return s_src[jj - J0];
     int lo = 0, hi = kTile - 1;  // one old clone with very many copies: search j_lo
@@ -616,7 +668,11 @@ __global__ void __launch_bounds__(NT, FUSE ? POP_FUSE_MIN_BLOCKS : (NT == 128 ? 
     return lo;
   };
   if constexpr (FUSE) {
-    // dynamical stage of interval beta + 1 for the new slots [J0, J1)
+    // dynamical stage of interval beta + 1 for the new slots [J0, J1): each lane holds
+    // NCL clones; an empty clone slot takes the next new slot of the tile from the
+    // shared counter (all of a warp's empty slots in one atomic), so lanes stay busy
+    // until the tile's slots run out.  Every live clone takes one Philox draw (its next
+    // two BKL steps) per iteration; the steps are predicated, without branches.
     const uint32_t beta1 = beta + 1u;
     const int pn = par ^ 1;
     unsigned long long* const Xn = B.Xb[pn];
@@ -625,77 +681,102 @@ __global__ void __launch_bounds__(NT, FUSE ? POP_FUSE_MIN_BLOCKS : (NT == 128 ? 
     float* const An = B.Ab[pn];
     const int n = (int)(J1 - J0);
     const int L = d.L;
-    const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
-    int c = -1, src_k = 0;  // the lane's new slot (offset from J0) and its ancestor
-    unsigned long long x[W];
-    float t = 0.0f, acc = 0.0f;
-    int h = 0;
-    uint32_t q = 0u;
+    const unsigned int lt_mask = (1u << lane) - 1u;
+    int cl[NCL], h[NCL];              // the slot's new clone (offset from J0, -1: empty)
+    int kold[NCL];                    // its ancestor's cumulative activity
+    uint32_t q[NCL];
+    float t[NCL], acc[NCL];
+    unsigned long long x[NCL][W];
     int hmin = INT_MAX, hmax = INT_MIN, amin = INT_MAX, amax = INT_MIN;
     unsigned int ev = 0u;
 #pragma unroll
-    for (int w = 0; w < W; ++w) x[w] = 0ull;
+    for (int k = 0; k < NCL; ++k) {
+      cl[k] = -1;
+      kold[k] = 0;
+      h[k] = 0;
+      q[k] = 0u;
+      t[k] = 0.0f;
+      acc[k] = 0.0f;
+#pragma unroll
+      for (int w = 0; w < W; ++w) x[k][w] = 0ull;
+    }
     for (;;) {
+      unsigned int m[NCL];
+      int tot = 0;
+#pragma unroll
+      for (int k = 0; k < NCL; ++k) {
+        m[k] = __ballot_sync(0xffffffffu, cl[k] < 0);
+        tot += __popc(m[k]);
+      }
       // one read of the counter per warp keeps every branch below warp-uniform
       int taken = 0;
       if (lane == 0) taken = *(volatile int*)&s_take;
       taken = __shfl_sync(0xffffffffu, taken, 0);
-      const bool need = c < 0;
-      const unsigned int m = __ballot_sync(0xffffffffu, need);
-      if (m != 0u && taken < n) {
-        const int leader = __ffs(m) - 1;
+      if (tot != 0 && taken < n) {
         int base_i = 0;
-        if (lane == leader) base_i = atomicAdd(&s_take, __popc(m));
-        base_i = __shfl_sync(0xffffffffu, base_i, leader);
-        if (need) {
-          const int idx = base_i + __popc(m & ((1u << lane) - 1u));
-          if (idx < n) {
-            c = idx;
-            src_k = source(J0 + (uint32_t)idx);
+        if (lane == 0) base_i = atomicAdd(&s_take, tot);
+        base_i = __shfl_sync(0xffffffffu, base_i, 0);
 #pragma unroll
-            for (int w = 0; w < W; ++w) x[w] = s_x[src_k][w];
-            t = 0.0f;
-            acc = 0.0f;
-            h = 0;
-            q = 0u;
+        for (int k = 0; k < NCL; ++k) {
+          const int idx = base_i + __popc(m[k] & lt_mask);
+          if (cl[k] < 0 && idx < n) {
+            cl[k] = idx;
+            const int sk = source(J0 + (uint32_t)idx);
+            kold[k] = KXo[base + sk];
+#pragma unroll
+            for (int w = 0; w < W; ++w) x[k][w] = s_x[sk][w];
+            t[k] = 0.0f;
+            acc[k] = 0.0f;
+            h[k] = 0;
+            q[k] = 0u;
           }
+          base_i += __popc(m[k]);
         }
       }
-      if (__ballot_sync(0xffffffffu, c >= 0) == 0u) {
+      bool any = false;
+#pragma unroll
+      for (int k = 0; k < NCL; ++k) any = any || cl[k] >= 0;
+      if (__ballot_sync(0xffffffffu, any) == 0u) {
         if (lane == 0) taken = *(volatile int*)&s_take;
         if (__shfl_sync(0xffffffffu, taken, 0) >= n) break;
+        continue;
       }
-      if (c >= 0) {
-        const uint32_t jj = J0 + (uint32_t)c;
-        const uint4 d4 = philox4x32_10(make_uint4(q, beta1, jj, kTagEvolve), k0, k1);
-        const float E1 = neg_ln_u(d4.x, s_logtab), E2 = neg_ln_u(d4.z, s_logtab);
-        bool run = false;
-        if (bkl_step<W, MOD>(x, t, acc, L, s_inv, E1, d4.y, dt_f)) {
-          ++h;
-          if (bkl_step<W, MOD>(x, t, acc, L, s_inv, E2, d4.w, dt_f)) {
-            ++h;
-            run = true;
-          }
-        }
-        ++q;
-        if (run && q >= kStepLimit / 2u) {  // guard: an interval must end; report, never spin
+      uint4 d4[NCL];
+      float E1[NCL], E2[NCL];
+#pragma unroll
+      for (int k = 0; k < NCL; ++k)
+        d4[k] = philox4x32_10_rk(make_uint4(q[k], beta1, J0 + (uint32_t)cl[k], kTagEvolve), s_keys);
+#pragma unroll
+      for (int k = 0; k < NCL; ++k) {
+        E1[k] = neg_ln_u(d4[k].x, s_logtab);
+        E2[k] = neg_ln_u(d4[k].z, s_logtab);
+      }
+#pragma unroll
+      for (int k = 0; k < NCL; ++k) {
+        const bool live = cl[k] >= 0;
+        const bool h1 = bkl_step_pred<W, MOD>(x[k], t[k], acc[k], L, s_inv, E1[k], d4[k].y, dt_f, live);
+        const bool h2 = bkl_step_pred<W, MOD>(x[k], t[k], acc[k], L, s_inv, E2[k], d4[k].w, dt_f, h1);
+        h[k] += (int)h1 + (int)h2;
+        ++q[k];
+        bool run = h2;
+        if (run && q[k] >= kStepLimit / 2u) {  // guard: an interval must end; report, never spin
           st->err = kErrRange;
           run = false;
         }
-        if (!run) {
-          const int64_t dst = d.off + (int64_t)jj;
-          store_lat<W>(Xn, dst, x);
-          KXn[dst] = s_K[src_k] + h;
-          dKn[dst] = h;
+        if (live && !run) {
+          const int64_t dst = d.off + (int64_t)J0 + cl[k];
+          store_lat<W>(Xn, dst, x[k]);
+          KXn[dst] = kold[k] + h[k];
+          dKn[dst] = h[k];
           if (MOD) {
-            An[dst] = acc;
-            amin = min(amin, __float_as_int(acc));  // A >= 0: float bits order like values
-            amax = max(amax, __float_as_int(acc));
+            An[dst] = acc[k];
+            amin = min(amin, __float_as_int(acc[k]));  // A >= 0: float bits order like values
+            amax = max(amax, __float_as_int(acc[k]));
           }
-          hmin = min(hmin, h);
-          hmax = max(hmax, h);
-          ev += (unsigned int)h;
-          c = -1;
+          hmin = min(hmin, h[k]);
+          hmax = max(hmax, h[k]);
+          ev += (unsigned int)h[k];
+          cl[k] = -1;
         }
       }
     }
