@@ -436,13 +436,15 @@ def main():
     # dominant kernel: the launches pop_run makes for this batch in the tuned
     # configuration, each between CUDA events recorded by the library on the stream it
     # launches on (pop_kernel_times), continuing the same run
+    # (with several chains an interval's fused launches run side by side: the time is
+    # their span per interval, and the operations those of the whole interval)
     R = args.kernel_intervals
     torch.cuda.nvtx.range_push("fused_kernel_timing")
     kt = b.kernel_times(dt, s, R + 1)
     torch.cuda.nvtx.range_pop()
     t_k_us, n_k, hops_k = kt["gather_evolve"]
     t_k = t_k_us / 1e6
-    ops_per_launch = (OPS_HOP * hops_k + (OPS_STOP + OPS_GATHER) * clones * n_k) / n_k
+    ops_per_launch = OPS_HOP * hops_k / R + (OPS_STOP + OPS_GATHER) * clones
     peaks, peak_kind = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -566,7 +568,8 @@ def main():
                              if counters_valid else None),
                      "peak_kind": "issue rate %d SM x 128 lanes x %.0f MHz (%s max clock)"
                                   % (n_sm, sm_max, peak_kind),
-                     "launch_us": t_k_us, "launches_timed": n_k, "ops_per_launch": ops_per_launch,
+                     "launch_us": t_k_us, "launches_timed": n_k, "intervals_timed": R,
+                     "launches_per_interval": n_k / R, "ops_per_launch": ops_per_launch,
                      "per_interval_us": per_interval_us,
                      "launches_from": "pop_kernel_times: the launch sequence of pop_run for this batch "
                                       "(%d chain%s), continuing the timed run" % (n_chains, "s" if n_chains > 1 else ""),

@@ -179,15 +179,53 @@ int pop_copy_state(pop_t* pop, int32_t p, uint64_t* h_lattice, int32_t* h_K,
                    int32_t* h_anc, int32_t* h_dK);
 
 /*
- * Launch-configuration tuning for this batch (the paper has none: its codes had
- * fixed thread counts).  Times `trials` launches of the dynamical stage of the first
- * interval for every candidate persistent grid (1 .. the maximum number of
- * resident blocks per SM, times the SM count) and keeps the fastest; the counters
- * and activities are restored, so results are identical with and without tuning.
- * Before the first interval only (else POP_ERR_STATE); fixes s like pop_evolve.
- * h_evolve_grid (may be NULL) receives the chosen grid.  Waits for the stream.
+ * Launch configuration of a batch (the paper has none: its codes had fixed thread
+ * counts).  Every choice changes only speed, never a result:
+ *   evolve_grid     persistent grid of the separate dynamical stage (the first interval
+ *                   of a fused run; every interval of a batch that does not fuse)
+ *   fuse_threads    threads per block of the fused cloning + dynamical stage: 128 or 256
+ *   fuse_clones     clones each lane of the fused stage advances together: 1 or 2
+ *                   (2 only with 128 threads)
+ *   chains          chains of pop_run (1 .. 8; the split actually used may have fewer,
+ *                   see pop_run_chains)
+ *   gather_threads  threads per block of the separate cloning stage: 128, 256, or 0 for
+ *                   the rule (256 above 4096 tiles)
+ *   default_us_per_interval, tuned_us_per_interval: the times per interval pop_autotune
+ *                   measured for the configuration pop_init chose and for its choice
+ *                   (0 until it has run; ignored by pop_set_tuning)
+ */
+typedef struct pop_tuning {
+  int32_t evolve_grid;
+  int32_t fuse_threads;
+  int32_t fuse_clones;
+  int32_t chains;
+  int32_t gather_threads;
+  float default_us_per_interval;
+  float tuned_us_per_interval;
+} pop_tuning;
+
+/*
+ * Choose the launch configuration by timing on this batch's own shape.  Times `trials`
+ * launches of the dynamical stage of the first interval for every candidate persistent
+ * grid (1 .. the resident blocks per SM, times the SM count); for a batch that fuses,
+ * three replays of `trials` fused intervals captured as a CUDA graph (as pop_run runs
+ * them) for each fused-kernel form (128 threads with one or two clones per lane, 256
+ * threads with one) and each chain split (up to 1, 2, 4, 8); for a
+ * batch that does not, `trials` whole intervals for each block size of the separate
+ * cloning stage.  Keeps the fastest of each.  Every trial starts again from interval 1
+ * and the counters, activities and (for the cloning-stage trials) the population are
+ * put back, so results are identical with and without tuning.  Before the first interval
+ * only (else POP_ERR_STATE); fixes s like pop_evolve.  h_evolve_grid (may be NULL)
+ * receives the chosen grid; pop_get_tuning gives the whole choice.  Waits for the stream.
  */
 int pop_autotune(pop_t* pop, double dt, const double* s, int32_t trials, int32_t* h_evolve_grid);
+
+/* The current launch configuration (host struct). */
+int pop_get_tuning(pop_t* pop, pop_tuning* out);
+
+/* Set the launch configuration (values outside the ranges above: POP_ERR_ARG; between
+ * pop_evolve and pop_resample: POP_ERR_STATE).  Results do not depend on it. */
+int pop_set_tuning(pop_t* pop, const pop_tuning* cfg);
 
 /*
  * Population mean of |delta rho_n|^2 over the current configurations (eq. fourdens:

@@ -35,7 +35,8 @@ EXPORTS = ("pop_workspace_bytes", "pop_init", "pop_set_state", "pop_evolve", "po
            "pop_set_potential", "pop_lineage", "pop_slots", "pop_first_slot",
            "pop_mlp_workspace_bytes", "pop_mlp_init", "pop_mlp_grad", "pop_mlp_step",
            "pop_mlp_params", "pop_mlp_potential", "pop_mlp_free",
-           "pop_launch_count", "pop_run_chains", "pop_strerror", "pop_free")
+           "pop_launch_count", "pop_run_chains", "pop_get_tuning", "pop_set_tuning",
+           "pop_strerror", "pop_free")
 KERNEL_KINDS = ("evolve", "weights", "gather", "gather_evolve", "other")
 POP_NOALLOC_MAX_CLONES = 1 << 20
 
@@ -44,6 +45,16 @@ class PopParams(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("N", ctypes.c_int32), ("n_clones", ctypes.c_int64),
                 ("seed", ctypes.c_uint64), ("weight_mode", ctypes.c_int32),
                 ("selection", ctypes.c_int32)]
+
+
+class PopTuning(ctypes.Structure):
+    _fields_ = [("evolve_grid", ctypes.c_int32), ("fuse_threads", ctypes.c_int32),
+                ("fuse_clones", ctypes.c_int32), ("chains", ctypes.c_int32),
+                ("gather_threads", ctypes.c_int32), ("default_us_per_interval", ctypes.c_float),
+                ("tuned_us_per_interval", ctypes.c_float)]
+
+
+TUNING_KEYS = ("evolve_grid", "fuse_threads", "fuse_clones", "chains", "gather_threads")
 
 
 class PopError(RuntimeError):
@@ -126,6 +137,10 @@ def library():
     L.pop_launch_count.restype = ctypes.c_int
     L.pop_run_chains.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]
     L.pop_run_chains.restype = ctypes.c_int32
+    L.pop_get_tuning.argtypes = [ctypes.c_void_p, ctypes.POINTER(PopTuning)]
+    L.pop_get_tuning.restype = ctypes.c_int
+    L.pop_set_tuning.argtypes = [ctypes.c_void_p, ctypes.POINTER(PopTuning)]
+    L.pop_set_tuning.restype = ctypes.c_int
     L.pop_select_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_uint64,
                                      ctypes.c_uint32, ctypes.c_void_p, _f64p, ctypes.c_void_p]
     L.pop_select_noalloc.restype = ctypes.c_int
@@ -243,11 +258,25 @@ class PopulationBatch:
         return dict(lattice=lat, K=K, anc=anc, dK=dK)
 
     def autotune(self, dt, s, trials=5):
-        """Choose the persistent evolve grid by timing (before the first interval)."""
+        """Choose the launch configuration by timing on this batch (before the first
+        interval); returns it as get_tuning() does."""
         s, sp = self._s(s)
         g = ctypes.c_int32(0)
         _check(self._lib.pop_autotune(self._h, float(dt), sp, int(trials), ctypes.byref(g)), "pop_autotune")
-        return int(g.value)
+        return self.get_tuning()
+
+    def get_tuning(self):
+        """The launch configuration (pop_tuning) as a dict."""
+        t = PopTuning()
+        _check(self._lib.pop_get_tuning(self._h, ctypes.byref(t)), "pop_get_tuning")
+        return {name: getattr(t, name) for name, _ in PopTuning._fields_}
+
+    def set_tuning(self, **cfg):
+        """Change entries of the launch configuration (results do not depend on it)."""
+        cur = self.get_tuning()
+        cur.update(cfg)
+        t = PopTuning(*(int(cur[k]) for k in TUNING_KEYS), 0.0, 0.0)
+        _check(self._lib.pop_set_tuning(self._h, ctypes.byref(t)), "pop_set_tuning")
 
     def run_chains(self):
         """First tile of each chain of run() and the tile count (K + 1 entries; [] when

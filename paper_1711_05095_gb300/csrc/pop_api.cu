@@ -16,6 +16,7 @@
 // need no new arguments.  The evolved lattices, K, dK and A are double-buffered by the
 // parity of the interval, so one interval's dynamical stage never overwrites the
 // population its cloning stage is still reading.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
@@ -187,6 +188,11 @@ struct pop_batch {
   cudaEvent_t ev_fork = nullptr;
   cudaEvent_t ev_join[kMaxChains - 1] = {};
   Batch chain[kMaxChains]{};                 // the batch with each chain's own interval counter
+  // launch configuration (rule-based at pop_init; pop_autotune or pop_set_tuning may change it)
+  int fuse_threads = 128;                    // fused kernel: threads per block (128 or 256)
+  int fuse_clones = kFuseClones;             // fused kernel: clones per lane (1 or 2)
+  int gather_threads = 0;                    // separate cloning stage: 128, 256, or 0 for the rule
+  float tuned_default_us = 0.0f, tuned_us = 0.0f;
   cudaGraphExec_t graph = nullptr;
   float graph_dt = 0.0f;
   unsigned char* ws = nullptr;
@@ -209,6 +215,8 @@ struct pop_batch {
   // pop_kernel_times: events recorded around every launch while set
   std::vector<cudaEvent_t>* timer_events = nullptr;
   std::vector<int>* timer_kinds = nullptr;
+  std::vector<int>* timer_intervals = nullptr;
+  int timer_interval = 0;
 };
 
 namespace {
@@ -291,6 +299,7 @@ void kernel_begin(pop_t* h, cudaStream_t st, int kind) {
     cudaEventRecord(e, st);
     h->timer_events->push_back(e);
     h->timer_kinds->push_back(kind);
+    if (h->timer_intervals) h->timer_intervals->push_back(h->timer_interval);
   }
 }
 
@@ -348,7 +357,8 @@ int launch_resample(pop_t* h, cudaStream_t st) {
   launch_weights(h, st);
   constexpr int GT = POP_GATHER_THREADS;
   kernel_begin(h, st, POP_K_GATHER);
-  if (h->lay.ntiles > kGatherWideTiles) {
+  const bool wide_blocks = h->gather_threads == 0 ? h->lay.ntiles > kGatherWideTiles : h->gather_threads == 256;
+  if (wide_blocks) {
     // many waves of tiles: 256-thread blocks keep more bytes in flight (measured
     // 4567 against 4379 GB/s on 2^25 two-word clones)
     constexpr int GW = POP_GATHER_WIDE_THREADS;
@@ -373,6 +383,18 @@ int launch_resample(pop_t* h, cudaStream_t st) {
   return cuda_status(cudaGetLastError());
 }
 
+// The fused kernel in the handle's configuration: 128 threads per block with one or two
+// clones per lane, or 256 threads with one.
+template <int W, bool MOD, bool SCAN>
+void launch_fused(pop_t* h, unsigned grid, cudaStream_t st, const Batch& Bx, float dt_f, int tile0) {
+  if (h->fuse_threads == 256)
+    k_gather<W, 256, true, MOD, SCAN, 1><<<grid, 256, 0, st>>>(Bx, dt_f, tile0);
+  else if (h->fuse_clones == 2)
+    k_gather<W, 128, true, MOD, SCAN, 2><<<grid, 128, 0, st>>>(Bx, dt_f, tile0);
+  else
+    k_gather<W, 128, true, MOD, SCAN, 1><<<grid, 128, 0, st>>>(Bx, dt_f, tile0);
+}
+
 // pop_run fuses the cloning stage of one interval with the dynamical stage of
 // the next when every population uses [eq] selection on a ring of at most 128 sites.
 bool fusable(const pop_t* h) {
@@ -391,59 +413,65 @@ int launch_resample_evolve_range(pop_t* h, cudaStream_t st, float dt_f, const Ba
   bool scan = true;
   for (int p = pop0; p < pop1; ++p) scan = scan && h->desc[p].ntiles > kScanTiles;
   if (scan) launch_tile_scan(h, st, Bx, pop0, pop1);
-  constexpr int GT = POP_FUSE_THREADS;
   kernel_begin(h, st, POP_K_GATHER_EVOLVE);
   if (h->lay.W == 1) {
     if (h->any_mod) {
-      if (scan) k_gather<1, GT, true, true, true, kFuseClones><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
-      else k_gather<1, GT, true, true, false, kFuseClones><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
+      if (scan) launch_fused<1, true, true>(h, grid, st, Bx, dt_f, tile0);
+      else launch_fused<1, true, false>(h, grid, st, Bx, dt_f, tile0);
     } else {
-      if (scan) k_gather<1, GT, true, false, true, kFuseClones><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
-      else k_gather<1, GT, true, false, false, kFuseClones><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
+      if (scan) launch_fused<1, false, true>(h, grid, st, Bx, dt_f, tile0);
+      else launch_fused<1, false, false>(h, grid, st, Bx, dt_f, tile0);
     }
   } else {
     if (h->any_mod) {
-      if (scan) k_gather<2, GT, true, true, true, kFuseClones><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
-      else k_gather<2, GT, true, true, false, kFuseClones><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
+      if (scan) launch_fused<2, true, true>(h, grid, st, Bx, dt_f, tile0);
+      else launch_fused<2, true, false>(h, grid, st, Bx, dt_f, tile0);
     } else {
-      if (scan) k_gather<2, GT, true, false, true, kFuseClones><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
-      else k_gather<2, GT, true, false, false, kFuseClones><<<grid, GT, 0, st>>>(Bx, dt_f, tile0);
+      if (scan) launch_fused<2, false, true>(h, grid, st, Bx, dt_f, tile0);
+      else launch_fused<2, false, false>(h, grid, st, Bx, dt_f, tile0);
     }
   }
   kernel_end(h, st);
   return cuda_status(cudaGetLastError());
 }
 
-int launch_resample_evolve(pop_t* h, cudaStream_t st, float dt_f) {
-  return launch_resample_evolve_range(h, st, dt_f, h->B, 0, h->lay.ntiles, 0, h->lay.P);
-}
 
-// pop_run's chains.  In a batch of at most two waves of the fused kernel the drain at
-// the end of each launch and the k_weights between launches are a large part of an
-// interval, and more chains fill them; in a larger batch more chains only compete.
-int size_chains(pop_t* h) {
+// pop_run's chains: the largest K <= want of choose_chains, each chain a copy of the
+// batch with its own interval counter (the counter word after the batch's own).
+void set_chains(pop_t* h, int want) {
   h->nch = 1;
   h->chain_tile[0] = 0;
   h->chain_tile[1] = h->lay.ntiles;
-  h->chain_pop[0] = 0;
-  h->chain_pop[1] = h->lay.P;
-  if (!fusable(h)) return POP_OK;
-  constexpr int GT = POP_FUSE_THREADS;
-  const void* f = h->lay.W == 1
-                      ? (h->any_mod ? (const void*)k_gather<1, GT, true, true, false, kFuseClones>
-                                    : (const void*)k_gather<1, GT, true, false, false, kFuseClones>)
-                      : (h->any_mod ? (const void*)k_gather<2, GT, true, true, false, kFuseClones>
-                                    : (const void*)k_gather<2, GT, true, false, false, kFuseClones>);
-  int per_sm = 0, sms = 0;
-  POP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, GT, 0));
-  POP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
-  const long long wave = (long long)(per_sm < 1 ? 1 : per_sm) * sms;
-  const int want = h->lay.ntiles <= 2 * wave ? POP_RUN_CHAINS : POP_RUN_CHAINS_LARGE;
-  h->nch = choose_chains(h->desc, h->lay.ntiles, want, h->chain_tile);
+  if (fusable(h) && want > 1) h->nch = choose_chains(h->desc, h->lay.ntiles, want, h->chain_tile);
   for (int c = 0, p = 0; c <= h->nch; ++c) {  // chains hold whole populations
     while (p < h->lay.P && h->desc[p].first_tile < h->chain_tile[c]) ++p;
     h->chain_pop[c] = p;
   }
+  for (int c = 0; c < h->nch; ++c) {
+    h->chain[c] = h->B;
+    h->chain[c].beta = h->B.beta + 1 + c;
+  }
+}
+
+// The rule pop_init starts from: in a batch of at most two waves of the fused kernel
+// the drain at the end of each launch and the k_weights between launches are a large
+// part of an interval, and more chains fill them; in a larger batch more chains only
+// compete.
+int size_chains(pop_t* h) {
+  int want = 1;
+  if (fusable(h)) {
+    const void* f = h->lay.W == 1
+                        ? (h->any_mod ? (const void*)k_gather<1, 128, true, true, false, 1>
+                                      : (const void*)k_gather<1, 128, true, false, false, 1>)
+                        : (h->any_mod ? (const void*)k_gather<2, 128, true, true, false, 1>
+                                      : (const void*)k_gather<2, 128, true, false, false, 1>);
+    int per_sm = 0, sms = 0;
+    POP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, 128, 0));
+    POP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    const long long wave = (long long)(per_sm < 1 ? 1 : per_sm) * sms;
+    want = h->lay.ntiles <= 2 * wave ? POP_RUN_CHAINS : POP_RUN_CHAINS_LARGE;
+  }
+  set_chains(h, want);
   return POP_OK;
 }
 
@@ -489,6 +517,46 @@ int size_evolve_grid_wide(pop_t* h) {
   h->evolve_grid_cap = h->evolve_grid;
   h->evolve_smem = 0;
   return POP_OK;
+}
+
+// n fused intervals over the chains: chain 0 on st, the others on the auxiliary
+// streams forked from st and joined back into it, each chain with its own interval
+// counter (copy_chain_counters brings them in line with the batch's counter before and
+// the batch's back from chain 0 after).
+int run_chains(pop_t* h, cudaStream_t st, float dt_f, int64_t n) {
+  if (h->nch == 1) {
+    int lr = POP_OK;
+    for (int64_t i = 0; i < n && lr == POP_OK; ++i)
+      lr = launch_resample_evolve_range(h, st, dt_f, h->chain[0], 0, h->lay.ntiles, 0, h->lay.P);
+    return lr;
+  }
+  if (cudaEventRecord(h->ev_fork, st) != cudaSuccess) return POP_ERR_CUDA;
+  for (int c = 0; c + 1 < h->nch; ++c)
+    if (cudaStreamWaitEvent(h->aux_stream[c], h->ev_fork, 0) != cudaSuccess) return POP_ERR_CUDA;
+  int lr = POP_OK;
+  for (int64_t i = 0; i < n && lr == POP_OK; ++i)
+    for (int c = 0; c < h->nch && lr == POP_OK; ++c)
+      lr = launch_resample_evolve_range(h, c == 0 ? st : h->aux_stream[c - 1], dt_f, h->chain[c],
+                                        h->chain_tile[c], h->chain_tile[c + 1] - h->chain_tile[c],
+                                        h->chain_pop[c], h->chain_pop[c + 1]);
+  // the joins are made even after a failed launch, so a capture can end cleanly
+  for (int c = 0; c + 1 < h->nch; ++c)
+    if (cudaEventRecord(h->ev_join[c], h->aux_stream[c]) != cudaSuccess ||
+        cudaStreamWaitEvent(st, h->ev_join[c], 0) != cudaSuccess)
+      return POP_ERR_CUDA;
+  return lr;
+}
+
+cudaError_t copy_chain_counters(pop_t* h, bool to_chains) {
+  for (int c = 0; c < h->nch; ++c) {
+    if (!to_chains && c > 0) break;
+    const cudaError_t e = to_chains ? cudaMemcpyAsync(h->chain[c].beta, h->B.beta, sizeof(unsigned int),
+                                                      cudaMemcpyDeviceToDevice, h->stream)
+                                    : cudaMemcpyAsync(h->B.beta, h->chain[0].beta, sizeof(unsigned int),
+                                                      cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 int check_device_errors(pop_t* h, std::vector<PopState>* out) {
@@ -651,18 +719,14 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
   B.dKb[1] = B.dKb[0] + lay.nslots;
   B.anc = (int32_t*)(ws + lay.o_anc);
   B.ntiles = lay.ntiles;
-  if (size_chains(h) != POP_OK) return fail(POP_ERR_CUDA);
-  for (int c = 0; c < h->nch; ++c) {
-    h->chain[c] = B;
-    h->chain[c].beta = B.beta + 1 + c;
-  }
-  for (int c = 0; c + 1 < h->nch; ++c)
-    if (cudaStreamCreateWithFlags(&h->aux_stream[c], cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->ev_join[c], cudaEventDisableTiming) != cudaSuccess)
-      return fail(POP_ERR_CUDA);
   B.nunits = lay.nunits;
   B.nslots = lay.nslots;
   B.W = lay.W;
+  if (size_chains(h) != POP_OK) return fail(POP_ERR_CUDA);
+  for (int c = 0; c + 1 < kMaxChains; ++c)
+    if (cudaStreamCreateWithFlags(&h->aux_stream[c], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_join[c], cudaEventDisableTiming) != cudaSuccess)
+      return fail(POP_ERR_CUDA);
   const bool mod = h->any_mod;
   const int grc = lay.W == 1 ? (mod ? size_evolve_grid<1, true>(h) : size_evolve_grid<1, false>(h))
                   : lay.W == 2 ? (mod ? size_evolve_grid<2, true>(h) : size_evolve_grid<2, false>(h))
@@ -742,9 +806,9 @@ int pop_run(pop_t* h, double dt, const double* s, int64_t n_intervals) {
   if (rc != POP_OK) return rc;
   if (n_intervals == 0) return POP_OK;
   const float dt_f = (float)dt;
-  // fused: evolve, then (n - 1) x [weights, gather + next evolve], then weights, gather;
-  // otherwise n x [evolve, weights, gather].  The graph holds kGraphIntervals of the
-  // repeated part.
+  // fused: evolve, then (n - 1) x [weights, gather + next evolve] over the chains, then
+  // weights, gather; otherwise n x [evolve, weights, gather].  The graph holds
+  // kGraphIntervals of the repeated part.
   const bool fuse = fusable(h);
   if (fuse) {
     rc = launch_evolve(h, h->stream, dt_f);
@@ -753,36 +817,16 @@ int pop_run(pop_t* h, double dt, const double* s, int64_t n_intervals) {
   const int64_t n_rep = fuse ? n_intervals - 1 : n_intervals;
   const int64_t n_graph = n_rep / kGraphIntervals;
   const int64_t n_rest = n_rep % kGraphIntervals;
-  // chains: each part of the batch runs its own sequence, chain 0 on st and the others
-  // on the auxiliary streams (forked from and joined back into st), each with its own
-  // interval counter
-  const bool split = fuse && h->nch > 1;
-  auto one = [&](cudaStream_t st) {
-    if (fuse) return launch_resample_evolve(h, st, dt_f);
-    const int lr = launch_evolve(h, st, dt_f);
-    return lr == POP_OK ? launch_resample(h, st) : lr;
-  };
-  auto chains = [&](cudaStream_t st, int64_t n) {
-    if (cudaEventRecord(h->ev_fork, st) != cudaSuccess) return (int)POP_ERR_CUDA;
-    for (int c = 0; c + 1 < h->nch; ++c)
-      if (cudaStreamWaitEvent(h->aux_stream[c], h->ev_fork, 0) != cudaSuccess) return (int)POP_ERR_CUDA;
+  auto block = [&](cudaStream_t st, int64_t n) {
+    if (fuse) return run_chains(h, st, dt_f, n);
     int lr = POP_OK;
-    for (int64_t i = 0; i < n && lr == POP_OK; ++i)
-      for (int c = 0; c < h->nch && lr == POP_OK; ++c)
-        lr = launch_resample_evolve_range(h, c == 0 ? st : h->aux_stream[c - 1], dt_f, h->chain[c],
-                                          h->chain_tile[c], h->chain_tile[c + 1] - h->chain_tile[c],
-                                          h->chain_pop[c], h->chain_pop[c + 1]);
-    // the joins are made even after a failed launch, so a capture can end cleanly
-    for (int c = 0; c + 1 < h->nch; ++c)
-      if (cudaEventRecord(h->ev_join[c], h->aux_stream[c]) != cudaSuccess ||
-          cudaStreamWaitEvent(st, h->ev_join[c], 0) != cudaSuccess)
-        return (int)POP_ERR_CUDA;
+    for (int64_t i = 0; i < n && lr == POP_OK; ++i) {
+      lr = launch_evolve(h, st, dt_f);
+      if (lr == POP_OK) lr = launch_resample(h, st);
+    }
     return lr;
   };
-  if (split)
-    for (int c = 0; c < h->nch; ++c)
-      POP_CUDA(cudaMemcpyAsync(h->chain[c].beta, h->B.beta, sizeof(unsigned int),
-                               cudaMemcpyDeviceToDevice, h->stream));
+  if (fuse) POP_CUDA(copy_chain_counters(h, true));
   if (n_graph > 0 && (h->graph == nullptr || h->graph_dt != dt_f)) {
     if (h->graph != nullptr) {
       cudaGraphExecDestroy(h->graph);
@@ -790,12 +834,9 @@ int pop_run(pop_t* h, double dt, const double* s, int64_t n_intervals) {
     }
     cudaGraph_t g = nullptr;
     POP_CUDA(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
-    int lr = POP_OK;
     for (uint64_t& c : h->graph_counts) c = 0;
     h->count = h->graph_counts;
-    if (split) lr = chains(h->capture_stream, kGraphIntervals);
-    else
-      for (int i = 0; i < kGraphIntervals && lr == POP_OK; ++i) lr = one(h->capture_stream);
+    const int lr = block(h->capture_stream, kGraphIntervals);
     h->count = h->launches;
     const cudaError_t ec = cudaStreamEndCapture(h->capture_stream, &g);
     if (lr != POP_OK || ec != cudaSuccess) {
@@ -814,20 +855,12 @@ int pop_run(pop_t* h, double dt, const double* s, int64_t n_intervals) {
     POP_CUDA(cudaGraphLaunch(h->graph, h->stream));
     for (int k = 0; k < POP_NKINDS; ++k) h->launches[k] += h->graph_counts[k];
   }
-  if (split && n_rest > 0) {
-    rc = chains(h->stream, n_rest);
+  if (n_rest > 0) {
+    rc = block(h->stream, n_rest);
     if (rc != POP_OK) return rc;
-  } else {
-    for (int64_t i = 0; i < n_rest; ++i) {
-      rc = one(h->stream);
-      if (rc != POP_OK) return rc;
-    }
-  }
-  if (split) {
-    POP_CUDA(cudaMemcpyAsync(h->B.beta, h->chain[0].beta, sizeof(unsigned int),
-                             cudaMemcpyDeviceToDevice, h->stream));
   }
   if (fuse) {
+    POP_CUDA(copy_chain_counters(h, false));
     rc = launch_resample(h, h->stream);
     if (rc != POP_OK) return rc;
   }
@@ -854,43 +887,74 @@ int pop_kernel_times(pop_t* h, double dt, const double* s, int64_t n_intervals, 
   rc = total_hops(&hops0);
   if (rc != POP_OK) return rc;
   std::vector<cudaEvent_t> events;
-  std::vector<int> kinds;
-  events.reserve((size_t)(6 * n_intervals + 4));
+  std::vector<int> kinds, ivs;
+  events.reserve((size_t)(6 * (n_intervals + 2) * h->nch));
+  cudaEvent_t origin = nullptr;
+  POP_CUDA(cudaEventCreate(&origin));
+  POP_CUDA(cudaEventRecord(origin, h->stream));
   h->timer_events = &events;
   h->timer_kinds = &kinds;
+  h->timer_intervals = &ivs;
+  h->timer_interval = 0;
   const float dt_f = (float)dt;
   const bool fuse = per_step == 0 && fusable(h);
-  // the same launches, in the same order, as pop_run (or the per-step calls)
+  // the same launches, in the same order and on the same streams, as pop_run (or the
+  // per-step calls), each interval's launches tagged with its index
   if (fuse) {
     rc = launch_evolve(h, h->stream, dt_f);
     if (rc == POP_OK) rc = total_hops(&hops1);
-    for (int64_t i = 1; i < n_intervals && rc == POP_OK; ++i)
-      rc = launch_resample_evolve(h, h->stream, dt_f);
+    if (rc == POP_OK) rc = copy_chain_counters(h, true) == cudaSuccess ? POP_OK : POP_ERR_CUDA;
+    for (int64_t i = 1; i < n_intervals && rc == POP_OK; ++i) {
+      h->timer_interval = (int)i;
+      rc = run_chains(h, h->stream, dt_f, 1);
+    }
+    h->timer_interval = (int)n_intervals;
+    if (rc == POP_OK) rc = copy_chain_counters(h, false) == cudaSuccess ? POP_OK : POP_ERR_CUDA;
     if (rc == POP_OK) rc = launch_resample(h, h->stream);
   } else {
     for (int64_t i = 0; i < n_intervals && rc == POP_OK; ++i) {
+      h->timer_interval = (int)i;
       rc = launch_evolve(h, h->stream, dt_f);
       if (rc == POP_OK) rc = launch_resample(h, h->stream);
     }
   }
   h->timer_events = nullptr;
   h->timer_kinds = nullptr;
+  h->timer_intervals = nullptr;
   if (rc == POP_OK) rc = total_hops(&hops2);
-  double sum_ms[POP_NKINDS] = {};
+  // per kind and interval: the span from the first start to the last end of its launches
+  // (the launches of the chains run side by side), times from the common origin event
+  const int64_t nspan = (int64_t)POP_NKINDS * (n_intervals + 1);
+  std::vector<double> t0(nspan, 1e300), t1(nspan, -1e300);
   int64_t cnt[POP_NKINDS] = {};
-  for (size_t i = 0; i < kinds.size(); ++i) {
-    float ms = 0.0f;
-    if (rc == POP_OK && cudaEventElapsedTime(&ms, events[2 * i], events[2 * i + 1]) != cudaSuccess)
+  for (size_t i = 0; i < kinds.size() && rc == POP_OK; ++i) {
+    float a = 0.0f, b = 0.0f;
+    if (cudaEventElapsedTime(&a, origin, events[2 * i]) != cudaSuccess ||
+        cudaEventElapsedTime(&b, origin, events[2 * i + 1]) != cudaSuccess) {
       rc = POP_ERR_CUDA;
-    sum_ms[kinds[i]] += ms;
+      break;
+    }
+    const int64_t at = (int64_t)kinds[i] * (n_intervals + 1) + ivs[i];
+    t0[at] = std::min(t0[at], (double)a);
+    t1[at] = std::max(t1[at], (double)b);
     cnt[kinds[i]] += 1;
   }
   for (cudaEvent_t e : events) cudaEventDestroy(e);
+  cudaEventDestroy(origin);
   if (rc != POP_OK) return rc;
   h->intervals += n_intervals;
   h->t_obs += (double)n_intervals * dt;
   for (int k = 0; k < POP_NKINDS; ++k) {
-    if (h_us) h_us[k] = cnt[k] ? 1e3 * sum_ms[k] / (double)cnt[k] : 0.0;
+    double sum = 0.0;
+    int64_t groups = 0;
+    for (int64_t i = 0; i <= n_intervals; ++i) {
+      const int64_t at = (int64_t)k * (n_intervals + 1) + i;
+      if (t1[at] >= t0[at]) {
+        sum += t1[at] - t0[at];
+        ++groups;
+      }
+    }
+    if (h_us) h_us[k] = groups ? 1e3 * sum / (double)groups : 0.0;
     if (h_n) h_n[k] = cnt[k];
     if (h_hops) h_hops[k] = 0;
   }
@@ -1010,50 +1074,202 @@ int pop_autotune(pop_t* h, double dt, const double* s, int32_t trials, int32_t* 
   if (h->phase != kReady || h->intervals != 0) return POP_ERR_STATE;
   int rc = fix_biases(h, s);
   if (rc != POP_OK) return rc;
-  // the trials evolve interval 1 repeatedly; the per-population counters and the
-  // activities are put back afterwards, so tuning changes no result
+  // Every trial runs from interval 1 on the initial population (the fused intervals and
+  // the dynamical stage write only the evolved buffers; a trial of the separate cloning
+  // stage writes the population, which is kept in the free evolved buffers of the even
+  // parity meanwhile); the per-population counters, the interval counters and the
+  // activities are put back afterwards, so tuning changes no result.
   std::vector<PopState> saved((size_t)h->lay.P);
   POP_CUDA(cudaMemcpyAsync(saved.data(), h->ws + h->lay.o_st, saved.size() * sizeof(PopState),
                            cudaMemcpyDeviceToHost, h->stream));
   POP_CUDA(cudaStreamSynchronize(h->stream));
+  const unsigned int beta1 = 1u;
+  auto restore = [&]() {
+    if (cudaMemcpyAsync(h->ws + h->lay.o_st, saved.data(), saved.size() * sizeof(PopState),
+                        cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+      return false;
+    for (int c = 0; c <= kMaxChains; ++c)
+      if (cudaMemcpyAsync(h->B.beta + c, &beta1, sizeof beta1, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+        return false;
+    return cudaMemsetAsync(h->B.dKb[0], 0, 2 * (size_t)h->lay.nslots * sizeof(int32_t), h->stream) == cudaSuccess &&
+           cudaStreamSynchronize(h->stream) == cudaSuccess;
+  };
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  POP_CUDA(cudaEventCreate(&e0));
+  POP_CUDA(cudaEventCreate(&e1));
+  const float dt_f = (float)dt;
+  // time of `reps` repetitions of a launch sequence after one untimed one, ms per repetition
+  auto timed = [&](auto&& seq, int reps, float* ms_out) {
+    if (!restore()) return (int)POP_ERR_CUDA;
+    int lr = seq(true);
+    if (lr == POP_OK && cudaEventRecord(e0, h->stream) != cudaSuccess) lr = POP_ERR_CUDA;
+    for (int i = 0; i < reps && lr == POP_OK; ++i) lr = seq(false);
+    if (lr == POP_OK && (cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+      lr = POP_ERR_CUDA;
+    float ms = 0.0f;
+    if (lr == POP_OK) cudaEventElapsedTime(&ms, e0, e1);
+    *ms_out = ms / (float)reps;
+    return lr;
+  };
+
+  uint64_t launches_before[POP_NKINDS];
+  for (int k = 0; k < POP_NKINDS; ++k) launches_before[k] = h->launches[k];
+  // (1) the persistent grid of the separate dynamical stage (first interval of a fused
+  // run, every interval otherwise): 1 .. the resident blocks per SM, times the SM count
   int sms = 0;
   POP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
   const int cap = h->evolve_grid_cap;
   const int per_sm = cap / (sms > 0 ? sms : 1);
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  POP_CUDA(cudaEventCreate(&e0));
-  POP_CUDA(cudaEventCreate(&e1));
   int best = cap;
   float best_ms = 1e30f;
-  const float dt_f = (float)dt;
-  for (int b = per_sm > 0 ? per_sm : 1; b >= 1; --b) {
+  for (int b = per_sm > 0 ? per_sm : 1; b >= 1 && rc == POP_OK; --b) {
     const int grid = per_sm > 0 ? b * sms : cap;
     set_evolve_grid(h, grid);
-    rc = launch_evolve(h, h->stream, dt_f);  // warm-up
-    for (int i = 0; i < trials && rc == POP_OK; ++i) {
-      if (i == 0) cudaEventRecord(e0, h->stream);
-      rc = launch_evolve(h, h->stream, dt_f);
-    }
-    cudaEventRecord(e1, h->stream);
-    if (rc != POP_OK || cudaEventSynchronize(e1) != cudaSuccess) { rc = POP_ERR_CUDA; break; }
     float ms = 0.0f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best_ms) { best_ms = ms; best = grid; }
+    rc = timed([&](bool) { return launch_evolve(h, h->stream, dt_f); }, trials, &ms);
+    if (rc == POP_OK && ms < best_ms) { best_ms = ms; best = grid; }
     if (per_sm <= 0) break;
+  }
+  set_evolve_grid(h, best);
+
+  // (2) fused batches: the fused kernel's form (threads per block, clones per lane) and
+  // the chains of pop_run, by the time per interval of `trials` fused intervals
+  if (rc == POP_OK && fusable(h)) {
+    const int forms[3][2] = {{128, 1}, {128, 2}, {256, 1}};
+    const int wants[4] = {1, 2, 4, 8};
+    const int def_threads = h->fuse_threads, def_clones = h->fuse_clones, def_nch = h->nch;
+    int bt = def_threads, bc = def_clones, bw = def_nch;
+    float bms = 1e30f, def_ms = 0.0f;
+    int last_nch = -1;
+    for (int f = 0; f < 3 && rc == POP_OK; ++f) {
+      last_nch = -1;
+      for (int w = 0; w < 4 && rc == POP_OK; ++w) {
+        h->fuse_threads = forms[f][0];
+        h->fuse_clones = forms[f][1];
+        set_chains(h, wants[w]);
+        if (h->nch == last_nch) continue;  // the same split as the smaller want
+        last_nch = h->nch;
+        // `trials` fused intervals captured as a graph, as pop_run replays them (launched
+        // one by one, many short chains would be timed by their launch overhead)
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        if (cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+          rc = POP_ERR_CUDA;
+          break;
+        }
+        uint64_t* const count = h->count;
+        h->count = h->graph_counts;  // launches made while tuning are not the batch's
+        const int lc = run_chains(h, h->capture_stream, dt_f, trials);
+        h->count = count;
+        const cudaError_t ec = cudaStreamEndCapture(h->capture_stream, &g);
+        if (lc != POP_OK || ec != cudaSuccess || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) {
+          if (g) cudaGraphDestroy(g);
+          rc = POP_ERR_CUDA;
+          break;
+        }
+        cudaGraphDestroy(g);
+        float ms = 0.0f;
+        rc = timed([&](bool first) {
+              int lr = POP_OK;
+              if (first) {
+                lr = launch_evolve(h, h->stream, dt_f);
+                if (lr == POP_OK && copy_chain_counters(h, true) != cudaSuccess) lr = POP_ERR_CUDA;
+              }
+              if (lr == POP_OK && cudaGraphLaunch(ge, h->stream) != cudaSuccess) lr = POP_ERR_CUDA;
+              return lr;
+            }, 3, &ms);
+        cudaGraphExecDestroy(ge);
+        ms /= (float)trials;
+        if (rc != POP_OK) break;
+        if (forms[f][0] == def_threads && forms[f][1] == def_clones && h->nch == def_nch) def_ms = ms;
+        if (ms < bms) { bms = ms; bt = forms[f][0]; bc = forms[f][1]; bw = wants[w]; }
+      }
+    }
+    h->fuse_threads = bt;
+    h->fuse_clones = bc;
+    set_chains(h, bw);
+    h->tuned_default_us = 1e3f * def_ms;
+    h->tuned_us = 1e3f * bms;
+  }
+
+  // (3) batches that do not fuse: the separate cloning stage's block size, by the time
+  // of whole intervals; the population is kept in the even-parity evolved buffers
+  if (rc == POP_OK && !fusable(h)) {
+    const size_t lat = (size_t)h->lay.nslots * h->lay.W * sizeof(unsigned long long);
+    const size_t ks = (size_t)h->lay.nslots * sizeof(int32_t);
+    POP_CUDA(cudaMemcpyAsync(h->B.Xb[0], h->B.Y, lat, cudaMemcpyDeviceToDevice, h->stream));
+    POP_CUDA(cudaMemcpyAsync(h->B.KXb[0], h->B.KY, ks, cudaMemcpyDeviceToDevice, h->stream));
+    const int def = h->gather_threads;
+    float def_ms = 0.0f, bms = 1e30f;
+    int bg = def;
+    for (int g : {0, 128, 256}) {
+      h->gather_threads = g;
+      float ms = 0.0f;
+      rc = timed([&](bool) {
+            int lr = cudaMemcpyAsync(h->B.Y, h->B.Xb[0], lat, cudaMemcpyDeviceToDevice, h->stream) == cudaSuccess &&
+                             cudaMemcpyAsync(h->B.KY, h->B.KXb[0], ks, cudaMemcpyDeviceToDevice, h->stream) == cudaSuccess
+                         ? POP_OK : POP_ERR_CUDA;
+            if (lr == POP_OK) lr = launch_evolve(h, h->stream, dt_f);
+            if (lr == POP_OK) lr = launch_resample(h, h->stream);
+            if (lr == POP_OK) {  // the next repetition evolves interval 1 again
+              for (int c = 0; c <= kMaxChains && lr == POP_OK; ++c)
+                if (cudaMemcpyAsync(h->B.beta + c, &beta1, sizeof beta1, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+                  lr = POP_ERR_CUDA;
+            }
+            return lr;
+          }, trials, &ms);
+      if (rc != POP_OK) break;
+      if (g == def) def_ms = ms;
+      if (ms < bms) { bms = ms; bg = g; }
+    }
+    h->gather_threads = bg;
+    POP_CUDA(cudaMemcpyAsync(h->B.Y, h->B.Xb[0], lat, cudaMemcpyDeviceToDevice, h->stream));
+    POP_CUDA(cudaMemcpyAsync(h->B.KY, h->B.KXb[0], ks, cudaMemcpyDeviceToDevice, h->stream));
+    h->tuned_default_us = 1e3f * def_ms;
+    h->tuned_us = 1e3f * bms;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  set_evolve_grid(h, best);
+  for (int k = 0; k < POP_NKINDS; ++k) h->launches[k] = launches_before[k];
   if (h->graph != nullptr) {  // a captured graph holds the old launch configuration
     cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
   }
-  POP_CUDA(cudaMemcpyAsync(h->ws + h->lay.o_st, saved.data(), saved.size() * sizeof(PopState),
-                           cudaMemcpyHostToDevice, h->stream));
-  POP_CUDA(cudaMemsetAsync(h->B.dKb[0], 0, 2 * (size_t)h->lay.nslots * sizeof(int32_t), h->stream));
-  POP_CUDA(cudaStreamSynchronize(h->stream));
+  if (!restore()) return POP_ERR_CUDA;
   if (rc != POP_OK) return rc;
   if (h_evolve_grid) *h_evolve_grid = best;
+  return POP_OK;
+}
+
+int pop_get_tuning(pop_t* h, pop_tuning* out) {
+  if (h == nullptr || out == nullptr) return POP_ERR_ARG;
+  out->evolve_grid = h->evolve_grid;
+  out->fuse_threads = h->fuse_threads;
+  out->fuse_clones = h->fuse_clones;
+  out->chains = h->nch;
+  out->gather_threads = h->gather_threads;
+  out->default_us_per_interval = h->tuned_default_us;
+  out->tuned_us_per_interval = h->tuned_us;
+  return POP_OK;
+}
+
+int pop_set_tuning(pop_t* h, const pop_tuning* cfg) {
+  if (h == nullptr || cfg == nullptr) return POP_ERR_ARG;
+  if (cfg->evolve_grid < 1 || (cfg->fuse_threads != 128 && cfg->fuse_threads != 256) ||
+      (cfg->fuse_clones != 1 && cfg->fuse_clones != 2) || (cfg->fuse_threads == 256 && cfg->fuse_clones != 1) ||
+      cfg->chains < 1 || cfg->chains > kMaxChains ||
+      (cfg->gather_threads != 0 && cfg->gather_threads != 128 && cfg->gather_threads != 256))
+    return POP_ERR_ARG;
+  if (h->phase != kReady) return POP_ERR_STATE;
+  set_evolve_grid(h, cfg->evolve_grid);
+  h->fuse_threads = cfg->fuse_threads;
+  h->fuse_clones = cfg->fuse_clones;
+  h->gather_threads = cfg->gather_threads;
+  set_chains(h, cfg->chains);
+  if (h->graph != nullptr) {  // the captured graph holds the old launch configuration
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
   return POP_OK;
 }
 

@@ -489,7 +489,7 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(Batch B, int pop0) {
 // NCL (FUSE only): clones each lane advances together in the dynamical stage, 1 or 2
 // (two independent Philox and bit-select chains in flight per lane).
 template <int W, int NT, bool FUSE = false, bool MOD = false, bool SCAN = true, int NCL = 1>
-__global__ void __launch_bounds__(NT, FUSE ? (NCL == 1 ? POP_FUSE_MIN_BLOCKS : POP_FUSE2_MIN_BLOCKS)
+__global__ void __launch_bounds__(NT, FUSE ? (NCL == 1 ? POP_FUSE_MIN_BLOCKS * 128 / NT : POP_FUSE2_MIN_BLOCKS)
                                            : (NT == 128 ? 11 : (NT == 256 ? 6 : 3)))
     k_gather(Batch B, float dt_f, int tile0) {
   constexpr int NI = kTile / NT;   // old clones per thread

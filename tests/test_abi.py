@@ -89,12 +89,14 @@ def test_every_handle_call_rejects_a_null_handle(lib):
     assert lib.pop_autotune(None, 0.1, None, 1, None) == E
     assert lib.pop_lineage(None, None, None) == E
     assert lib.pop_density_mode(None, 1, None) == E
+    assert lib.pop_get_tuning(None, None) == E
+    assert lib.pop_set_tuning(None, None) == E
     assert lib.pop_run_chains(None, None) == -1
     assert lib.pop_slots(None) == -1
     assert lib.pop_first_slot(None, 0) == -1
 
 
 def test_strerror(lib):
-    for code in (0, -1, -2, -3, -4, -5):
+    for code in (0, -1, -2, -3, -5):
         assert lib.pop_strerror(code)
     assert pg.strerror(-3).startswith("interval activity")

@@ -406,8 +406,9 @@ def test_autotune_changes_no_result(pg):
     pops = [dict(L=50, N=25, n_clones=5000, seed=9), dict(L=128, N=64, n_clones=3000, seed=10)]
     s = [0.01, -0.002]
     a = pg.PopulationBatch(pops)
-    grid = a.autotune(0.1, s, trials=3)
-    assert grid > 0
+    tuned = a.autotune(0.1, s, trials=3)
+    assert tuned["evolve_grid"] > 0 and tuned["tuned_us_per_interval"] > 0
+    assert tuned["tuned_us_per_interval"] <= tuned["default_us_per_interval"]
     b = pg.PopulationBatch(pops)
     a.run(0.1, s, 40)
     b.run(0.1, s, 40)
@@ -421,10 +422,66 @@ def test_autotune_changes_no_result(pg):
         a.autotune(0.1, s)   # only before the first interval
 
 
+@pytest.mark.parametrize("cfg", [
+    dict(fuse_threads=128, fuse_clones=1, chains=1), dict(fuse_threads=128, fuse_clones=2, chains=1),
+    dict(fuse_threads=256, fuse_clones=1, chains=1), dict(fuse_threads=128, fuse_clones=1, chains=2),
+    dict(fuse_threads=128, fuse_clones=2, chains=4), dict(fuse_threads=256, fuse_clones=1, chains=8),
+    dict(evolve_grid=7, chains=3), dict(gather_threads=256), dict(gather_threads=128)])
+def test_every_tuned_parameter_changes_no_result(pg, cfg):
+    # every value of every tuned parameter gives the same lattices, activities,
+    # ancestors and psi as the configuration pop_init chose (a fused batch of five
+    # populations, mixed L and tile counts, both signs of s)
+    pops = [dict(L=50, N=25, n_clones=5000, seed=31), dict(L=128, N=64, n_clones=3000, seed=32),
+            dict(L=100, N=40, n_clones=1100, seed=33), dict(L=70, N=35, n_clones=2500, seed=34),
+            dict(L=128, N=60, n_clones=4100, seed=35)]
+    s = [0.01, -0.002, 0.004, 0.0, 0.02]
+    a = pg.PopulationBatch(pops)
+    a.set_tuning(**cfg)
+    got = a.get_tuning()
+    for k, v in cfg.items():
+        assert got[k] == v or (k == "chains" and 1 <= got[k] <= v), (k, got[k], v)
+    b = pg.PopulationBatch(pops)
+    a.run(0.1, s, 37)
+    b.run(0.1, s, 37)
+    for p in range(len(pops)):
+        ga, gb = a.copy_state(p), b.copy_state(p)
+        for key in ("lattice", "K", "anc", "dK"):
+            assert np.array_equal(ga[key], gb[key]), (p, key)
+    np.testing.assert_array_equal(a.estimate_psi()[0], b.estimate_psi()[0])
+    np.testing.assert_array_equal(a.events(), b.events())
+
+
+def test_gather_tuning_of_a_batch_that_does_not_fuse_changes_no_result(pg):
+    # an [iid] population keeps the separate cloning stage, whose block size the tuner
+    # times on trials that write the population (kept aside and put back)
+    pops = [dict(L=50, N=25, n_clones=6000, seed=41, selection=pg.POP_IID),
+            dict(L=128, N=64, n_clones=5000, seed=42)]
+    s = [0.01, 0.003]
+    a = pg.PopulationBatch(pops)
+    tuned = a.autotune(0.1, s, trials=2)
+    assert tuned["gather_threads"] in (0, 128, 256)
+    b = pg.PopulationBatch(pops)
+    a.run(0.1, s, 20)
+    b.run(0.1, s, 20)
+    for p in range(2):
+        ga, gb = a.copy_state(p), b.copy_state(p)
+        for key in ("lattice", "K", "anc", "dK"):
+            assert np.array_equal(ga[key], gb[key]), (p, key)
+    np.testing.assert_array_equal(a.estimate_psi()[0], b.estimate_psi()[0])
+
+
+def test_set_tuning_rejects_out_of_range(pg):
+    a = pg.PopulationBatch([dict(L=50, N=25, n_clones=2000, seed=1)])
+    for bad in (dict(fuse_threads=64), dict(fuse_clones=3), dict(fuse_threads=256, fuse_clones=2),
+                dict(chains=0), dict(chains=9), dict(gather_threads=512), dict(evolve_grid=0)):
+        with pytest.raises(pg.PopError):
+            a.set_tuning(**bad)
+
+
 def test_kernel_times_equals_run_and_counts(pg):
     # pop_kernel_times launches what pop_run launches (results identical); the
     # launch counters follow the fused sequence: one dynamical stage, then
-    # (n - 1) x [weights, fused stage], then weights and the cloning stage
+    # (n - 1) x [weights, fused stage] per chain, then weights and the cloning stage
     pops = [dict(L=50, N=25, n_clones=3000, seed=21), dict(L=90, N=45, n_clones=2000, seed=22)]
     s = [0.02, -0.003]
     n = 40
@@ -437,15 +494,18 @@ def test_kernel_times_equals_run_and_counts(pg):
         for key in ("lattice", "K", "anc", "dK"):
             assert np.array_equal(ga[key], gb[key]), key
     np.testing.assert_array_equal(a.events(), b.events())
-    assert kt["evolve"][1] == 1 and kt["gather_evolve"][1] == n - 1
-    assert kt["weights"][1] == n and kt["gather"][1] == 1
+    # two chains (below): each fused interval is two launches of each kind, and the
+    # reported time is the span of the two side by side
+    assert kt["evolve"][1] == 1 and kt["gather_evolve"][1] == 2 * (n - 1)
+    assert kt["weights"][1] == 2 * (n - 1) + 1 and kt["gather"][1] == 1
     assert kt["evolve"][2] + kt["gather_evolve"][2] == int(b.events().sum())
     for name in ("evolve", "weights", "gather", "gather_evolve"):
         assert kt[name][0] > 0.0
     # pop_run splits this batch (3 + 2 tiles, each at least a quarter) into two chains,
-    # each with its own [weights, fused stage] per interval; kernel_times never does
-    assert a.run_chains() == [0, 3, 5]
-    for batch, chains in ((a, 2), (b, 1)):
+    # each with its own [weights, fused stage] per interval, and kernel_times launches
+    # the same chains
+    assert a.run_chains() == [0, 3, 5] and b.run_chains() == [0, 3, 5]
+    for batch, chains in ((a, 2), (b, 2)):
         c = batch.launch_count()
         assert c["evolve"] == 1 and c["gather_evolve"] == chains * (n - 1)
         assert c["weights"] == chains * (n - 1) + 1
