@@ -66,8 +66,10 @@ extern "C" {
                           an integer in units of 2^-40 whose logarithm is known to 3e-9;
                           Upsilon = prod_hops (e^-s / rate) exp(-int (r - r') dt) of the
                           rates simulated, so the estimate is unbiased for any phi.
-                          18 <= L <= 128, and every population of the batch must be
-                          GUIDED.  phi is set by pop_set_potential (default 0) */
+                          18 <= L <= 128, every population of the batch must be
+                          GUIDED, and a GUIDED batch holds at most 65535 populations
+                          (each with 1.5 MiB of rate tables in the workspace).  phi is
+                          set by pop_set_potential (default 0) */
 
 /* clone selection (Sec. 4.1) */
 #define POP_EQ 0  /* equally spaced alpha_j, eq. (alpha-Ups) */

@@ -60,7 +60,7 @@ constexpr int kGatherWideTiles = 4096;
 struct Layout {
   int32_t P = 0, W = 0, ntiles = 0, nunits = 0;
   int64_t nslots = 0;
-  size_t o_pops, o_st, o_tile_pop, o_wtab, o_qtab, o_qm1tab, o_inv, o_logtab, o_exp2, o_A, o_S, o_cs, o_tacc, o_hist, o_tile_sum, o_tile_excl, o_beta, o_phi, o_gtab,
+  size_t o_pops, o_st, o_tile_pop, o_wtab, o_qtab, o_qm1tab, o_inv, o_logtab, o_exp2, o_A, o_S, o_cs, o_tacc, o_hist, o_tile_sum, o_tile_excl, o_beta, o_phi, o_gtab, o_gdu, o_gq,
       o_ksum, o_X, o_Y, o_KX, o_KY, o_dK, o_anc, total;
 };
 
@@ -79,7 +79,7 @@ bool valid_params(const pop_params* params, int32_t n_pops) {
     if (q.selection != POP_EQ && q.selection != POP_IID) return false;
     // GUIDED: one clone per thread with 18-site windows, and the whole batch guided
     if ((q.weight_mode == POP_GUIDED) != (params[0].weight_mode == POP_GUIDED)) return false;
-    if (q.weight_mode == POP_GUIDED && (q.L < 18 || q.L > kMaxL)) return false;
+    if (q.weight_mode == POP_GUIDED && (q.L < 18 || q.L > kMaxL || n_pops > 65535)) return false;
   }
   return true;
 }
@@ -118,6 +118,10 @@ bool make_layout(const pop_params* params, int32_t n_pops, Layout* lay) {
   l.o_ksum = take(P * sizeof(long long));
   l.o_phi = take(P * 512 * sizeof(int32_t));
   l.o_gtab = take((kGuideTabA + kGuideTabB) * sizeof(unsigned long long));
+  // GUIDED batches: the per-population bond tables (dU and its rate Q by segment)
+  const bool guided = params[0].weight_mode == POP_GUIDED;
+  l.o_gdu = take(guided ? P * kGuideSeg * sizeof(int32_t) : 0);
+  l.o_gq = take(guided ? P * kGuideSeg * sizeof(unsigned long long) : 0);
   l.o_X = take(2 * ns * (size_t)l.W * sizeof(unsigned long long));
   l.o_Y = take(ns * (size_t)l.W * sizeof(unsigned long long));
   l.o_KX = take(2 * ns * sizeof(int32_t));
@@ -199,6 +203,7 @@ struct pop_batch {
   Batch B{};
   bool any_mod = false;
   bool guided = false;       // every population GUIDED
+  bool guided_q_stale = true; // GUIDED: the rate tables need (re)building once s is fixed
   int evolve_grid = 0;
   int evolve_grid_cap = 0;  // persistent grid at full occupancy
   size_t evolve_smem = 0;
@@ -229,6 +234,18 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? POP_OK : POP_ERR_CUDA
     if (e_ != cudaSuccess) return POP_ERR_CUDA;     \
   } while (0)
 
+// GUIDED: Q(clamp(dU - s_q)) of every segment of every population, rebuilt after s is
+// fixed and after a potential changes (outside any capture: a launch of its own).
+int guided_rate_tables(pop_t* h) {
+  if (!h->guided || !h->guided_q_stale) return POP_OK;
+  const dim3 grid((unsigned)(kGuideSeg / kThreads), (unsigned)h->lay.P);
+  h->launches[POP_K_OTHER] += 1;
+  k_guided_qtab<<<grid, kThreads, 0, h->stream>>>(h->B);
+  if (cudaGetLastError() != cudaSuccess) return POP_ERR_CUDA;
+  h->guided_q_stale = false;
+  return POP_OK;
+}
+
 int fix_biases(pop_t* h, const double* s) {
   if (s == nullptr) return POP_ERR_ARG;
   for (int32_t p = 0; p < h->lay.P; ++p)
@@ -236,7 +253,7 @@ int fix_biases(pop_t* h, const double* s) {
   if (h->s_fixed) {
     for (int32_t p = 0; p < h->lay.P; ++p)
       if (s[p] != h->s[p]) return POP_ERR_STATE;
-    return POP_OK;
+    return guided_rate_tables(h);
   }
   // Fixed-point weights (64-bit): F = 61 - ceil(log2 N_c), so N_c weights of at most
   // 2^F sum to at most 2^61; wtab[k] = nearest integer to 2^F exp(-|s| k).  The psi
@@ -284,7 +301,7 @@ int fix_biases(pop_t* h, const double* s) {
   POP_CUDA(cudaStreamSynchronize(h->stream));
   h->s.assign(s, s + h->lay.P);
   h->s_fixed = true;
-  return POP_OK;
+  return guided_rate_tables(h);
 }
 
 bool valid_dt(double dt) { return std::isfinite(dt) && dt > 0.0 && dt < 1e30; }
@@ -317,7 +334,7 @@ int launch_evolve(pop_t* h, cudaStream_t st, float dt_f) {
   const size_t sm = h->evolve_smem;
   kernel_begin(h, st, POP_K_EVOLVE);
   if (h->guided) {
-    const unsigned gg = (unsigned)(h->lay.nslots / kGuideThreads);
+    const unsigned gg = (unsigned)h->lay.ntiles;
     if (h->lay.W == 1) k_evolve_guided<1><<<gg, kGuideThreads, 0, st>>>(h->B, dt_f);
     else k_evolve_guided<2><<<gg, kGuideThreads, 0, st>>>(h->B, dt_f);
   } else if (h->any_mod) {
@@ -708,6 +725,8 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
   B.beta = (unsigned int*)(ws + lay.o_beta);
   B.phi = (const int32_t*)(ws + lay.o_phi);
   B.gtab = (const unsigned long long*)(ws + lay.o_gtab);
+  B.gdu = (int32_t*)(ws + lay.o_gdu);
+  B.gq = (unsigned long long*)(ws + lay.o_gq);
   B.ksum = (long long*)(ws + lay.o_ksum);
   B.Xb[0] = (unsigned long long*)(ws + lay.o_X);
   B.Xb[1] = B.Xb[0] + lay.nslots * lay.W;
@@ -1041,6 +1060,15 @@ int pop_set_potential(pop_t* h, int32_t p, const float* h_phi) {
   }
   POP_CUDA(cudaMemcpyAsync(h->ws + h->lay.o_phi + (size_t)p * 512 * sizeof(int32_t), q.data(),
                            512 * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+  // the bond table of this population, and (once s is fixed) every rate table
+  h->launches[POP_K_OTHER] += 1;
+  k_guided_table<<<(unsigned)(kGuideSeg / kThreads), kThreads, 0, h->stream>>>(h->B, p);
+  POP_CUDA(cudaGetLastError());
+  h->guided_q_stale = true;
+  if (h->s_fixed) {
+    const int rc = guided_rate_tables(h);
+    if (rc != POP_OK) return rc;
+  }
   POP_CUDA(cudaStreamSynchronize(h->stream));
   return POP_OK;
 }

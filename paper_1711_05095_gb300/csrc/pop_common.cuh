@@ -106,6 +106,8 @@ struct Batch {
   const float* exp2tab;                 // [64] 2^(i/64) of the MODIFIED weight exponential
   const int32_t* phi;                   // GUIDED: [P][512] potential, fixed point phi 2^16
   const unsigned long long* gtab;       // GUIDED: TA[1025] then TB[2048], the rate tables
+  int32_t* gdu;                         // GUIDED: [P][2^17] dU of an active bond by its segment
+  unsigned long long* gq;               // GUIDED: [P][2^17] its rate Q(clamp(dU - s_q))
   float* Ab[2];                         // MODIFIED: rate integral, by interval parity
   unsigned long long* S;                // [iid]: exclusive prefix sums of the weights
   unsigned int* hist;                   // [P][kKcap] activity histogram (zero between intervals)

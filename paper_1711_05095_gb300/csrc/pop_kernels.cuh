@@ -939,85 +939,160 @@ __global__ void __launch_bounds__(kThreads) k_select_iid(Batch B) {
 // 2^40 exp(k 2^-17) to 3e-9 (k + 2^20 = 2^11 a + c), with the exponent
 // k_b = clamp(dU_b - s_q, +-2^20): dU_b = U(C^b) - U(C) from the ten windows that
 // contain the bond's sites (exact fixed-point integers), s_q = s in units of 2^-17.
-// One clone per thread; its exponents live in shared memory (bond-major, so the
-// threads of a warp never share a bank), with rate sums over groups of 16 bonds for
-// the bond choice.  After a hop only the 19 bonds whose windows see the two flipped
-// sites get new exponents.  Step e uses draw (e, beta, j, 5): E = -ln u(w0);
-// r'_f = float(R) 2^-40 with R = sum Q; tau = E / r'_f; the bond is the first whose
-// cumulative Q exceeds floor((w2 2^32 + w1) R / 2^64).  Log weight in FP32, every term
-// formed at its own size (no large terms that cancel):
+// dU_b depends only on the 18 sites b-8..b+9, of which sites b and b+1 differ, so it is
+// tabulated per population over the 17 free bits (k_guided_table, when the potential is
+// set), and Q(k_b) likewise once s is fixed (k_guided_qtab): a bond's rate is one load.
+// Step e uses draw (e, beta, j, 5): E = -ln u(w0); r'_f = float(R) 2^-40 with R = sum Q;
+// tau = E / r'_f; the bond is the first whose cumulative Q exceeds
+// floor((w2 2^32 + w1) R / 2^64).  Log weight in FP32, every term formed at its own size
+// (no large terms that cancel):
 //   X = sum_hops ((c_s - float(k_b + s_q) 2^-17) - eta) - sum_segments (r - r'_f) tau,
 // c_s = float(s_q 2^-17 - s), eta = (2^40 r'_f - R) / R the rounding of the total rate;
 // this is the weight of the rates simulated, so the estimate is unbiased for any
 // potential.  Requires 18 <= L <= 128.
 // ---------------------------------------------------------------------------
-constexpr int kGuideThreads = 64;
-constexpr int kGuideGroup = 16;
-constexpr int kGuideOff = INT_MIN;  // exponent slot of an inactive bond
+constexpr int kGuideThreads = 128;
+constexpr int kGuideGroup = 8;              // bonds per rate-sum group
+constexpr int kGuideSegBits = 17;
+constexpr int kGuideSeg = 1 << kGuideSegBits;
 
-// 18 sites starting at `start` (site start + k is bit k), 18 <= L, ring wrap included.
-template <int W>
-__device__ __forceinline__ uint32_t guided_seg(const unsigned long long (&x)[W], int L,
-                                               int start) {
-  if (W == 1 || L <= 64) {
-    const unsigned long long x0 = x[0];
-    const unsigned long long y = (start == 0) ? x0 : ((x0 >> start) | (x0 << (L - start)));
-    return (uint32_t)(y & 0x3FFFFull);
-  } else {
-    const unsigned long long x0 = x[0], x1 = x[W - 1];
-    auto bits_at = [&](int pos) -> unsigned long long {
-      if (pos == 0) return x0;
-      if (pos < 64) return (x0 >> pos) | (x1 << (64 - pos));
-      return x1 >> (pos - 64);
-    };
-    if (start + 18 <= L) return (uint32_t)(bits_at(start) & 0x3FFFFull);
-    const int n1 = L - start;
-    const uint32_t lo = (uint32_t)(bits_at(start) & ((1ull << n1) - 1ull));
-    const uint32_t hi = (uint32_t)(x0 & ((1ull << (18 - n1)) - 1ull));
-    return lo | (hi << n1);
-  }
+// The table index of an active bond's segment: its bits 0..8 (sites b-8..b) and
+// 10..17 (sites b+2..b+9); bit 9 (site b+1) is the complement of bit 8.
+__device__ __forceinline__ uint32_t guided_index(uint32_t seg) {
+  return (seg & 0x1FFu) | ((seg >> 10) << 9);
 }
 
-// Rate exponent of the hop across active bond b.
-template <int W>
-__device__ __forceinline__ int guided_k(const unsigned long long (&x)[W], int L, int b,
-                                        const int32_t* phi, int s_q) {
-  int start = b - 8;
-  if (start < 0) start += L;
-  const uint32_t seg = guided_seg<W>(x, L, start);
-  const uint32_t seg2 = seg ^ (3u << 8);
-  int dU = 0;
-#pragma unroll
-  for (int m = 0; m < 10; ++m) dU += phi[(seg2 >> m) & 511u] - phi[(seg >> m) & 511u];
-  return min(max(dU - s_q, -kGuideKmax), kGuideKmax);
-}
-
-// Q(k) = floor(TA[a] TB[c] / 2^44); 0 for an inactive bond.
+// Q(k) = floor(TA[a] TB[c] / 2^44).
 __device__ __forceinline__ unsigned long long guided_q(int k, const unsigned long long* tab) {
-  if (k == kGuideOff) return 0ull;
   const uint32_t u = (uint32_t)(k + kGuideKmax);
   const unsigned long long ta = __ldg(tab + (u >> 11)), tb = __ldg(tab + kGuideTabA + (u & 2047u));
   return (__umul64hi(ta, tb) << 20) | ((ta * tb) >> 44);
 }
 
+// dU of the active bond whose segment has table index i, population p.
+__global__ void __launch_bounds__(kThreads) k_guided_table(Batch B, int p) {
+  const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
+  if (i >= (uint32_t)kGuideSeg) return;
+  const uint32_t b8 = (i >> 8) & 1u;
+  const uint32_t seg = (i & 0x1FFu) | ((b8 ^ 1u) << 9) | ((i >> 9) << 10);
+  const uint32_t seg2 = seg ^ (3u << 8);
+  const int32_t* phi = B.phi + (size_t)p * 512;
+  int dU = 0;
+#pragma unroll
+  for (int m = 0; m < 10; ++m) dU += phi[(seg2 >> m) & 511u] - phi[(seg >> m) & 511u];
+  B.gdu[(size_t)p * kGuideSeg + i] = dU;
+}
+
+// Q(clamp(dU - s_q)) of every table index of every population (s fixed for the run).
+__global__ void __launch_bounds__(kThreads) k_guided_qtab(Batch B) {
+  const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
+  const int p = (int)blockIdx.y;
+  const int s_q = B.pops[p].s_q;
+  const size_t at = (size_t)p * kGuideSeg + i;
+  const int k = min(max(B.gdu[at] - s_q, -kGuideKmax), kGuideKmax);
+  B.gq[at] = guided_q(k, B.gtab);
+}
+
+// Sites start, start+1, ..., start+63 (mod L) of a configuration as the bits of one
+// word (bit k = site (start + k) mod L), 18 <= L, 0 <= start < L; bits of x at or
+// above L are zero.
 template <int W>
-__global__ void __launch_bounds__(kGuideThreads) k_evolve_guided(Batch B, float dt_f) {
-  __shared__ int32_t s_phi[512];
-  __shared__ float2 s_log[64];
-  // exponents and group sums of nb = 64 W bonds, the bonds a lattice of W words holds
-  // (a one-word batch keeps half the shared memory per block, so twice the warps)
+__device__ __forceinline__ unsigned long long ring_window(const unsigned long long (&x)[W], int L,
+                                                         int start) {
+  if (W == 1 || L <= 64) {
+    const unsigned long long x0 = x[0];
+    unsigned long long y = (start == 0) ? x0 : ((x0 >> start) | (x0 << (L - start)));
+    if (L < 64) {
+      y &= (1ull << L) - 1ull;
+      y |= y << L;                       // 2L >= 36 sites
+      if (2 * L < 64) y |= y << (2 * L);  // 4L >= 72 sites
+    }
+    return y;
+  } else {
+    const unsigned long long x0 = x[0], x1 = x[W - 1];
+    unsigned long long y = (start == 0) ? x0 : (start < 64 ? ((x0 >> start) | (x1 << (64 - start)))
+                                                           : (x1 >> (start - 64)));
+    const int valid = L - start;  // sites before the wrap to site 0
+    if (valid < 64) y |= x0 << valid;
+    return y;
+  }
+}
+
+// Rate of the bond whose 18-site segment starts at bit o of window v (its sites at bits
+// o + 8 and o + 9): Q from the table if they differ, else 0.  PRED: load only for an
+// active bond (measured faster for two-word lattices); otherwise load in any case and
+// select, which keeps more loads in flight (faster for one-word lattices).
+template <bool PRED>
+__device__ __forceinline__ unsigned long long guided_q_at(unsigned long long v, int o,
+                                                          const unsigned long long* qtab) {
+  const uint32_t seg = (uint32_t)(v >> o) & 0x3FFFFu;
+  const bool act = ((seg >> 8) ^ (seg >> 9)) & 1u;
+  if constexpr (PRED) {
+    unsigned long long q = 0ull;
+    if (act) q = __ldg(qtab + guided_index(seg));
+    return q;
+  } else {
+    const unsigned long long q = __ldg(qtab + guided_index(seg));
+    return act ? q : 0ull;
+  }
+}
+
+// float(v) rounded to nearest (ties to even) for a 64-bit unsigned v, in 32-bit integer
+// arithmetic (the 64-bit integer <-> float conversions run on the narrow FP64 pipe):
+// the 24 leading bits, rounded by the bits below them.
+__device__ __forceinline__ float u64_to_float_rn(unsigned long long v) {
+  if ((v >> 24) == 0ull) return __uint2float_rn((uint32_t)v);  // exact
+  const int p = 63 - __clzll((long long)v);                        // leading one, >= 24
+  const int sh = p - 23;
+  uint32_t m = (uint32_t)(v >> sh);                                // 24 bits
+  const unsigned long long rest = v & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+  m += (rest > half || (rest == half && (m & 1u))) ? 1u : 0u;
+  int e = p;
+  if (m == (1u << 24)) { m >>= 1; ++e; }
+  return __uint_as_float(((uint32_t)(e + 127) << 23) | (m & 0x007fffffu));
+}
+
+// The integer value of a float that holds an integer in [1, 2^64): mantissa shifted.
+__device__ __forceinline__ unsigned long long float_to_u64_exact(float f) {
+  const uint32_t bits = __float_as_uint(f);
+  const int e = (int)((bits >> 23) & 0xffu) - 127;
+  const unsigned long long m = (unsigned long long)((bits & 0x007fffffu) | 0x00800000u);
+  return e >= 23 ? m << (e - 23) : m >> (23 - e);
+}
+
+__device__ __forceinline__ float i64_to_float_rn(long long v) {
+  if (v >= -2147483647ll && v <= 2147483647ll) return __int2float_rn((int)v);
+  const float f = u64_to_float_rn(v < 0 ? (unsigned long long)(-v) : (unsigned long long)v);
+  return v < 0 ? -f : f;
+}
+
+// One lane per clone; a lane whose clone has ended takes the next clone of the block's
+// tile.  The rate sums of a clone's groups of eight bonds live in shared memory
+// (group-major: the lanes of a warp never share a bank); a newly taken clone's sums
+// are formed by the whole warp (each lane four or two bonds), so refills stay uniform.
+#ifndef POP_GUIDE_MIN_BLOCKS
+#define POP_GUIDE_MIN_BLOCKS 5   // two-word lattices: up to 96 registers
+#endif
+#ifndef POP_GUIDE1_MIN_BLOCKS
+#define POP_GUIDE1_MIN_BLOCKS 1  // one-word lattices: every table load of a re-rate in flight
+#endif
+template <int W>
+__global__ void __launch_bounds__(kGuideThreads, W == 1 ? POP_GUIDE1_MIN_BLOCKS : POP_GUIDE_MIN_BLOCKS)
+    k_evolve_guided(Batch B, float dt_f) {
   constexpr int nb = 64 * W, ng = nb / kGuideGroup;
-  __shared__ int32_t s_k[nb][kGuideThreads];
+  constexpr int BPL = nb / 32;  // bonds per lane in the cooperative sums
   __shared__ unsigned long long s_g[ng][kGuideThreads];
+  __shared__ float2 s_log[64];
+  __shared__ int s_take;
   __shared__ int s_min, s_max, s_amin, s_amax;
   __shared__ unsigned int s_ev;
-  const int tid = threadIdx.x;
-  const int64_t slot0 = (int64_t)blockIdx.x * kGuideThreads;
-  const int p = B.tile_pop[slot0 / kTile];
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int tile = blockIdx.x;
+  const int p = B.tile_pop[tile];
   const PopDesc d = B.pops[p];
-  for (int i = tid; i < 512; i += kGuideThreads) s_phi[i] = B.phi[(size_t)p * 512 + i];
-  s_log[tid] = B.logtab[tid];
+  if (tid < 64) s_log[tid] = B.logtab[tid];
   if (tid == 0) {
+    s_take = 0;
     s_min = INT_MAX;
     s_max = INT_MIN;
     s_amin = INT_MAX;
@@ -1027,99 +1102,183 @@ __global__ void __launch_bounds__(kGuideThreads) k_evolve_guided(Batch B, float 
   __syncthreads();
   const uint32_t beta = *B.beta;
   const int par = (int)(beta & 1u);
-  const int64_t slot = slot0 + tid;
-  const int64_t j = slot - d.off;
+  const int64_t base = (int64_t)tile * kTile;
+  const int n = (int)min((int64_t)kTile, d.nc - (base - d.off));  // clones of this tile
   const int L = d.L;
-  const unsigned long long* tab = B.gtab;
-  if (j < d.nc) {
-    unsigned long long x[W];
-    load_lat<W>(B.Y, slot, x);
-    const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
-    // exponents and rates of every bond, group sums, total
-    unsigned long long a[W];
-    active_bonds<W>(x, L, a);
-    int r = popc_lat<W>(a);
-    unsigned long long R = 0ull;
-    for (int g = 0; g < ng; ++g) {
-      unsigned long long gs = 0ull;
-      for (int b = g * kGuideGroup; b < (g + 1) * kGuideGroup; ++b) {
-        int k = kGuideOff;
-        if (b < L && ((a[b >> 6] >> (b & 63)) & 1ull)) k = guided_k<W>(x, L, b, s_phi, d.s_q);
-        s_k[b][tid] = k;
-        gs += guided_q(k, tab);
+  const unsigned long long* const qtab = B.gq + (size_t)p * kGuideSeg;
+  const int32_t* const dtab = B.gdu + (size_t)p * kGuideSeg;
+  const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
+  const unsigned int lt_mask = (1u << lane) - 1u;
+  int cl = -1;  // the lane's clone (offset in the tile), -1 when it has none
+  unsigned long long x[W], a[W];
+  unsigned long long R = 0ull;
+  int r = 0, h = 0;
+  uint32_t e = 0u;
+  float t = 0.0f, a_r = 0.0f, a_h = 0.0f;
+  int hmin = INT_MAX, hmax = INT_MIN, xmin = INT_MAX, xmax = INT_MIN;
+  unsigned int ev = 0u;
+#pragma unroll
+  for (int w = 0; w < W; ++w) x[w] = a[w] = 0ull;
+  for (;;) {
+    const unsigned int m = __ballot_sync(0xffffffffu, cl < 0);
+    int taken = 0;
+    if (lane == 0) taken = *(volatile int*)&s_take;
+    taken = __shfl_sync(0xffffffffu, taken, 0);
+    if (m != 0u && taken < n) {
+      int base_i = 0;
+      if (lane == 0) base_i = atomicAdd(&s_take, __popc(m));
+      base_i = __shfl_sync(0xffffffffu, base_i, 0);
+      const int idx = base_i + __popc(m & lt_mask);
+      const bool got = cl < 0 && idx < n;
+      if (got) {
+        cl = idx;
+        load_lat<W>(B.Y, base + idx, x);
+        active_bonds<W>(x, L, a);
+        r = popc_lat<W>(a);
+        h = 0;
+        e = 0u;
+        t = a_r = a_h = 0.0f;
       }
-      s_g[g][tid] = gs;
-      R += gs;
+      // the rate sums of every new clone, one clone at a time by the whole warp
+      unsigned int todo = __ballot_sync(0xffffffffu, got);
+      while (todo != 0u) {
+        const int o = __ffs(todo) - 1;
+        todo &= todo - 1u;
+        unsigned long long xo[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) xo[w] = __shfl_sync(0xffffffffu, x[w], o);
+        // the lane's bonds b0 .. b0 + BPL - 1 (those below L): segments from one window
+        const int b0 = lane * BPL;
+        unsigned long long v = 0ull;
+        if (b0 < L) {
+          const int st0 = b0 >= 8 ? b0 - 8 : b0 - 8 + L;
+          const unsigned long long win = ring_window<W>(xo, L, st0);
+#pragma unroll
+          for (int i = 0; i < BPL; ++i)
+            if (b0 + i < L) v += guided_q_at<W == 2>(win, i, qtab);
+        }
+        // a group of eight bonds spans 8 / BPL lanes
+#pragma unroll
+        for (int off = 1; off < kGuideGroup / BPL; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane % (kGuideGroup / BPL) == 0) s_g[lane / (kGuideGroup / BPL)][(tid & ~31) + o] = v;
+#pragma unroll
+        for (int off = kGuideGroup / BPL; off < 32; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == o) R = v;
+      }
+      __syncwarp();
     }
-    float t = 0.0f, a_r = 0.0f, a_h = 0.0f;
-    int h = 0;
-    for (uint32_t e = 0;; ++e) {
-      if (r == 0) break;
-      if (e >= kStepLimit) {  // guard: an interval must end; report, never spin
-        B.st[p].err = kErrRange;
-        break;
-      }
-      const float Rf = __ull2float_rn(R);
+    if (__ballot_sync(0xffffffffu, cl >= 0) == 0u) {
+      if (lane == 0) taken = *(volatile int*)&s_take;
+      if (__shfl_sync(0xffffffffu, taken, 0) >= n) break;
+      continue;
+    }
+    if (cl >= 0) {
+      const uint32_t j = (uint32_t)(base - d.off + cl);
+      const float Rf = u64_to_float_rn(R);
       const float rp = __fmul_rn(Rf, 0x1p-40f);
-      const long long D = (long long)(__float2ull_rz(Rf) - R);
-      const float eta = __fdiv_rn(__ll2float_rn(D), Rf);
+      const long long D = (long long)(float_to_u64_exact(Rf) - R);
+      const float eta = __fdiv_rn(i64_to_float_rn(D), Rf);
       const float dr = __fsub_rn(__int2float_rn(r), rp);
-      const uint4 w = philox4x32_10(make_uint4(e, beta, (uint32_t)j, kTagGuided), k0, k1);
+      const uint4 w = philox4x32_10(make_uint4(e, beta, j, kTagGuided), k0, k1);
       const float E = neg_ln_u(w.x, s_log);
       const float tau = __fdiv_rn(E, rp);
       const float t_new = __fadd_rn(t, tau);
-      if (t_new >= dt_f) {
+      bool run = r != 0;
+      if (run && e >= kStepLimit) {  // guard: an interval must end; report, never spin
+        B.st[p].err = kErrRange;
+        run = false;
+      }
+      if (run && t_new >= dt_f) {
         a_r = __fmaf_rn(dr, __fsub_rn(dt_f, t), a_r);
-        break;
+        run = false;
       }
-      a_r = __fmaf_rn(dr, tau, a_r);
-      t = t_new;
-      const unsigned long long kk = __umul64hi(((unsigned long long)w.z << 32) | w.y, R);
-      // the first bond whose inclusive cumulative rate exceeds kk (kk < R = the sum of
-      // the group sums, so both loops stop inside the arrays; the bounds make it explicit)
-      unsigned long long cum = 0ull;
-      int g = 0;
-      while (g < ng - 1 && cum + s_g[g][tid] <= kk) {
-        cum += s_g[g][tid];
-        ++g;
-      }
-      int b = g * kGuideGroup;
-      for (; b < nb - 1; ++b) {
-        cum += guided_q(s_k[b][tid], tab);
-        if (cum > kk) break;
-      }
-      const int kb = s_k[b][tid];
-      a_h = __fadd_rn(a_h, __fsub_rn(__fsub_rn(d.c_s, __fmul_rn(__int2float_rn(kb + d.s_q), 0x1p-17f)),
-                                     eta));
-      hop<W>(x, b, L);
-      ++h;
-      active_bonds<W>(x, L, a);
-      r = popc_lat<W>(a);
-      // new exponents for the bonds whose windows contain site b or b+1
-      for (int db = -9; db <= 9; ++db) {
-        int c = b + db;
-        if (c < 0) c += L;
-        if (c >= L) c -= L;
-        const int kn = ((a[c >> 6] >> (c & 63)) & 1ull) ? guided_k<W>(x, L, c, s_phi, d.s_q) : kGuideOff;
-        const int ko = s_k[c][tid];
-        if (kn != ko) {
-          s_k[c][tid] = kn;
-          const unsigned long long qn = guided_q(kn, tab), qo = guided_q(ko, tab);
-          s_g[c / kGuideGroup][tid] += qn - qo;
-          R += qn - qo;
+      if (run) {
+        a_r = __fmaf_rn(dr, tau, a_r);
+        t = t_new;
+        const unsigned long long kk = __umul64hi(((unsigned long long)w.z << 32) | w.y, R);
+        // the first bond whose inclusive cumulative rate exceeds kk < R: the group from the
+        // group sums, then the bond inside it (the last group if the sums run out first)
+        unsigned long long cum = 0ull;
+        int g = ng - 1;
+        bool found = false;
+#pragma unroll
+        for (int gg = 0; gg < ng - 1; ++gg) {
+          const unsigned long long v = s_g[gg][tid];
+          if (!found) {
+            if (cum + v <= kk) cum += v;
+            else { found = true; g = gg; }
+          }
+        }
+        const int gb = g * kGuideGroup;  // < L: the group holds the bond kk falls on
+        const unsigned long long gwin = ring_window<W>(x, L, gb >= 8 ? gb - 8 : gb - 8 + L);
+        int b = gb + kGuideGroup - 1;
+        uint32_t bseg = 0u;
+        found = false;
+#pragma unroll
+        for (int i = 0; i < kGuideGroup; ++i) {
+          const unsigned long long q = gb + i < L ? guided_q_at<W == 2>(gwin, i, qtab) : 0ull;
+          if (!found) {
+            cum += q;
+            if (cum > kk) {
+              found = true;
+              b = gb + i;
+              bseg = (uint32_t)(gwin >> i) & 0x3FFFFu;
+            }
+          }
+        }
+        const int kb = min(max(__ldg(dtab + guided_index(bseg)) - d.s_q, -kGuideKmax), kGuideKmax);
+        a_h = __fadd_rn(a_h, __fsub_rn(__fsub_rn(d.c_s, __fmul_rn(__int2float_rn(kb + d.s_q), 0x1p-17f)), eta));
+        // the bonds b-9 .. b+9, whose windows contain site b or b+1, change rate: their
+        // segments (sites b-17 .. b+18) from one window before and one after the hop
+        const int ws = b >= 17 ? b - 17 : b - 17 + L;
+        const unsigned long long wo = ring_window<W>(x, L, ws);
+        hop<W>(x, b, L);
+        ++h;
+        active_bonds<W>(x, L, a);
+        r = popc_lat<W>(a);
+        const unsigned long long wn = ring_window<W>(x, L, ws);
+#pragma unroll
+        for (int db = -9; db <= 9; ++db) {
+          if (db == 9 && L <= 18) continue;  // on 18 sites bond b+9 is bond b-9
+          int c = b + db;
+          if (c < 0) c += L;
+          if (c >= L) c -= L;
+          const unsigned long long qo = guided_q_at<W == 2>(wo, db + 9, qtab);
+          const unsigned long long qn = guided_q_at<W == 2>(wn, db + 9, qtab);
+          if (qn != qo) {
+            s_g[c / kGuideGroup][tid] += qn - qo;
+            R += qn - qo;
+          }
         }
       }
+      ++e;
+      if (!run) {
+        const float X = __fsub_rn(a_h, a_r);
+        const int64_t slot = base + cl;
+        store_lat<W>(B.Xb[par], slot, x);
+        B.KXb[par][slot] = B.KY[slot] + h;
+        B.dKb[par][slot] = h;
+        B.Ab[par][slot] = X;
+        hmin = min(hmin, h);
+        hmax = max(hmax, h);
+        ev += (unsigned int)h;
+        xmin = min(xmin, float_order(X));
+        xmax = max(xmax, float_order(X));
+        cl = -1;
+      }
     }
-    const float X = __fsub_rn(a_h, a_r);
-    store_lat<W>(B.Xb[par], slot, x);
-    B.KXb[par][slot] = B.KY[slot] + h;
-    B.dKb[par][slot] = h;
-    B.Ab[par][slot] = X;
-    atomicMin(&s_min, h);
-    atomicMax(&s_max, h);
-    atomicAdd(&s_ev, (unsigned int)h);
-    atomicMin(&s_amin, float_order(X));
-    atomicMax(&s_amax, float_order(X));
+  }
+  hmin = __reduce_min_sync(0xffffffffu, hmin);
+  hmax = __reduce_max_sync(0xffffffffu, hmax);
+  ev = __reduce_add_sync(0xffffffffu, ev);
+  xmin = __reduce_min_sync(0xffffffffu, xmin);
+  xmax = __reduce_max_sync(0xffffffffu, xmax);
+  if (lane == 0 && hmin != INT_MAX) {
+    atomicMin(&s_min, hmin);
+    atomicMax(&s_max, hmax);
+    atomicAdd(&s_ev, ev);
+    atomicMin(&s_amin, xmin);
+    atomicMax(&s_amax, xmax);
   }
   __syncthreads();
   if (tid == 0 && s_min != INT_MAX) {
