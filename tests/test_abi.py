@@ -55,8 +55,12 @@ def test_workspace_bytes(lib):
     assert pg.workspace_bytes([P(L=129, N=64, weight_mode=G)]) == 0
     assert pg.workspace_bytes([P(weight_mode=G), P()]) == 0
     assert pg.workspace_bytes([P(), P(weight_mode=G)]) == 0
-    # the potential table is part of the workspace
-    assert pg.workspace_bytes([P(weight_mode=G)]) == pg.workspace_bytes([P()])
+    # a GUIDED population adds its bond tables: dU (int32) and the rate Q (uint64) of
+    # each of the 2^17 segments of an active bond
+    per_pop = (1 << 17) * (4 + 8)
+    assert pg.workspace_bytes([P(weight_mode=G)]) == pg.workspace_bytes([P()]) + per_pop
+    assert (pg.workspace_bytes([P(weight_mode=G), P(weight_mode=G, seed=2)])
+            == pg.workspace_bytes([P(), P(seed=2)]) + 2 * per_pop)
 
 
 def test_init_rejects_bad_arguments_without_device(lib):
