@@ -55,6 +55,19 @@ UNIT = "events/s"
 #   loop bookkeeping (step and hop counters, exit test)                         = 3
 OPS_HOP = 49 + 20 + 4 + 7 + 25 + 7 + 3          # a step that hops: 115
 OPS_STOP = OPS_HOP - 25 - 7 - 1                 # the step that ends the interval: 82
+# The same step on a two-word (65..128-site) lattice, in 32-bit operations:
+#   active bonds and rate: rotate-by-one of four words with the wrap at L (10), xor of
+#     four words (4), popc of four words and their sum (7), r == 0 test (1)    = 22
+#   bond choice: multiply-high (1), k-th set bit of 128 bits (7 levels x 4)   = 29
+#   hop: b+1 mod L (3), the two bits' word masks (6), xor of four words (4)     = 13
+OPS_HOP_W2 = 49 + 20 + 4 + 22 + 29 + 13 + 3     # 140
+OPS_STOP_W2 = OPS_HOP_W2 - 29 - 13 - 1          # 97
+
+
+def step_ops(W):
+    """(operations of a step that hops, of the step that ends the interval) for a
+    batch of W-word lattices."""
+    return (OPS_HOP, OPS_STOP) if W == 1 else (OPS_HOP_W2, OPS_STOP_W2)
 # Cloning stage, per old clone ([eq], Sec. 2.3): weight = table[|dK - k_ref|] (3),
 # its prefix sum (2), the inverse j_lo of the prefix by 128-bit products and compares
 # (16), and for the new clone the ancestor lookup and its lattice and K (3)
@@ -90,6 +103,8 @@ def parse():
     ap.add_argument("--kernel-intervals", type=int, default=100)
     ap.add_argument("--config5", action="store_true",
                     help="the learned-potential study at full size instead of the bench line")
+    ap.add_argument("--selection-study", action="store_true",
+                    help="the cloning-interval and selection study (Sec. 4.3) instead of the bench line")
     return ap.parse_args()
 
 
@@ -345,12 +360,68 @@ def config5(args):
     print(json.dumps(out), flush=True)
 
 
+def selection_study(args):
+    """The cloning interval and the selection method (Sec. 4.3, Fig. Tau; Sec. 4.4): at
+    lambda = 28 on rings of L = 20 and 50 (N = L/2), t_obs = 10^4, N_c = 2^16, for
+    dt in {0.1, 0.3, 1, 3, 10}, [eq] against [iid] selection, each with plain and
+    MODIFIED weights, 16 seeds each: the mean and spread of k_hat (eq. khat) and
+    psi_hat (eq. psihat), the [eq]/[iid] variance ratio of k_hat, and the device time.
+    The paper's own runs at this state point extrapolate to k_inf = 0.3433-0.3437 (L = 20)
+    and 0.3620-0.3666 (L = 50) (its Table of fits in t_obs, N_c = 10^5)."""
+    import torch
+    import paper_1711_05095_gb300 as pg
+    from paper_1711_05095_gb300 import build as pbuild
+    pbuild.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    lam, t_obs, nc, seeds = 28.0, 1.0e4, 1 << 16, 16
+    rows = []
+    for L in (20, 50):
+        s = lam / L ** 2
+        for dt in (0.1, 0.3, 1.0, 3.0, 10.0):
+            M = int(round(t_obs / dt))
+            for sel_name, sel in (("eq", pg.POP_EQ), ("iid", pg.POP_IID)):
+                pops = [dict(L=L, N=L // 2, n_clones=nc, seed=800000 + 100000 * L + 1000 * int(10 * dt) + r + 50 * m,
+                             weight_mode=wm, selection=sel)
+                        for m, wm in enumerate((pg.POP_PLAIN, pg.POP_MODIFIED)) for r in range(seeds)]
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                b = pg.PopulationBatch(pops, device=dev, stream=stream)
+                b.run(dt, [s] * len(pops), M)
+                psi, kh, _ = b.estimate_psi()
+                e1.record(stream)
+                e1.synchronize()
+                sec = e0.elapsed_time(e1) / 1e3
+                b.close()
+                for m, wname in enumerate(("plain", "modified")):
+                    k = kh[m * seeds:(m + 1) * seeds]
+                    ps = psi[m * seeds:(m + 1) * seeds]
+                    rows.append(dict(L=L, dt=dt, selection=sel_name, weights=wname, intervals=M,
+                                     k_mean=float(np.mean(k)), k_std=float(np.std(k, ddof=1)),
+                                     psi_mean=float(np.mean(ps)), psi_std=float(np.std(ps, ddof=1)),
+                                     batch_seconds=sec))
+    ratios = []
+    for L in (20, 50):
+        for dt in (0.1, 0.3, 1.0, 3.0, 10.0):
+            for wname in ("plain", "modified"):
+                eq = [r for r in rows if (r["L"], r["dt"], r["selection"], r["weights"]) == (L, dt, "eq", wname)][0]
+                iid = [r for r in rows if (r["L"], r["dt"], r["selection"], r["weights"]) == (L, dt, "iid", wname)][0]
+                ratios.append(dict(L=L, dt=dt, weights=wname, var_ratio_eq_over_iid=(eq["k_std"] / iid["k_std"]) ** 2))
+    out = {"kind": "cloning interval and selection study", "lambda": lam, "t_obs": t_obs, "n_clones": nc,
+           "seeds": seeds, "rows": rows, "variance_ratios": ratios,
+           "paper_k_inf": {"20": [0.3433, 0.3437], "50": [0.3620, 0.3666]}}
+    print(json.dumps(out), flush=True)
+
+
 # ---------------------------------------------------------------------------
 def main():
     args = parse()
     world, rank, local = dist_setup()
     if args.config5:
         return config5(args)
+    if args.selection_study:
+        return selection_study(args)
     w = workloads.large_population()
     if args.impl == "reference":
         return reference_arm(args, w, rank)
@@ -444,13 +515,16 @@ def main():
     torch.cuda.nvtx.range_pop()
     t_k_us, n_k, hops_k = kt["gather_evolve"]
     t_k = t_k_us / 1e6
-    ops_per_launch = OPS_HOP * hops_k / R + (OPS_STOP + OPS_GATHER) * clones
+    ops_hop, ops_stop = step_ops(pg.lattice_words(pops))
+    ops_per_launch = ops_hop * hops_k / R + (ops_stop + OPS_GATHER) * clones
     peaks, peak_kind = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_gops = n_sm * ISSUE_OPS_PER_SM_CLK * sm_max * 1e6 / 1e9
     achieved = ops_per_launch / t_k / 1e9
-    ops_run = OPS_HOP * ev_total + (OPS_STOP + OPS_GATHER) * clones * block * args.steps
+    ops_run = ops_hop * ev_total + (ops_stop + OPS_GATHER) * clones * block * args.steps
+    # the same with the one-word step count, for comparison with earlier figures
+    ops_run_w1 = OPS_HOP * ev_total + (OPS_STOP + OPS_GATHER) * clones * block * args.steps
     achieved_run = ops_run / (sum(ms) / 1e3) / 1e9
     per_interval_us = {k: v[0] for k, v in kt.items() if v[1]}
     counters_valid = KERNEL_TRAFFIC is not None and kernel_sources_digest() == KERNEL_TRAFFIC["sources"]
@@ -574,7 +648,9 @@ def main():
                      "launches_from": "pop_kernel_times: the launch sequence of pop_run for this batch "
                                       "(%d chain%s), continuing the timed run" % (n_chains, "s" if n_chains > 1 else ""),
                      "dominant_ms_per_step": t_k_us * block / 1e3,
-                     "achieved_in_run": achieved_run, "frac_in_run": achieved_run / peak_gops},
+                     "achieved_in_run": achieved_run, "frac_in_run": achieved_run / peak_gops,
+                     "ops_per_hop_step": ops_hop, "ops_per_end_step": ops_stop, "ops_per_clone_cloning": OPS_GATHER,
+                     "frac_in_run_one_word_count": ops_run_w1 / (sum(ms) / 1e3) / 1e9 / peak_gops},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "step": "pop_init + pop_set_state of every population from pinned host memory + %d intervals "
                         "+ pop_estimate_psi (wall clock; the 32 populations start from the same host "

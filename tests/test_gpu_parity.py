@@ -319,6 +319,17 @@ def test_parity_mixed_modes_batch(pg):
     run_parity(pg, pops, [0.1, -0.05, 0.02, 0.3], 0.1, 4)
 
 
+@pytest.mark.parametrize("L,dt", [(20, 10.0), (50, 1.0), (50, 10.0)])
+def test_selection_study_state_point_matches_oracle(pg, L, dt):
+    # the cloning-interval and selection study's configuration (lambda = 28, [eq] and
+    # [iid], plain and MODIFIED weights in one batch, long intervals with wide activity
+    # spreads), truncated to a few intervals: bit for bit against the oracle
+    s = 28.0 / L ** 2
+    pops = [dict(L=L, N=L // 2, n_clones=2100, seed=70 + 10 * m + e, weight_mode=m, selection=e)
+            for m in (0, MOD) for e in (0, IID)]
+    run_parity(pg, pops, [s] * 4, dt, 3)
+
+
 @pytest.mark.parametrize("L,N,nc,W_case", [(50, 25, 2500, 1), (100, 50, 1300, 2), (300, 90, 700, 0)])
 def test_density_mode_matches_oracle(pg, L, N, nc, W_case):
     q = dict(L=L, N=N, n_clones=nc, seed=31 + L)
