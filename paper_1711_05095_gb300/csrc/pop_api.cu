@@ -18,6 +18,7 @@
 // population its cloning stage is still reading.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -60,7 +61,7 @@ constexpr int kGatherWideTiles = 4096;
 struct Layout {
   int32_t P = 0, W = 0, ntiles = 0, nunits = 0;
   int64_t nslots = 0;
-  size_t o_pops, o_st, o_tile_pop, o_wtab, o_qtab, o_qm1tab, o_inv, o_logtab, o_exp2, o_A, o_S, o_cs, o_tacc, o_hist, o_tile_sum, o_tile_excl, o_beta, o_phi, o_gtab, o_gdu, o_gq,
+  size_t o_pops, o_st, o_tile_pop, o_wtab, o_qtab, o_qm1tab, o_inv, o_logtab, o_exp2, o_A, o_S, o_cs, o_tacc, o_hist, o_tile_sum, o_tile_excl, o_beta, o_phi, o_gtab, o_gdu, o_gq, o_gcar,
       o_ksum, o_X, o_Y, o_KX, o_KY, o_dK, o_anc, total;
 };
 
@@ -122,6 +123,7 @@ bool make_layout(const pop_params* params, int32_t n_pops, Layout* lay) {
   const bool guided = params[0].weight_mode == POP_GUIDED;
   l.o_gdu = take(guided ? P * kGuideSeg * sizeof(int32_t) : 0);
   l.o_gq = take(guided ? P * kGuideSeg * sizeof(unsigned long long) : 0);
+  l.o_gcar = take(guided ? 2 * ns * (size_t)(8 * l.W) * sizeof(unsigned long long) : 0);
   l.o_X = take(2 * ns * (size_t)l.W * sizeof(unsigned long long));
   l.o_Y = take(ns * (size_t)l.W * sizeof(unsigned long long));
   l.o_KX = take(2 * ns * sizeof(int32_t));
@@ -727,6 +729,8 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
   B.gtab = (const unsigned long long*)(ws + lay.o_gtab);
   B.gdu = (int32_t*)(ws + lay.o_gdu);
   B.gq = (unsigned long long*)(ws + lay.o_gq);
+  B.gcar[0] = (unsigned long long*)(ws + lay.o_gcar);
+  B.gcar[1] = B.gcar[0] + (size_t)lay.nslots * (8 * lay.W);
   B.ksum = (long long*)(ws + lay.o_ksum);
   B.Xb[0] = (unsigned long long*)(ws + lay.o_X);
   B.Xb[1] = B.Xb[0] + lay.nslots * lay.W;
@@ -1060,6 +1064,10 @@ int pop_set_potential(pop_t* h, int32_t p, const float* h_phi) {
   }
   POP_CUDA(cudaMemcpyAsync(h->ws + h->lay.o_phi + (size_t)p * 512 * sizeof(int32_t), q.data(),
                            512 * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+  // the clones' carried rate sums were those of the old potential
+  const int32_t zero = 0;
+  POP_CUDA(cudaMemcpyAsync(h->ws + h->lay.o_st + (size_t)p * sizeof(PopState) + offsetof(PopState, gcarry),
+                           &zero, sizeof zero, cudaMemcpyHostToDevice, h->stream));
   // the bond table of this population, and (once s is fixed) every rate table
   h->launches[POP_K_OTHER] += 1;
   k_guided_table<<<(unsigned)(kGuideSeg / kThreads), kThreads, 0, h->stream>>>(h->B, p);
@@ -1239,10 +1247,13 @@ int pop_autotune(pop_t* h, double dt, const double* s, int32_t trials, int32_t* 
                          ? POP_OK : POP_ERR_CUDA;
             if (lr == POP_OK) lr = launch_evolve(h, h->stream, dt_f);
             if (lr == POP_OK) lr = launch_resample(h, h->stream);
-            if (lr == POP_OK) {  // the next repetition evolves interval 1 again
+            if (lr == POP_OK) {  // the next repetition evolves interval 1 again, from the start
               for (int c = 0; c <= kMaxChains && lr == POP_OK; ++c)
                 if (cudaMemcpyAsync(h->B.beta + c, &beta1, sizeof beta1, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
                   lr = POP_ERR_CUDA;
+              if (lr == POP_OK && cudaMemcpyAsync(h->ws + h->lay.o_st, saved.data(), saved.size() * sizeof(PopState),
+                                                  cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+                lr = POP_ERR_CUDA;
             }
             return lr;
           }, trials, &ms);

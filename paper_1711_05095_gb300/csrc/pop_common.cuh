@@ -90,7 +90,9 @@ struct PopState {
                                // (float bits, A >= 0)
   float a_ref;                 // MODIFIED: reference A of this interval (k_weights)
   uint32_t beta;               // interval being resampled (k_weights)
-  int32_t pad;
+  int32_t gcarry;              // GUIDED: the clones' rate sums of the last interval are
+                               // carried (set by the cloning stage, cleared by the host
+                               // when the potential changes)
   unsigned long long T;        // total weight of this interval (k_tile_scan or k_gather)
 };
 
@@ -108,6 +110,8 @@ struct Batch {
   const unsigned long long* gtab;       // GUIDED: TA[1025] then TB[2048], the rate tables
   int32_t* gdu;                         // GUIDED: [P][2^17] dU of an active bond by its segment
   unsigned long long* gq;               // GUIDED: [P][2^17] its rate Q(clamp(dU - s_q))
+  unsigned long long* gcar[2];          // GUIDED: each clone's final rate sums [slots][8 W], by
+                                        // interval parity
   float* Ab[2];                         // MODIFIED: rate integral, by interval parity
   unsigned long long* S;                // [iid]: exclusive prefix sums of the weights
   unsigned int* hist;                   // [P][kKcap] activity histogram (zero between intervals)

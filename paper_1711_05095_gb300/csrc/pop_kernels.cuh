@@ -876,6 +876,9 @@ __global__ void __launch_bounds__(NT, FUSE ? (NCL == 1 ? POP_FUSE_MIN_BLOCKS * 1
       st->a_max[par] = INT_MIN;
     }
   }
+  // GUIDED: the new clones' ancestors are known, so the next dynamical stage can start
+  // each new clone from its ancestor's rate sums
+  if (d.guided && lt == 0 && tid == 0) st->gcarry = 1;
   // the interval ends here unless [iid] selection still has to run
   if (!B.any_iid && blockIdx.x == gridDim.x - 1 && tid == 0) *B.beta += 1u;
 }
@@ -1109,6 +1112,11 @@ __global__ void __launch_bounds__(kGuideThreads, W == 1 ? POP_GUIDE1_MIN_BLOCKS 
   const int32_t* const dtab = B.gdu + (size_t)p * kGuideSeg;
   const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
   const unsigned int lt_mask = (1u << lane) - 1u;
+  // the rate sums of the clones' final configurations of the last interval, if carried:
+  // a new clone starts from its ancestor's
+  const bool carry = B.st[p].gcarry != 0;
+  const unsigned long long* const gin = B.gcar[par ^ 1];
+  unsigned long long* const gout = B.gcar[par];
   int cl = -1;  // the lane's clone (offset in the tile), -1 when it has none
   unsigned long long x[W], a[W];
   unsigned long long R = 0ull;
@@ -1138,9 +1146,20 @@ __global__ void __launch_bounds__(kGuideThreads, W == 1 ? POP_GUIDE1_MIN_BLOCKS 
         h = 0;
         e = 0u;
         t = a_r = a_h = 0.0f;
+        if (carry) {
+          const unsigned long long* src = gin + (d.off + (int64_t)B.anc[base + idx]) * ng;
+          R = 0ull;
+#pragma unroll
+          for (int g = 0; g < ng; ++g) {
+            const unsigned long long v = src[g];
+            s_g[g][tid] = v;
+            R += v;
+          }
+        }
       }
-      // the rate sums of every new clone, one clone at a time by the whole warp
-      unsigned int todo = __ballot_sync(0xffffffffu, got);
+      // the rate sums of every new clone without carried ones, one clone at a time by
+      // the whole warp
+      unsigned int todo = __ballot_sync(0xffffffffu, got && !carry);
       while (todo != 0u) {
         const int o = __ffs(todo) - 1;
         todo &= todo - 1u;
@@ -1255,6 +1274,8 @@ __global__ void __launch_bounds__(kGuideThreads, W == 1 ? POP_GUIDE1_MIN_BLOCKS 
       if (!run) {
         const float X = __fsub_rn(a_h, a_r);
         const int64_t slot = base + cl;
+#pragma unroll
+        for (int g = 0; g < ng; ++g) gout[slot * ng + g] = s_g[g][tid];
         store_lat<W>(B.Xb[par], slot, x);
         B.KXb[par][slot] = B.KY[slot] + h;
         B.dKb[par][slot] = h;

@@ -56,11 +56,13 @@ def test_workspace_bytes(lib):
     assert pg.workspace_bytes([P(weight_mode=G), P()]) == 0
     assert pg.workspace_bytes([P(), P(weight_mode=G)]) == 0
     # a GUIDED population adds its bond tables: dU (int32) and the rate Q (uint64) of
-    # each of the 2^17 segments of an active bond
+    # each of the 2^17 segments of an active bond; and every slot (1024 per tile) its
+    # carried rate sums, 8 W per slot and interval parity
     per_pop = (1 << 17) * (4 + 8)
-    assert pg.workspace_bytes([P(weight_mode=G)]) == pg.workspace_bytes([P()]) + per_pop
+    carry = 2 * 1024 * 8 * 8
+    assert pg.workspace_bytes([P(weight_mode=G)]) == pg.workspace_bytes([P()]) + per_pop + carry
     assert (pg.workspace_bytes([P(weight_mode=G), P(weight_mode=G, seed=2)])
-            == pg.workspace_bytes([P(), P(seed=2)]) + 2 * per_pop)
+            == pg.workspace_bytes([P(), P(seed=2)]) + 2 * per_pop + 2 * carry)
 
 
 def test_init_rejects_bad_arguments_without_device(lib):

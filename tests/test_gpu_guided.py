@@ -125,3 +125,29 @@ def test_guided_argument_errors(pg):
     bad[7] = 65.0
     with pytest.raises(pg.PopError):
         g.set_potential(0, bad)
+
+
+def test_potential_changed_between_intervals(pg):
+    # the clones carry their rate sums from one interval to the next; a new potential
+    # invalidates them (they are formed again from the new bond tables): bit for bit
+    # against the oracle with the potential switched after two intervals, also in run()
+    L, N, nc, s, dt = 60, 30, 2300, 0.03, 0.1
+    phi1, phi2 = potential(11, 0.3), potential(12, 0.4)
+    q = dict(L=L, N=N, n_clones=nc, seed=77, weight_mode=GUIDED)
+    batch = pg.PopulationBatch([q])
+    batch.set_potential(0, phi1)
+    o = oracle.Population(L, N, nc, q["seed"], phi=phi1)
+    batch.run(dt, [s], 2)
+    for _ in range(2):
+        o.evolve(dt, s)
+        o.resample(s)
+    batch.set_potential(0, phi2)
+    o.phi_q = oracle.phi_fixed(phi2)
+    batch.run(dt, [s], 3)
+    for _ in range(3):
+        o.evolve(dt, s)
+        o.resample(s)
+    g = batch.copy_state(0)
+    assert np.array_equal(g["lattice"], oracle.sites_to_words(o.sites, batch.W))
+    assert np.array_equal(g["K"], o.K) and np.array_equal(g["anc"], o.anc)
+    np.testing.assert_allclose(batch.estimate_psi()[0][0], o.estimates()[0], rtol=PSI_RTOL, atol=0.0)
