@@ -105,6 +105,8 @@ def parse():
                     help="the learned-potential study at full size instead of the bench line")
     ap.add_argument("--selection-study", action="store_true",
                     help="the cloning-interval and selection study (Sec. 4.3) instead of the bench line")
+    ap.add_argument("--profile-case", choices=["fused", "guided"], default=None,
+                    help="a small run of one kernel shape, for a profiler capture, instead of the bench line")
     return ap.parse_args()
 
 
@@ -414,6 +416,35 @@ def selection_study(args):
     print(json.dumps(out), flush=True)
 
 
+def profile_case(args):
+    """A small run of one kernel shape for a profiler: 'fused', the L = 128 batch shape
+    with 4 populations of 2^20 clones (lambda = 15, 20 intervals through pop_run, then 4
+    through pop_kernel_times); 'guided', 8 GUIDED populations of 2^14 clones at L = 128
+    under a seeded window potential (10 intervals)."""
+    import torch
+    import paper_1711_05095_gb300 as pg
+    from paper_1711_05095_gb300 import build as pbuild
+    pbuild.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    if args.profile_case == "fused":
+        w = workloads.large_population(lams=(15.0,), n_seeds=4)
+        b = pg.PopulationBatch(w["pops"], device=dev)
+        b.run(w["dt"], w["s"], 20)
+        kt = b.kernel_times(w["dt"], w["s"], 4)
+        print(json.dumps({"case": "fused", "chains": b.run_chains(), "kernel_us": kt}))
+    else:
+        pops = [dict(L=128, N=64, n_clones=1 << 14, seed=300 + i, weight_mode=pg.POP_GUIDED) for i in range(8)]
+        b = pg.PopulationBatch(pops, device=dev)
+        phi = np.random.default_rng(3).normal(0, 0.05, 512).astype(np.float32)
+        for p in range(len(pops)):
+            b.set_potential(p, phi)
+        s = [15.0 / 128 ** 2] * len(pops)
+        b.run(0.05, s, 10)
+        print(json.dumps({"case": "guided", "events": int(b.events().sum())}))
+    b.close()
+
+
 # ---------------------------------------------------------------------------
 def main():
     args = parse()
@@ -422,6 +453,8 @@ def main():
         return config5(args)
     if args.selection_study:
         return selection_study(args)
+    if args.profile_case:
+        return profile_case(args)
     w = workloads.large_population()
     if args.impl == "reference":
         return reference_arm(args, w, rank)
@@ -481,6 +514,7 @@ def main():
     sampler.start()
     t_wall0 = time.perf_counter()
     ms = []
+    torch.cuda.nvtx.range_push("timed_steps")  # selects the timed kernels in a profiler
     for _ in range(args.steps):
         if state["done"] + block > M:
             fresh_run()
@@ -493,6 +527,7 @@ def main():
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
         state["done"] += block
+    torch.cuda.nvtx.range_pop()
     barrier()
     wall = time.perf_counter() - t_wall0
     clocks = sampler.stop()

@@ -206,6 +206,7 @@ struct pop_batch {
   bool any_mod = false;
   bool guided = false;       // every population GUIDED
   bool guided_q_stale = true; // GUIDED: the rate tables need (re)building once s is fixed
+  int guided_split = 1;       // GUIDED: blocks per tile of the dynamical stage (1, 2, 4, 8)
   int evolve_grid = 0;
   int evolve_grid_cap = 0;  // persistent grid at full occupancy
   size_t evolve_smem = 0;
@@ -336,9 +337,12 @@ int launch_evolve(pop_t* h, cudaStream_t st, float dt_f) {
   const size_t sm = h->evolve_smem;
   kernel_begin(h, st, POP_K_EVOLVE);
   if (h->guided) {
-    const unsigned gg = (unsigned)h->lay.ntiles;
-    if (h->lay.W == 1) k_evolve_guided<1><<<gg, kGuideThreads, 0, st>>>(h->B, dt_f);
-    else k_evolve_guided<2><<<gg, kGuideThreads, 0, st>>>(h->B, dt_f);
+    // a tile per block, or a half, quarter or eighth of one for a batch of fewer tiles
+    // than two waves of blocks
+    const int spb = kTile / h->guided_split;
+    const unsigned gg = (unsigned)((int64_t)h->lay.ntiles * h->guided_split);
+    if (h->lay.W == 1) k_evolve_guided<1><<<gg, kGuideThreads, 0, st>>>(h->B, dt_f, spb);
+    else k_evolve_guided<2><<<gg, kGuideThreads, 0, st>>>(h->B, dt_f, spb);
   } else if (h->any_mod) {
     if (h->lay.W == 1) k_evolve<1, true><<<grid, kThreads, sm, st>>>(h->B, dt_f);
     else if (h->lay.W == 2) k_evolve<2, true><<<grid, kThreads, sm, st>>>(h->B, dt_f);
@@ -755,6 +759,15 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
                   : lay.W == 2 ? (mod ? size_evolve_grid<2, true>(h) : size_evolve_grid<2, false>(h))
                                : (mod ? size_evolve_grid_wide<true>(h) : size_evolve_grid_wide<false>(h));
   if (grc != POP_OK) return fail(POP_ERR_CUDA);
+  if (h->guided) {
+    int per_sm = 0, sms = 0;
+    const void* f = lay.W == 1 ? (const void*)k_evolve_guided<1> : (const void*)k_evolve_guided<2>;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kGuideThreads, 0) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess)
+      return fail(POP_ERR_CUDA);
+    const long long want = 2ll * (per_sm < 1 ? 1 : per_sm) * sms;
+    while (h->guided_split < 8 && (long long)lay.ntiles * h->guided_split < want) h->guided_split *= 2;
+  }
 
   const unsigned grid = (unsigned)(lay.nslots / kThreads);
   h->launches[POP_K_OTHER] += 1;

@@ -1070,7 +1070,9 @@ __device__ __forceinline__ float i64_to_float_rn(long long v) {
 }
 
 // One lane per clone; a lane whose clone has ended takes the next clone of the block's
-// tile.  The rate sums of a clone's groups of eight bonds live in shared memory
+// share of a tile (spb slots: a whole tile, or a half, quarter or eighth of one for a
+// batch of few tiles, so that it still fills the GPU).  The rate sums of a clone's
+// groups of eight bonds live in shared memory
 // (group-major: the lanes of a warp never share a bank); a newly taken clone's sums
 // are formed by the whole warp (each lane four or two bonds), so refills stay uniform.
 #ifndef POP_GUIDE_MIN_BLOCKS
@@ -1081,7 +1083,7 @@ __device__ __forceinline__ float i64_to_float_rn(long long v) {
 #endif
 template <int W>
 __global__ void __launch_bounds__(kGuideThreads, W == 1 ? POP_GUIDE1_MIN_BLOCKS : POP_GUIDE_MIN_BLOCKS)
-    k_evolve_guided(Batch B, float dt_f) {
+    k_evolve_guided(Batch B, float dt_f, int spb) {
   constexpr int nb = 64 * W, ng = nb / kGuideGroup;
   constexpr int BPL = nb / 32;  // bonds per lane in the cooperative sums
   __shared__ unsigned long long s_g[ng][kGuideThreads];
@@ -1090,8 +1092,8 @@ __global__ void __launch_bounds__(kGuideThreads, W == 1 ? POP_GUIDE1_MIN_BLOCKS 
   __shared__ int s_min, s_max, s_amin, s_amax;
   __shared__ unsigned int s_ev;
   const int tid = threadIdx.x, lane = tid & 31;
-  const int tile = blockIdx.x;
-  const int p = B.tile_pop[tile];
+  const int64_t base = (int64_t)blockIdx.x * spb;  // the block's first slot
+  const int p = B.tile_pop[base / kTile];
   const PopDesc d = B.pops[p];
   if (tid < 64) s_log[tid] = B.logtab[tid];
   if (tid == 0) {
@@ -1105,8 +1107,7 @@ __global__ void __launch_bounds__(kGuideThreads, W == 1 ? POP_GUIDE1_MIN_BLOCKS 
   __syncthreads();
   const uint32_t beta = *B.beta;
   const int par = (int)(beta & 1u);
-  const int64_t base = (int64_t)tile * kTile;
-  const int n = (int)min((int64_t)kTile, d.nc - (base - d.off));  // clones of this tile
+  const int n = (int)max((int64_t)0, min((int64_t)spb, d.nc - (base - d.off)));  // clones of the block
   const int L = d.L;
   const unsigned long long* const qtab = B.gq + (size_t)p * kGuideSeg;
   const int32_t* const dtab = B.gdu + (size_t)p * kGuideSeg;
