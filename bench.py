@@ -78,7 +78,10 @@ ISSUE_OPS_PER_SM_CLK = 128                      # 4 schedulers x 32 lanes
 # of a smaller batch of the same shape scaled to a full launch: DRAM bytes (read +
 # write), issue slots busy, ALU pipe and active lanes per instruction; valid only for
 # the kernel sources they were taken on (hash of the two device headers).
-KERNEL_TRAFFIC = None
+KERNEL_TRAFFIC = {"bytes_per_tile": 26841, "issue_slots_busy": 0.6802, "alu_pipe": 0.6231,
+                  "lanes_per_instruction": 28.37, "sources": "7abe5ab526df4547",
+                  "captured": "one 2048-tile launch of k_gather<2, 128, FUSE> (bench.py --profile-case fused): "
+                              "51.39 MB read + 3.58 MB written"}
 
 
 def kernel_sources_digest():
@@ -419,8 +422,8 @@ def selection_study(args):
 def profile_case(args):
     """A small run of one kernel shape for a profiler: 'fused', the L = 128 batch shape
     with 4 populations of 2^20 clones (lambda = 15, 20 intervals through pop_run, then 4
-    through pop_kernel_times); 'guided', 8 GUIDED populations of 2^14 clones at L = 128
-    under a seeded window potential (10 intervals)."""
+    through pop_kernel_times); 'guided', 32 GUIDED populations of 2^14 clones at L = 128
+    (the guided batch of the bench line) under a seeded window potential (10 intervals)."""
     import torch
     import paper_1711_05095_gb300 as pg
     from paper_1711_05095_gb300 import build as pbuild
@@ -434,7 +437,7 @@ def profile_case(args):
         kt = b.kernel_times(w["dt"], w["s"], 4)
         print(json.dumps({"case": "fused", "chains": b.run_chains(), "kernel_us": kt}))
     else:
-        pops = [dict(L=128, N=64, n_clones=1 << 14, seed=300 + i, weight_mode=pg.POP_GUIDED) for i in range(8)]
+        pops = [dict(L=128, N=64, n_clones=1 << 14, seed=300 + i, weight_mode=pg.POP_GUIDED) for i in range(32)]
         b = pg.PopulationBatch(pops, device=dev)
         phi = np.random.default_rng(3).normal(0, 0.05, 512).astype(np.float32)
         for p in range(len(pops)):
@@ -672,7 +675,10 @@ def main():
         "gpu_launches": int(launches_end - launches_start),
         "roofline": {"bound": "alu", "kernel": "k_gather<fused> (cloning stage + next dynamical stage)",
                      "achieved": achieved, "peak": peak_gops, "unit": "Gop/s", "frac": achieved / peak_gops,
-                     "traffic": KERNEL_TRAFFIC["bytes"] if counters_valid else None,
+                     "traffic": (KERNEL_TRAFFIC["bytes_per_tile"] * sum((q["n_clones"] + 1023) // 1024 for q in pops)
+                                 if counters_valid else None),
+                     "traffic_from": KERNEL_TRAFFIC["captured"] + ", scaled by tiles (writes mostly stay in L2 "
+                                     "at that size)" if counters_valid else None,
                      "ncu": ({k: KERNEL_TRAFFIC[k] for k in ("issue_slots_busy", "alu_pipe", "lanes_per_instruction")}
                              if counters_valid else None),
                      "peak_kind": "issue rate %d SM x 128 lanes x %.0f MHz (%s max clock)"
