@@ -286,6 +286,100 @@ __device__ __forceinline__ void hop(unsigned long long (&x)[W], int b, int L) {
   }
 }
 
+// The same lattice operations on 32-bit words (u[j] holds sites [32j, 32j + 32)),
+// the ALU's native width.  Shifts that may fall outside a word use the clamped
+// funnel shift: __funnelshift_lc(0, v, n) = v << min(n, 32), which is 0 for n >= 32
+// and, with n formed in unsigned arithmetic, for "negative" n too.
+template <int W>
+__device__ __forceinline__ void split32(const unsigned long long (&x)[W], uint32_t (&u)[2 * W]) {
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    u[2 * w] = (uint32_t)x[w];
+    u[2 * w + 1] = (uint32_t)(x[w] >> 32);
+  }
+}
+
+template <int W>
+__device__ __forceinline__ void join32(const uint32_t (&u)[2 * W], unsigned long long (&x)[W]) {
+#pragma unroll
+  for (int w = 0; w < W; ++w) x[w] = ((unsigned long long)u[2 * w + 1] << 32) | u[2 * w];
+}
+
+// a = x XOR rot(x) on 2W words; lm1 = L - 1 (site L-1's right neighbour is site 0).
+// p[j] = popc(a[j]).
+template <int NW>
+__device__ __forceinline__ void active_bonds32(const uint32_t (&u)[NW], uint32_t lm1, uint32_t (&a)[NW],
+                                               uint32_t (&p)[NW]) {
+  const uint32_t c0 = u[0] & 1u;
+#pragma unroll
+  for (int j = 0; j < NW; ++j) {
+    const uint32_t nxt = (j + 1 < NW) ? u[j + 1] : 0u;
+    const uint32_t rot = __funnelshift_r(u[j], nxt, 1) | __funnelshift_lc(0u, c0, lm1 - 32u * (uint32_t)j);
+    a[j] = u[j] ^ rot;
+    p[j] = (uint32_t)__popc(a[j]);
+  }
+}
+
+// Position of the k-th (0-based) set bit of the 2W-word mask a (k < sum p, p[j] =
+// popc(a[j])): the word by the prefix of the word counts, then halves of 16 and 8
+// bits, then the byte table kth8[8 v + k] (the k-th set bit of the byte v).  For
+// a = 0 and k = 0 it returns a position inside the lattice words without reading
+// outside the table.
+template <int NW>
+__device__ __forceinline__ uint32_t kth_bond32(const uint32_t (&a)[NW], const uint32_t (&p)[NW], uint32_t k,
+                                               const uint8_t* kth8) {
+  uint32_t w, pos;
+  if constexpr (NW == 2) {
+    const bool h = k >= p[0];
+    k = h ? k - p[0] : k;
+    w = h ? a[1] : a[0];
+    pos = h ? 32u : 0u;
+  } else {
+    const uint32_t p01 = p[0] + p[1];
+    const bool h2 = k >= p01;
+    k = h2 ? k - p01 : k;
+    const uint32_t w0 = h2 ? a[2] : a[0], w1 = h2 ? a[3] : a[1], q0 = h2 ? p[2] : p[0];
+    const bool h1 = k >= q0;
+    k = h1 ? k - q0 : k;
+    w = h1 ? w1 : w0;
+    pos = (h2 ? 64u : 0u) + (h1 ? 32u : 0u);
+  }
+  uint32_t c = (uint32_t)__popc(w & 0xffffu);
+  if (k >= c) { k -= c; w >>= 16; pos += 16u; }
+  c = (uint32_t)__popc(w & 0xffu);
+  if (k >= c) { k -= c; w >>= 8; pos += 8u; }
+  return pos + kth8[((w & 0xffu) << 3) | (k & 7u)];
+}
+
+// A hop across bond b flips sites b and c = (b + 1) mod L (lm1 = L - 1); b >= 32 NW
+// (with b != lm1) flips nothing, which is the predicated step's "no hop".
+template <int NW>
+__device__ __forceinline__ void hop32(uint32_t (&u)[NW], uint32_t b, uint32_t lm1) {
+  const uint32_t c = (b == lm1) ? 0u : b + 1u;
+#pragma unroll
+  for (int j = 0; j < NW; ++j)
+    u[j] ^= __funnelshift_lc(0u, 1u, b - 32u * (uint32_t)j) ^ __funnelshift_lc(0u, 1u, c - 32u * (uint32_t)j);
+}
+
+// kth8 as 512 words (4 table bytes per word, little-endian), built at compile time.
+struct Kth8Table {
+  uint32_t w[512];
+};
+constexpr Kth8Table make_kth8() {
+  Kth8Table t{};
+  for (int v = 0; v < 256; ++v) {
+    int k = 0;
+    for (int i = 0; i < 8; ++i)
+      if ((v >> i) & 1) {
+        const int e = 8 * v + k;
+        t.w[e >> 2] |= (uint32_t)i << (8 * (e & 3));
+        ++k;
+      }
+  }
+  return t;
+}
+__device__ __align__(16) const Kth8Table g_kth8 = make_kth8();
+
 template <int W>
 __device__ __forceinline__ void load_lat(const unsigned long long* base, int64_t slot,
                                          unsigned long long (&x)[W]) {

@@ -71,6 +71,7 @@ struct EvolveSmem {
   float a[kChunk];                  // MODIFIED: integral of the escape rate over the interval
   float inv[kChunkUnits][kMaxL + 1];
   float2 logtab[64];
+  __align__(16) uint32_t kth8[512];  // the byte table of kth_bond32
   uint2 u_key[kChunkUnits];         // Philox key of the unit's population
   int32_t u_j0[kChunkUnits];        // population-local index of the unit's first slot
   int32_t u_pop[kChunkUnits], u_L[kChunkUnits], u_valid[kChunkUnits];
@@ -81,22 +82,26 @@ struct EvolveSmem {
 };
 
 // One BKL step (Sec. 4 BKL; Sec. 3.1 rates 1 per possible hop) with the step's
-// exponential variate E = -ln u(wa) and bond word wb: r = active bonds (escape rate;
-// r = 0 ends the interval); tau = E * float(1/r); t_new = t + tau; t_new >= dt ends
-// the interval (the
-// residual waiting time is dropped, as the exponential law's memorylessness
-// allows); otherwise hop across the floor(wb r / 2^32)-th active bond.
-// Returns true if the clone hopped (and is still running).
+// exponential variate E = -ln u(wa) and bond word wb, on the lattice as 2W 32-bit
+// words u (lm1 = L - 1): r = active bonds (escape rate; r = 0 ends the interval);
+// tau = E * float(1/r); t_new = t + tau; t_new >= dt ends the interval (the residual
+// waiting time is dropped, as the exponential law's memorylessness allows);
+// otherwise hop across the floor(wb r / 2^32)-th active bond (kth8: the byte table of
+// kth_bond32).  Returns true if the clone hopped (and is still running).
 // MODIFIED dynamics (Sec. 3.2): inv holds float(e^s / r) and the integral of the
 // unmodified escape rate is accumulated, A <- fma(r, tau, A) per hop and
 // A <- fma(r, dt - t, A) for the last segment.
 template <int W, bool MOD>
-__device__ __forceinline__ bool bkl_step(unsigned long long (&x)[W], float& t, float& acc, int L,
-                                         const float* inv, float E, uint32_t wb, float dt_f) {
-  unsigned long long a[W];
-  active_bonds<W>(x, L, a);
-  const int r = popc_lat<W>(a);
-  if (r == 0) return false;
+__device__ __forceinline__ bool bkl_step(uint32_t (&u)[2 * W], float& t, float& acc, uint32_t lm1,
+                                         const float* inv, float E, uint32_t wb, float dt_f,
+                                         const uint8_t* kth8) {
+  constexpr int NW = 2 * W;
+  uint32_t a[NW], pc[NW];
+  active_bonds32<NW>(u, lm1, a, pc);
+  uint32_t r = 0u;
+#pragma unroll
+  for (int j = 0; j < NW; ++j) r += pc[j];
+  if (r == 0u) return false;
   const float tau = __fmul_rn(E, inv[r]);
   const float t_new = __fadd_rn(t, tau);
   if (t_new >= dt_f) {
@@ -105,38 +110,37 @@ __device__ __forceinline__ bool bkl_step(unsigned long long (&x)[W], float& t, f
   }
   if (MOD) acc = __fmaf_rn((float)r, tau, acc);
   t = t_new;
-  hop<W>(x, kth_bond<W>(a, __umulhi(wb, (uint32_t)r)), L);
+  hop32<NW>(u, kth_bond32<NW>(a, pc, __umulhi(wb, r), kth8), lm1);
   return true;
 }
 
 // The same step without branches, for a clone that is `live` (else nothing changes):
 // the rate, waiting time and bond are computed in any case and applied under the
-// step's predicate, so the lanes of a warp stay together and two steps of different
-// clones can be interleaved.  r = 0 or t_new >= dt ends the interval as in bkl_step
-// (MOD: the last segment r (dt - t) is added when r > 0; for r = 0 it adds nothing).
+// step's predicate, so the lanes of a warp stay together.  r = 0 or t_new >= dt ends
+// the interval as in bkl_step (MOD: the last segment r (dt - t) is added when r > 0;
+// for r = 0 it adds nothing).  A step that does not hop passes bond 1024, which
+// hop32 turns into no change.
 template <int W, bool MOD>
-__device__ __forceinline__ bool bkl_step_pred(unsigned long long (&x)[W], float& t, float& acc, int L,
+__device__ __forceinline__ bool bkl_step_pred(uint32_t (&u)[2 * W], float& t, float& acc, uint32_t lm1,
                                               const float* inv, float E, uint32_t wb, float dt_f,
-                                              bool live) {
-  unsigned long long a[W];
-  active_bonds<W>(x, L, a);
-  const int r = popc_lat<W>(a);
+                                              bool live, const uint8_t* kth8) {
+  constexpr int NW = 2 * W;
+  uint32_t a[NW], pc[NW];
+  active_bonds32<NW>(u, lm1, a, pc);
+  uint32_t r = 0u;
+#pragma unroll
+  for (int j = 0; j < NW; ++j) r += pc[j];
   const float tau = __fmul_rn(E, inv[r]);
   const float t_new = __fadd_rn(t, tau);
-  const bool moving = live && r != 0;
+  const bool moving = live && r != 0u;
   const bool hopped = moving && t_new < dt_f;
   if (MOD) {
     const float seg = hopped ? tau : __fsub_rn(dt_f, t);
     acc = moving ? __fmaf_rn((float)r, seg, acc) : acc;
   }
   t = hopped ? t_new : t;
-  const int b = kth_bond<W>(a, __umulhi(wb, (uint32_t)r));
-  unsigned long long y[W];
-#pragma unroll
-  for (int w = 0; w < W; ++w) y[w] = x[w];
-  hop<W>(y, b, L);
-#pragma unroll
-  for (int w = 0; w < W; ++w) x[w] = hopped ? y[w] : x[w];
+  const uint32_t b = kth_bond32<NW>(a, pc, __umulhi(wb, r), kth8);
+  hop32<NW>(u, hopped ? b : 1024u, lm1);
   return hopped;
 }
 
@@ -163,6 +167,8 @@ __global__ void __launch_bounds__(kThreads, POP_EVOLVE_MIN_BLOCKS) k_evolve(Batc
   int32_t* const dKo = B.dKb[par];
   float* const Ao = B.Ab[par];
   if (tid < 64) S.logtab[tid] = B.logtab[tid];
+  if (tid < 128) reinterpret_cast<uint4*>(S.kth8)[tid] = reinterpret_cast<const uint4*>(g_kth8.w)[tid];
+  const uint8_t* const kth8 = reinterpret_cast<const uint8_t*>(S.kth8);
   // this block's units: an even split of B.nunits over the grid, B.unit_q units each
   // and one more for the first B.unit_r blocks (no divisions on the device)
   const int bx = (int)blockIdx.x;
@@ -268,13 +274,16 @@ __global__ void __launch_bounds__(kThreads, POP_EVOLVE_MIN_BLOCKS) k_evolve(Batc
         // logarithms overlap
         const float E1 = neg_ln_u(d4.x, S.logtab), E2 = neg_ln_u(d4.z, S.logtab);
         bool run = false;
-        if (bkl_step<W, MOD>(x, t, acc, L, inv, E1, d4.y, dt_f)) {
+        uint32_t u[2 * W];
+        split32<W>(x, u);
+        if (bkl_step<W, MOD>(u, t, acc, (uint32_t)L - 1u, inv, E1, d4.y, dt_f, kth8)) {
           ++h;
-          if (bkl_step<W, MOD>(x, t, acc, L, inv, E2, d4.w, dt_f)) {
+          if (bkl_step<W, MOD>(u, t, acc, (uint32_t)L - 1u, inv, E2, d4.w, dt_f, kth8)) {
             ++h;
             run = true;
           }
         }
+        join32<W>(u, x);
         ++q;
         if (run && q >= kStepLimit / 2u) {  // guard: an interval must end; report, never spin
           B.st[S.u_pop[c / kUnit]].err = kErrRange;
@@ -517,6 +526,7 @@ __global__ void __launch_bounds__(NT, FUSE ? (NCL == 1 ? POP_FUSE_MIN_BLOCKS * 1
   __shared__ float s_inv[FUSE ? kMaxL + 1 : 1];
   __shared__ float2 s_logtab[FUSE ? 64 : 1];
   __shared__ uint2 s_keys[FUSE ? 10 : 1];
+  __shared__ __align__(16) uint32_t s_kth8[FUSE ? 512 : 1];
   __shared__ int s_take;
   __shared__ int s_nmin, s_nmax, s_namin, s_namax;
   __shared__ unsigned int s_nev;
@@ -539,6 +549,7 @@ __global__ void __launch_bounds__(NT, FUSE ? (NCL == 1 ? POP_FUSE_MIN_BLOCKS * 1
     const float* src = B.inv_rate + (size_t)p * kInvStride;
     for (int r = tid; r <= kMaxL; r += NT) s_inv[r] = (r <= d.L) ? src[r] : 0.0f;
     if (tid < 64) s_logtab[tid] = B.logtab[tid];
+    if (tid < 128) reinterpret_cast<uint4*>(s_kth8)[tid] = reinterpret_cast<const uint4*>(g_kth8.w)[tid];
     if (tid < 10)
       s_keys[tid] = make_uint2((uint32_t)d.seed + (uint32_t)tid * 0x9E3779B9u,
                                (uint32_t)(d.seed >> 32) + (uint32_t)tid * 0xBB67AE85u);
@@ -708,38 +719,41 @@ __global__ void __launch_bounds__(NT, FUSE ? (NCL == 1 ? POP_FUSE_MIN_BLOCKS * 1
         m[k] = __ballot_sync(0xffffffffu, cl[k] < 0);
         tot += __popc(m[k]);
       }
-      // one read of the counter per warp keeps every branch below warp-uniform
-      int taken = 0;
-      if (lane == 0) taken = *(volatile int*)&s_take;
-      taken = __shfl_sync(0xffffffffu, taken, 0);
-      if (tot != 0 && taken < n) {
-        int base_i = 0;
-        if (lane == 0) base_i = atomicAdd(&s_take, tot);
-        base_i = __shfl_sync(0xffffffffu, base_i, 0);
-#pragma unroll
-        for (int k = 0; k < NCL; ++k) {
-          const int idx = base_i + __popc(m[k] & lt_mask);
-          if (cl[k] < 0 && idx < n) {
-            cl[k] = idx;
-            const int sk = source(J0 + (uint32_t)idx);
-            kold[k] = KXo[base + sk];
-#pragma unroll
-            for (int w = 0; w < W; ++w) x[k][w] = s_x[sk][w];
-            t[k] = 0.0f;
-            acc[k] = 0.0f;
-            h[k] = 0;
-            q[k] = 0u;
-          }
-          base_i += __popc(m[k]);
-        }
-      }
-      bool any = false;
-#pragma unroll
-      for (int k = 0; k < NCL; ++k) any = any || cl[k] >= 0;
-      if (__ballot_sync(0xffffffffu, any) == 0u) {
+      if (tot != 0) {
+        // one read of the counter per warp keeps every branch below warp-uniform
+        int taken = 0;
         if (lane == 0) taken = *(volatile int*)&s_take;
-        if (__shfl_sync(0xffffffffu, taken, 0) >= n) break;
-        continue;
+        taken = __shfl_sync(0xffffffffu, taken, 0);
+        if (taken >= n) {
+          if (tot == 32 * NCL) break;  // nothing left to take and nothing running
+        } else {
+          int base_i = 0;
+          if (lane == 0) base_i = atomicAdd(&s_take, tot);
+          base_i = __shfl_sync(0xffffffffu, base_i, 0);
+#pragma unroll
+          for (int k = 0; k < NCL; ++k) {
+            const int idx = base_i + __popc(m[k] & lt_mask);
+            if (cl[k] < 0 && idx < n) {
+              cl[k] = idx;
+              const int sk = source(J0 + (uint32_t)idx);
+              kold[k] = KXo[base + sk];
+#pragma unroll
+              for (int w = 0; w < W; ++w) x[k][w] = s_x[sk][w];
+              t[k] = 0.0f;
+              acc[k] = 0.0f;
+              h[k] = 0;
+              q[k] = 0u;
+            }
+            base_i += __popc(m[k]);
+          }
+          if (tot == 32 * NCL) {
+            // every slot was empty and the claim may have come after the last clone
+            bool any = false;
+#pragma unroll
+            for (int k = 0; k < NCL; ++k) any = any || cl[k] >= 0;
+            if (__ballot_sync(0xffffffffu, any) == 0u) continue;
+          }
+        }
       }
       uint4 d4[NCL];
       float E1[NCL], E2[NCL];
@@ -754,8 +768,14 @@ __global__ void __launch_bounds__(NT, FUSE ? (NCL == 1 ? POP_FUSE_MIN_BLOCKS * 1
 #pragma unroll
       for (int k = 0; k < NCL; ++k) {
         const bool live = cl[k] >= 0;
-        const bool h1 = bkl_step_pred<W, MOD>(x[k], t[k], acc[k], L, s_inv, E1[k], d4[k].y, dt_f, live);
-        const bool h2 = bkl_step_pred<W, MOD>(x[k], t[k], acc[k], L, s_inv, E2[k], d4[k].w, dt_f, h1);
+        uint32_t u[2 * W];
+        split32<W>(x[k], u);
+        const uint8_t* kth8 = reinterpret_cast<const uint8_t*>(s_kth8);
+        const bool h1 = bkl_step_pred<W, MOD>(u, t[k], acc[k], (uint32_t)L - 1u, s_inv, E1[k], d4[k].y, dt_f,
+                                              live, kth8);
+        const bool h2 = bkl_step_pred<W, MOD>(u, t[k], acc[k], (uint32_t)L - 1u, s_inv, E2[k], d4[k].w, dt_f,
+                                              h1, kth8);
+        join32<W>(u, x[k]);
         h[k] += (int)h1 + (int)h2;
         ++q[k];
         bool run = h2;
