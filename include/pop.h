@@ -192,6 +192,14 @@ int pop_copy_state(pop_t* pop, int32_t p, uint64_t* h_lattice, int32_t* h_K,
  *                   see pop_run_chains)
  *   gather_threads  threads per block of the separate cloning stage: 128, 256, or 0 for
  *                   the rule (256 above 4096 tiles)
+ *   hist_mode       whether the fused stage of a batch without MODIFIED weights also
+ *                   counts the new clones' activities per tile, so that the next
+ *                   interval's tile weight sums and activity histogram come from those
+ *                   counts instead of a pass over every clone: 1 on, 0 off, -1 the rule
+ *                   (on when every population has more than 64 tiles of 1024 clones and
+ *                   dt * (largest L) <= 16, where an activity of 64 or more in one
+ *                   interval is very unlikely; such an activity is still handled, by a
+ *                   slower pass over the population's clones)
  *   default_us_per_interval, tuned_us_per_interval: the times per interval pop_autotune
  *                   measured for the configuration pop_init chose and for its choice
  *                   (0 until it has run; ignored by pop_set_tuning)
@@ -202,6 +210,7 @@ typedef struct pop_tuning {
   int32_t fuse_clones;
   int32_t chains;
   int32_t gather_threads;
+  int32_t hist_mode;
   float default_us_per_interval;
   float tuned_us_per_interval;
 } pop_tuning;

@@ -50,11 +50,11 @@ class PopParams(ctypes.Structure):
 class PopTuning(ctypes.Structure):
     _fields_ = [("evolve_grid", ctypes.c_int32), ("fuse_threads", ctypes.c_int32),
                 ("fuse_clones", ctypes.c_int32), ("chains", ctypes.c_int32),
-                ("gather_threads", ctypes.c_int32), ("default_us_per_interval", ctypes.c_float),
-                ("tuned_us_per_interval", ctypes.c_float)]
+                ("gather_threads", ctypes.c_int32), ("hist_mode", ctypes.c_int32),
+                ("default_us_per_interval", ctypes.c_float), ("tuned_us_per_interval", ctypes.c_float)]
 
 
-TUNING_KEYS = ("evolve_grid", "fuse_threads", "fuse_clones", "chains", "gather_threads")
+TUNING_KEYS = ("evolve_grid", "fuse_threads", "fuse_clones", "chains", "gather_threads", "hist_mode")
 
 
 class PopError(RuntimeError):

@@ -3,7 +3,8 @@
 // A handle owns only host state; every device buffer is carved out of the
 // caller's workspace.  Layout of the workspace (each region 256-byte aligned):
 //   PopDesc[P]  PopState[P]  tile_pop[ntiles]  wtab[P][4096] u64  qtab, qm1tab[P][4096] f64
-//   inv_rate[P][129] f32  logtab[64] f32x2  hist[P][4096] u32  tile_sum, tile_excl[ntiles] u64
+//   inv_rate[P][129] f32  logtab[64] f32x2  hist[P][4096] u32  thist[64][ntiles] u32
+//   tile_sum, tile_excl[ntiles] u64
 //   beta  ksum[P]
 //   X[2], Y lattices [nslots][W] u64   KX[2], KY, dK[2], anc [nslots] i32   A[2] [nslots] f32
 // where every population starts on a 1024-slot tile and nslots is the padded total.
@@ -61,7 +62,7 @@ constexpr int kGatherWideTiles = 4096;
 struct Layout {
   int32_t P = 0, W = 0, ntiles = 0, nunits = 0;
   int64_t nslots = 0;
-  size_t o_pops, o_st, o_tile_pop, o_wtab, o_qtab, o_qm1tab, o_inv, o_logtab, o_exp2, o_A, o_S, o_cs, o_tacc, o_hist, o_tile_sum, o_tile_excl, o_beta, o_phi, o_gtab, o_gdu, o_gq, o_gcar,
+  size_t o_pops, o_st, o_tile_pop, o_wtab, o_qtab, o_qm1tab, o_inv, o_logtab, o_exp2, o_A, o_S, o_cs, o_tacc, o_hist, o_thist, o_tile_sum, o_tile_excl, o_beta, o_phi, o_gtab, o_gdu, o_gq, o_gcar,
       o_ksum, o_X, o_Y, o_KX, o_KY, o_dK, o_anc, total;
 };
 
@@ -113,6 +114,7 @@ bool make_layout(const pop_params* params, int32_t n_pops, Layout* lay) {
   l.o_logtab = take(64 * sizeof(float2));
   l.o_exp2 = take(64 * sizeof(float));
   l.o_hist = take(P * kKcap * sizeof(unsigned int));
+  l.o_thist = take((size_t)kTH * nt * sizeof(unsigned int));
   l.o_tile_sum = take(nt * sizeof(unsigned long long));
   l.o_tile_excl = take(nt * sizeof(unsigned long long));
   l.o_beta = take((1 + kMaxChains) * sizeof(unsigned int));   // the interval counter, one per chain
@@ -198,6 +200,12 @@ struct pop_batch {
   int fuse_threads = 128;                    // fused kernel: threads per block (128 or 256)
   int fuse_clones = kFuseClones;             // fused kernel: clones per lane (1 or 2)
   int gather_threads = 0;                    // separate cloning stage: 128, 256, or 0 for the rule
+  int hist_mode = -1;                        // tile activity histograms: 1 on, 0 off, -1 the rule
+  int max_L = 0;
+  // the last dynamical stage was a fused launch that filled the tile histograms, so the
+  // next cloning stage takes its weights from them (k_tile_scan<true>)
+  bool hist_pending = false;
+  int graph_hist = -1;                       // hist_on of the captured graph
   float tuned_default_us = 0.0f, tuned_us = 0.0f;
   cudaGraphExec_t graph = nullptr;
   float graph_dt = 0.0f;
@@ -356,10 +364,12 @@ int launch_evolve(pop_t* h, cudaStream_t st, float dt_f) {
   return cuda_status(cudaGetLastError());
 }
 
-// The tile prefixes and totals of the populations [pop0, pop1).
-void launch_tile_scan(pop_t* h, cudaStream_t st, const Batch& Bx, int pop0, int pop1) {
-  kernel_begin(h, st, POP_K_OTHER);
-  k_tile_scan<<<(unsigned)(pop1 - pop0), kScanThreads, 0, st>>>(Bx, pop0);
+// The tile prefixes and totals of the populations [pop0, pop1); hist: the tile sums and
+// activity histograms too, from the tile histograms of the fused stage.
+void launch_tile_scan(pop_t* h, cudaStream_t st, const Batch& Bx, int pop0, int pop1, bool hist = false) {
+  kernel_begin(h, st, hist ? POP_K_WEIGHTS : POP_K_OTHER);
+  if (hist) k_tile_scan<true><<<(unsigned)(pop1 - pop0), kScanThreads, 0, st>>>(Bx, pop0);
+  else k_tile_scan<false><<<(unsigned)(pop1 - pop0), kScanThreads, 0, st>>>(Bx, pop0);
   kernel_end(h, st);
 }
 
@@ -377,7 +387,9 @@ void launch_weights(pop_t* h, cudaStream_t st) {
 
 int launch_resample(pop_t* h, cudaStream_t st) {
   const unsigned grid = (unsigned)h->lay.ntiles;
-  launch_weights(h, st);
+  if (h->hist_pending) launch_tile_scan(h, st, h->B, 0, h->lay.P, true);
+  else launch_weights(h, st);
+  h->hist_pending = false;
   constexpr int GT = POP_GATHER_THREADS;
   kernel_begin(h, st, POP_K_GATHER);
   const bool wide_blocks = h->gather_threads == 0 ? h->lay.ntiles > kGatherWideTiles : h->gather_threads == 256;
@@ -426,16 +438,22 @@ bool fusable(const pop_t* h) {
 
 // Cloning stage of the current interval and dynamical stage of the next one, for
 // the tiles [tile0, tile0 + ntiles) (whole populations) with the batch view Bx.
+// after_fused: the current interval's dynamical stage was a fused launch of this
+// configuration, so with Bx.hist_on its tile histograms stand in for k_weights.
 int launch_resample_evolve_range(pop_t* h, cudaStream_t st, float dt_f, const Batch& Bx,
-                                 int tile0, int ntiles, int pop0, int pop1) {
+                                 int tile0, int ntiles, int pop0, int pop1, bool after_fused) {
   const unsigned grid = (unsigned)ntiles;
-  launch_weights_range(h, st, Bx, tile0, ntiles);
-  // the tile prefixes from k_tile_scan when every population here has many tiles; a
-  // population of a few tiles is cheaper to sum inside the fused kernel than to scan in
-  // one more launch per interval
   bool scan = true;
-  for (int p = pop0; p < pop1; ++p) scan = scan && h->desc[p].ntiles > kScanTiles;
-  if (scan) launch_tile_scan(h, st, Bx, pop0, pop1);
+  if (after_fused && Bx.hist_on) {
+    launch_tile_scan(h, st, Bx, pop0, pop1, true);
+  } else {
+    launch_weights_range(h, st, Bx, tile0, ntiles);
+    // the tile prefixes from k_tile_scan when every population here has many tiles; a
+    // population of a few tiles is cheaper to sum inside the fused kernel than to scan
+    // in one more launch per interval
+    for (int p = pop0; p < pop1; ++p) scan = scan && h->desc[p].ntiles > kScanTiles;
+    if (scan) launch_tile_scan(h, st, Bx, pop0, pop1);
+  }
   kernel_begin(h, st, POP_K_GATHER_EVOLVE);
   if (h->lay.W == 1) {
     if (h->any_mod) {
@@ -474,6 +492,22 @@ void set_chains(pop_t* h, int want) {
     h->chain[c] = h->B;
     h->chain[c].beta = h->B.beta + 1 + c;
   }
+}
+
+// Whether the fused stage fills the tile histograms for this dt (pop_tuning hist_mode):
+// only without MODIFIED weights, and by the rule when every population has more than
+// kScanTiles tiles (so the tile scan runs in every interval anyway; for fewer tiles
+// k_weights' many short blocks and the fused stage's own tile sums are faster than one
+// scan block per population) and dt * (largest L) <= 16, where the number of hops of a
+// clone in one interval stays far below 64 (the escape rate is at most L).
+void set_hist(pop_t* h, float dt_f) {
+  bool many_tiles = true;
+  for (const PopDesc& d : h->desc) many_tiles = many_tiles && d.ntiles > kScanTiles;
+  const bool on = fusable(h) && !h->any_mod &&
+                  (h->hist_mode == 1 ||
+                   (h->hist_mode == -1 && many_tiles && (double)dt_f * h->max_L <= 16.0));
+  h->B.hist_on = on ? 1 : 0;
+  for (int c = 0; c < kMaxChains; ++c) h->chain[c].hist_on = h->B.hist_on;
 }
 
 // The rule pop_init starts from: in a batch of at most two waves of the fused kernel
@@ -545,12 +579,15 @@ int size_evolve_grid_wide(pop_t* h) {
 // n fused intervals over the chains: chain 0 on st, the others on the auxiliary
 // streams forked from st and joined back into it, each chain with its own interval
 // counter (copy_chain_counters brings them in line with the batch's counter before and
-// the batch's back from chain 0 after).
-int run_chains(pop_t* h, cudaStream_t st, float dt_f, int64_t n) {
+// the batch's back from chain 0 after).  after_fused: the interval before the first
+// was itself a fused one (its tile histograms are pending).
+int run_chains(pop_t* h, cudaStream_t st, float dt_f, int64_t n, bool after_fused) {
+  if (n > 0) h->hist_pending = h->B.hist_on != 0;
   if (h->nch == 1) {
     int lr = POP_OK;
     for (int64_t i = 0; i < n && lr == POP_OK; ++i)
-      lr = launch_resample_evolve_range(h, st, dt_f, h->chain[0], 0, h->lay.ntiles, 0, h->lay.P);
+      lr = launch_resample_evolve_range(h, st, dt_f, h->chain[0], 0, h->lay.ntiles, 0, h->lay.P,
+                                        after_fused || i > 0);
     return lr;
   }
   if (cudaEventRecord(h->ev_fork, st) != cudaSuccess) return POP_ERR_CUDA;
@@ -561,7 +598,7 @@ int run_chains(pop_t* h, cudaStream_t st, float dt_f, int64_t n) {
     for (int c = 0; c < h->nch && lr == POP_OK; ++c)
       lr = launch_resample_evolve_range(h, c == 0 ? st : h->aux_stream[c - 1], dt_f, h->chain[c],
                                         h->chain_tile[c], h->chain_tile[c + 1] - h->chain_tile[c],
-                                        h->chain_pop[c], h->chain_pop[c + 1]);
+                                        h->chain_pop[c], h->chain_pop[c + 1], after_fused || i > 0);
   // the joins are made even after a failed launch, so a capture can end cleanly
   for (int c = 0; c + 1 < h->nch; ++c)
     if (cudaEventRecord(h->ev_join[c], h->aux_stream[c]) != cudaSuccess ||
@@ -622,6 +659,7 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
   if (h == nullptr) return POP_ERR_ARG;
   h->lay = lay;
   h->params.assign(params, params + n_pops);
+  for (int32_t p = 0; p < n_pops; ++p) h->max_L = std::max(h->max_L, (int)params[p].L);
   h->stream = (cudaStream_t)cuda_stream;
   h->ws = (unsigned char*)d_workspace;
   auto fail = [&](int rc) { pop_free(h); return rc; };
@@ -726,6 +764,7 @@ int pop_init(pop_t** out, const pop_params* params, int32_t n_pops, void* d_work
   B.Ab[1] = B.Ab[0] + lay.nslots;
   B.S = (unsigned long long*)(ws + lay.o_S);
   B.hist = (unsigned int*)(ws + lay.o_hist);
+  B.thist = (unsigned int*)(ws + lay.o_thist);
   B.tile_sum = (unsigned long long*)(ws + lay.o_tile_sum);
   B.tile_excl = (unsigned long long*)(ws + lay.o_tile_excl);
   B.beta = (unsigned int*)(ws + lay.o_beta);
@@ -844,17 +883,25 @@ int pop_run(pop_t* h, double dt, const double* s, int64_t n_intervals) {
   const float dt_f = (float)dt;
   // fused: evolve, then (n - 1) x [weights, gather + next evolve] over the chains, then
   // weights, gather; otherwise n x [evolve, weights, gather].  The graph holds
-  // kGraphIntervals of the repeated part.
+  // kGraphIntervals of the repeated part.  The first fused interval follows the
+  // separate dynamical stage, so it runs before the graph, whose intervals all follow
+  // a fused one (with tile histograms, their weights come from those).
   const bool fuse = fusable(h);
+  set_hist(h, dt_f);
   if (fuse) {
     rc = launch_evolve(h, h->stream, dt_f);
     if (rc != POP_OK) return rc;
+    POP_CUDA(copy_chain_counters(h, true));
+    if (n_intervals > 1) {
+      rc = run_chains(h, h->stream, dt_f, 1, false);
+      if (rc != POP_OK) return rc;
+    }
   }
-  const int64_t n_rep = fuse ? n_intervals - 1 : n_intervals;
+  const int64_t n_rep = fuse ? (n_intervals > 1 ? n_intervals - 2 : 0) : n_intervals;
   const int64_t n_graph = n_rep / kGraphIntervals;
   const int64_t n_rest = n_rep % kGraphIntervals;
   auto block = [&](cudaStream_t st, int64_t n) {
-    if (fuse) return run_chains(h, st, dt_f, n);
+    if (fuse) return run_chains(h, st, dt_f, n, true);
     int lr = POP_OK;
     for (int64_t i = 0; i < n && lr == POP_OK; ++i) {
       lr = launch_evolve(h, st, dt_f);
@@ -862,8 +909,7 @@ int pop_run(pop_t* h, double dt, const double* s, int64_t n_intervals) {
     }
     return lr;
   };
-  if (fuse) POP_CUDA(copy_chain_counters(h, true));
-  if (n_graph > 0 && (h->graph == nullptr || h->graph_dt != dt_f)) {
+  if (n_graph > 0 && (h->graph == nullptr || h->graph_dt != dt_f || h->graph_hist != h->B.hist_on)) {
     if (h->graph != nullptr) {
       cudaGraphExecDestroy(h->graph);
       h->graph = nullptr;
@@ -886,6 +932,7 @@ int pop_run(pop_t* h, double dt, const double* s, int64_t n_intervals) {
       return POP_ERR_CUDA;
     }
     h->graph_dt = dt_f;
+    h->graph_hist = h->B.hist_on;
   }
   for (int64_t i = 0; i < n_graph; ++i) {
     POP_CUDA(cudaGraphLaunch(h->graph, h->stream));
@@ -934,6 +981,7 @@ int pop_kernel_times(pop_t* h, double dt, const double* s, int64_t n_intervals, 
   h->timer_interval = 0;
   const float dt_f = (float)dt;
   const bool fuse = per_step == 0 && fusable(h);
+  set_hist(h, dt_f);
   // the same launches, in the same order and on the same streams, as pop_run (or the
   // per-step calls), each interval's launches tagged with its index
   if (fuse) {
@@ -942,7 +990,7 @@ int pop_kernel_times(pop_t* h, double dt, const double* s, int64_t n_intervals, 
     if (rc == POP_OK) rc = copy_chain_counters(h, true) == cudaSuccess ? POP_OK : POP_ERR_CUDA;
     for (int64_t i = 1; i < n_intervals && rc == POP_OK; ++i) {
       h->timer_interval = (int)i;
-      rc = run_chains(h, h->stream, dt_f, 1);
+      rc = run_chains(h, h->stream, dt_f, 1, i > 1);
     }
     h->timer_interval = (int)n_intervals;
     if (rc == POP_OK) rc = copy_chain_counters(h, false) == cudaSuccess ? POP_OK : POP_ERR_CUDA;
@@ -1133,6 +1181,7 @@ int pop_autotune(pop_t* h, double dt, const double* s, int32_t trials, int32_t* 
                            cudaMemcpyDeviceToHost, h->stream));
   POP_CUDA(cudaStreamSynchronize(h->stream));
   const unsigned int beta1 = 1u;
+  set_hist(h, (float)dt);
   auto restore = [&]() {
     if (cudaMemcpyAsync(h->ws + h->lay.o_st, saved.data(), saved.size() * sizeof(PopState),
                         cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
@@ -1140,7 +1189,10 @@ int pop_autotune(pop_t* h, double dt, const double* s, int32_t trials, int32_t* 
     for (int c = 0; c <= kMaxChains; ++c)
       if (cudaMemcpyAsync(h->B.beta + c, &beta1, sizeof beta1, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
         return false;
+    h->hist_pending = false;  // a trial may end with its tile histograms filled
     return cudaMemsetAsync(h->B.dKb[0], 0, 2 * (size_t)h->lay.nslots * sizeof(int32_t), h->stream) == cudaSuccess &&
+           cudaMemsetAsync(h->B.thist, 0, (size_t)kTH * h->lay.ntiles * sizeof(unsigned int), h->stream) ==
+               cudaSuccess &&
            cudaStreamSynchronize(h->stream) == cudaSuccess;
   };
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1208,7 +1260,7 @@ int pop_autotune(pop_t* h, double dt, const double* s, int32_t trials, int32_t* 
         }
         uint64_t* const count = h->count;
         h->count = h->graph_counts;  // launches made while tuning are not the batch's
-        const int lc = run_chains(h, h->capture_stream, dt_f, trials);
+        const int lc = run_chains(h, h->capture_stream, dt_f, trials, false);
         h->count = count;
         const cudaError_t ec = cudaStreamEndCapture(h->capture_stream, &g);
         if (lc != POP_OK || ec != cudaSuccess || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) {
@@ -1300,6 +1352,7 @@ int pop_get_tuning(pop_t* h, pop_tuning* out) {
   out->fuse_clones = h->fuse_clones;
   out->chains = h->nch;
   out->gather_threads = h->gather_threads;
+  out->hist_mode = h->hist_mode;
   out->default_us_per_interval = h->tuned_default_us;
   out->tuned_us_per_interval = h->tuned_us;
   return POP_OK;
@@ -1310,13 +1363,15 @@ int pop_set_tuning(pop_t* h, const pop_tuning* cfg) {
   if (cfg->evolve_grid < 1 || (cfg->fuse_threads != 128 && cfg->fuse_threads != 256) ||
       (cfg->fuse_clones != 1 && cfg->fuse_clones != 2) || (cfg->fuse_threads == 256 && cfg->fuse_clones != 1) ||
       cfg->chains < 1 || cfg->chains > kMaxChains ||
-      (cfg->gather_threads != 0 && cfg->gather_threads != 128 && cfg->gather_threads != 256))
+      (cfg->gather_threads != 0 && cfg->gather_threads != 128 && cfg->gather_threads != 256) ||
+      cfg->hist_mode < -1 || cfg->hist_mode > 1)
     return POP_ERR_ARG;
   if (h->phase != kReady) return POP_ERR_STATE;
   set_evolve_grid(h, cfg->evolve_grid);
   h->fuse_threads = cfg->fuse_threads;
   h->fuse_clones = cfg->fuse_clones;
   h->gather_threads = cfg->gather_threads;
+  h->hist_mode = cfg->hist_mode;
   set_chains(h, cfg->chains);
   if (h->graph != nullptr) {  // the captured graph holds the old launch configuration
     cudaGraphExecDestroy(h->graph);

@@ -40,6 +40,7 @@ constexpr int kChunkUnits = 7;            // at most this many units staged in s
 constexpr int kChunk = kUnit * kChunkUnits;
 constexpr int kKcap = 4096;               // fixed-point weight table size
 constexpr int kHistSmem = 512;            // activity bins kept in shared memory
+constexpr int kTH = 64;                   // per-tile activity histogram bins (activities 0 .. 63)
 constexpr int kMap = 2048;                // new slots of one tile mapped in shared memory
 #ifndef POP_SCAN_TILES
 #define POP_SCAN_TILES 64
@@ -93,6 +94,9 @@ struct PopState {
   int32_t gcarry;              // GUIDED: the clones' rate sums of the last interval are
                                // carried (set by the cloning stage, cleared by the host
                                // when the potential changes)
+  int32_t hovf;                // some activity of this interval is >= kTH, so the tile
+                               // histograms do not hold every clone (set by the fused
+                               // stage, cleared by k_tile_scan<true>)
   unsigned long long T;        // total weight of this interval (k_tile_scan or k_gather)
 };
 
@@ -115,6 +119,9 @@ struct Batch {
   float* Ab[2];                         // MODIFIED: rate integral, by interval parity
   unsigned long long* S;                // [iid]: exclusive prefix sums of the weights
   unsigned int* hist;                   // [P][kKcap] activity histogram (zero between intervals)
+  unsigned int* thist;                  // [kTH][ntiles] activity histogram of each tile, filled
+                                        // by the fused stage when hist_on (zero between uses)
+  int32_t hist_on;                      // the fused stage fills thist
   unsigned long long* tile_sum;         // [ntiles] weight sum of each tile
   unsigned long long* tile_excl;        // [ntiles] sum of the population's earlier tiles
                                         // (k_tile_scan)

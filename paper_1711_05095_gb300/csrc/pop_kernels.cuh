@@ -430,13 +430,87 @@ __global__ void __launch_bounds__(kThreads) k_weights(Batch B, int tile0) {
 // the total T), so each block of the cloning stage reads two numbers instead of summing
 // all the population's tile sums, work that grows with the square of its tile count
 // (integer sums: the order of addition is immaterial).
+//
+// HIST: the interval's dynamical stage was the fused one with hist_on, so this kernel
+// also does k_weights' work for the population.  With every activity below kTH the
+// tile sums are sum_b n_tile(b) wtab[|b - k_ref|] over the tile histograms, which
+// count the clones of each activity b; the population histogram of |dK - k_ref| is the
+// sum of the tile histograms (both exact integer sums, so equal to the per-clone ones).
+// Otherwise the weights of every clone are formed as in k_weights.  The histograms
+// read are cleared for the next use.
 // ---------------------------------------------------------------------------
 constexpr int kScanThreads = 1024;
+static_assert(kScanThreads == kTile, "the fallback of k_tile_scan<true> takes a tile per pass");
+template <bool HIST>
 __global__ void __launch_bounds__(kScanThreads) k_tile_scan(Batch B, int pop0) {
   __shared__ unsigned long long s_part[kScanThreads / 32];
+  __shared__ unsigned int s_hb[HIST ? kTH : 1];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int p = pop0 + (int)blockIdx.x;
   const PopDesc d = B.pops[p];
+  if constexpr (HIST) {
+    PopState* st = B.st + p;
+    const uint32_t beta = *B.beta;  // the interval being resampled
+    const int par = (int)(beta & 1u);
+    const int dk_min = st->dk_min[par], dk_max = st->dk_max[par];
+    const int kref = d.s_neg ? dk_max : dk_min;
+    const bool ovf = st->hovf != 0 || dk_min < 0 || dk_max >= kTH;
+    for (int b = tid; b < kTH; b += kScanThreads) s_hb[b] = 0u;
+    __syncthreads();  // every thread has read hovf before it is cleared
+    if (tid == 0) {
+      st->kref = kref;
+      st->a_ref = __int_as_float(d.s_neg ? st->a_max[par] : st->a_min[par]);
+      st->beta = beta;
+      st->U = philox4x32_10(make_uint4(0u, beta, 0u, kTagResample), (uint32_t)d.seed,
+                            (uint32_t)(d.seed >> 32)).x;
+      st->hovf = 0;
+    }
+    const unsigned long long* wt = B.wtab + (size_t)p * kKcap;
+    unsigned int* const th = B.thist + d.first_tile;
+    if (!ovf) {
+      const int b0 = dk_min, b1 = dk_max;  // 0 <= b0 <= b1 < kTH
+      for (int i0 = 0; i0 < d.ntiles; i0 += kScanThreads) {
+        const int i = i0 + tid;
+        const bool in = i < d.ntiles;
+        unsigned long long v = 0ull;
+        for (int b = b0; b <= b1; ++b) {
+          unsigned int c = 0u;
+          if (in) {
+            unsigned int* cell = th + (size_t)b * B.ntiles + i;
+            c = *cell;
+            if (c) {
+              v += (unsigned long long)c * wt[abs_diff(b, kref)];
+              *cell = 0u;
+            }
+          }
+          const unsigned int cs = __reduce_add_sync(0xffffffffu, c);
+          if (lane == 0 && cs) atomicAdd(&s_hb[b - b0], cs);
+        }
+        if (in) B.tile_sum[d.first_tile + i] = v;
+      }
+      __syncthreads();
+      for (int b = b0 + tid; b <= b1; b += kScanThreads)
+        B.hist[(size_t)p * kKcap + abs_diff(b, kref)] = s_hb[b - b0];
+    } else {
+      // an activity at or above kTH: the weight of every clone, a tile per pass
+      for (int i = 0; i < d.ntiles; ++i) {
+        const int64_t j = (int64_t)i * kTile + tid;
+        unsigned long long w = 0ull;
+        if (j < d.nc) {
+          unsigned int k;
+          if (!clone_weight(d, B.dKb[par][d.off + j], kref, 0.0f, 0.0f, wt, B.exp2tab, w, k))
+            st->err = kErrRange;
+          else
+            atomicAdd(&B.hist[(size_t)p * kKcap + k], 1u);
+        }
+        const unsigned long long t = block_sum_u64_n<kScanThreads / 32>(w, s_part);
+        if (tid == 0) B.tile_sum[d.first_tile + i] = t;
+      }
+      for (int64_t e = tid; e < (int64_t)kTH * d.ntiles; e += kScanThreads)
+        th[(e / d.ntiles) * B.ntiles + e % d.ntiles] = 0u;
+    }
+    __syncthreads();  // the tile sums written above are read back below
+  }
   unsigned long long run = 0ull;
   for (int i0 = 0; i0 < d.ntiles; i0 += kScanThreads) {
     const int i = i0 + tid;
@@ -527,6 +601,9 @@ __global__ void __launch_bounds__(NT, FUSE ? (NCL == 1 ? POP_FUSE_MIN_BLOCKS * 1
   __shared__ float2 s_logtab[FUSE ? 64 : 1];
   __shared__ uint2 s_keys[FUSE ? 10 : 1];
   __shared__ __align__(16) uint32_t s_kth8[FUSE ? 512 : 1];
+  // FUSE, plain weights: activity histograms of the first three tiles the new clones
+  // fall in (the rest go straight to global memory)
+  __shared__ unsigned int s_th[(FUSE && !MOD) ? 3 * kTH : 1];
   __shared__ int s_take;
   __shared__ int s_nmin, s_nmax, s_namin, s_namax;
   __shared__ unsigned int s_nev;
@@ -550,6 +627,8 @@ __global__ void __launch_bounds__(NT, FUSE ? (NCL == 1 ? POP_FUSE_MIN_BLOCKS * 1
     for (int r = tid; r <= kMaxL; r += NT) s_inv[r] = (r <= d.L) ? src[r] : 0.0f;
     if (tid < 64) s_logtab[tid] = B.logtab[tid];
     if (tid < 128) reinterpret_cast<uint4*>(s_kth8)[tid] = reinterpret_cast<const uint4*>(g_kth8.w)[tid];
+    if constexpr (!MOD)
+      for (int e = tid; e < 3 * kTH; e += NT) s_th[e] = 0u;
     if (tid < 10)
       s_keys[tid] = make_uint2((uint32_t)d.seed + (uint32_t)tid * 0x9E3779B9u,
                                (uint32_t)(d.seed >> 32) + (uint32_t)tid * 0xBB67AE85u);
@@ -692,6 +771,11 @@ __global__ void __launch_bounds__(NT, FUSE ? (NCL == 1 ? POP_FUSE_MIN_BLOCKS * 1
     float* const An = B.Ab[pn];
     const int n = (int)(J1 - J0);
     const int L = d.L;
+    // the tile of the new slot J0 (tiles of the next interval: 1024 slots, populations
+    // tile-aligned), and whether an activity fell outside the histograms
+    const int t0 = (int)((d.off + (int64_t)J0) >> 10);
+    const bool hist_on = !MOD && B.hist_on != 0;
+    bool ovf = false;
     const unsigned int lt_mask = (1u << lane) - 1u;
     int cl[NCL], h[NCL];              // the slot's new clone (offset from J0, -1: empty)
     int kold[NCL];                    // its ancestor's cumulative activity
@@ -825,6 +909,28 @@ __global__ void __launch_bounds__(NT, FUSE ? (NCL == 1 ? POP_FUSE_MIN_BLOCKS * 1
         atomicMin(&st->a_min[pn], s_namin);
         atomicMax(&st->a_max[pn], s_namax);
       }
+    }
+    if (hist_on) {
+      // count the new clones' activities by tile (after the loop, from the activities
+      // just written: counting inside the loop costs the loop registers)
+      for (int jj = tid; jj < n; jj += NT) {
+        const int64_t dst = d.off + (int64_t)J0 + jj;
+        const int hh = dKn[dst];
+        if (hh < kTH) {
+          const int tn = (int)(dst >> 10);
+          if (tn - t0 < 3) atomicAdd(&s_th[(tn - t0) * kTH + hh], 1u);
+          else atomicAdd(&B.thist[(size_t)hh * B.ntiles + tn], 1u);
+        } else {
+          ovf = true;
+        }
+      }
+      __syncthreads();
+      // a shared bin holds only clones of its tile, so a non-zero bin names a real tile
+      for (int e = tid; e < 3 * kTH; e += NT) {
+        const unsigned int v = s_th[e];
+        if (v) atomicAdd(&B.thist[(size_t)(e % kTH) * B.ntiles + t0 + e / kTH], v);
+      }
+      if (ovf) st->hovf = 1;
     }
   } else if constexpr (W > 0) {
     for (uint32_t jj = J0 + (uint32_t)tid; jj < J1; jj += NT) {

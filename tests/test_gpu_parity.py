@@ -437,7 +437,8 @@ def test_autotune_changes_no_result(pg):
     dict(fuse_threads=128, fuse_clones=1, chains=1), dict(fuse_threads=128, fuse_clones=2, chains=1),
     dict(fuse_threads=256, fuse_clones=1, chains=1), dict(fuse_threads=128, fuse_clones=1, chains=2),
     dict(fuse_threads=128, fuse_clones=2, chains=4), dict(fuse_threads=256, fuse_clones=1, chains=8),
-    dict(evolve_grid=7, chains=3), dict(gather_threads=256), dict(gather_threads=128)])
+    dict(evolve_grid=7, chains=3), dict(gather_threads=256), dict(gather_threads=128),
+    dict(hist_mode=0), dict(hist_mode=1, chains=4), dict(hist_mode=0, fuse_clones=2, chains=2)])
 def test_every_tuned_parameter_changes_no_result(pg, cfg):
     # every value of every tuned parameter gives the same lattices, activities,
     # ancestors and psi as the configuration pop_init chose (a fused batch of five
@@ -484,7 +485,8 @@ def test_gather_tuning_of_a_batch_that_does_not_fuse_changes_no_result(pg):
 def test_set_tuning_rejects_out_of_range(pg):
     a = pg.PopulationBatch([dict(L=50, N=25, n_clones=2000, seed=1)])
     for bad in (dict(fuse_threads=64), dict(fuse_clones=3), dict(fuse_threads=256, fuse_clones=2),
-                dict(chains=0), dict(chains=9), dict(gather_threads=512), dict(evolve_grid=0)):
+                dict(chains=0), dict(chains=9), dict(gather_threads=512), dict(evolve_grid=0),
+                dict(hist_mode=2), dict(hist_mode=-2)):
         with pytest.raises(pg.PopError):
             a.set_tuning(**bad)
 
@@ -492,7 +494,10 @@ def test_set_tuning_rejects_out_of_range(pg):
 def test_kernel_times_equals_run_and_counts(pg):
     # pop_kernel_times launches what pop_run launches (results identical); the
     # launch counters follow the fused sequence: one dynamical stage, then
-    # (n - 1) x [weights, fused stage] per chain, then weights and the cloning stage
+    # (n - 1) x [weights, fused stage] per chain, then weights and the cloning stage.
+    # With populations of more than 64 tiles (below) the fused stages count activities
+    # per tile and, after the first fused interval, the tile scan takes k_weights' place
+    # (a launch of the "weights" kind that also scans)
     pops = [dict(L=50, N=25, n_clones=3000, seed=21), dict(L=90, N=45, n_clones=2000, seed=22)]
     s = [0.02, -0.003]
     n = 40
@@ -537,13 +542,51 @@ def test_kernel_times_equals_run_and_counts(pg):
     cnt = c.launch_count()
     assert cnt["evolve"] == 35 and cnt["weights"] == 35 and cnt["gather"] == 70
     assert cnt["gather_evolve"] == 0 and cnt["other"] == 1 + 35
-    # populations of more than 64 tiles: the fused stage takes the tile scan too
+    # populations of more than 64 tiles: the fused stage after k_weights takes the tile
+    # scan too (once per chain, in the first fused interval); without the tile
+    # histograms, in every interval
     big = [dict(L=50, N=25, n_clones=65 * 1024, seed=60 + i) for i in range(2)]
     d = pg.PopulationBatch(big)
     d.run(0.1, [0.02, 0.03], n)
     cnt = d.launch_count()
     chains = len(d.run_chains()) - 1
+    assert cnt["gather_evolve"] == chains * (n - 1) and cnt["other"] == 1 + chains
+    assert cnt["weights"] == chains * (n - 1) + 1
+    d = pg.PopulationBatch(big)
+    d.set_tuning(hist_mode=0)
+    d.run(0.1, [0.02, 0.03], n)
+    cnt = d.launch_count()
     assert cnt["gather_evolve"] == chains * (n - 1) and cnt["other"] == 1 + chains * (n - 1) + 1
+
+
+@pytest.mark.parametrize("dt", [0.1, 1.5])
+def test_tile_histograms_change_no_result(pg, dt):
+    # the fused stage's per-tile activity counts (hist_mode 1) against k_weights'
+    # pass over every clone (hist_mode 0): the same lattices, activities, ancestors and
+    # psi bit for bit, over two chains and populations of one and many tiles.  At
+    # dt = 1.5 the L = 128 populations hop about 100 times an interval, beyond the 64
+    # counted activities, so their tile sums come from the slower pass over the clones
+    # while the L = 20 population's still come from the counts
+    pops = [dict(L=20, N=10, n_clones=5000, seed=71), dict(L=128, N=64, n_clones=70 * 1024, seed=72),
+            dict(L=128, N=40, n_clones=3000, seed=73), dict(L=100, N=50, n_clones=66 * 1024, seed=74)]
+    s = [0.05, 0.002, -0.01, 0.0]
+    runs = []
+    for mode in (1, 0):
+        b = pg.PopulationBatch(pops)
+        b.set_tuning(hist_mode=mode, chains=2)
+        b.run(dt, s, 7)
+        b.run(dt, s, 5)   # a second call: the counts of the first were all consumed
+        runs.append(b)
+    a, b = runs
+    assert a.run_chains() == b.run_chains() and len(a.run_chains()) == 3
+    for p in range(len(pops)):
+        ga, gb = a.copy_state(p), b.copy_state(p)
+        for key in ("lattice", "K", "anc", "dK"):
+            assert np.array_equal(ga[key], gb[key]), (p, key)
+    np.testing.assert_array_equal(a.estimate_psi()[0], b.estimate_psi()[0])
+    np.testing.assert_array_equal(a.events(), b.events())
+    if dt > 1.0:
+        assert int(b.copy_state(1)["dK"].max()) >= 64
 
 
 def test_activity_spread_beyond_the_weight_table_is_reported(pg):
