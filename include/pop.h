@@ -221,7 +221,9 @@ typedef struct pop_tuning {
  * grid (1 .. the resident blocks per SM, times the SM count); for a batch that fuses,
  * three replays of `trials` fused intervals captured as a CUDA graph (as pop_run runs
  * them) for each fused-kernel form (128 threads with one or two clones per lane, 256
- * threads with one) and each chain split (up to 1, 2, 4, 8); for a
+ * threads with one) and each chain split (up to 1, 2, 4, 8), with and without the
+ * per-tile activity counts where dt * (largest L) <= 16 and no weights are MODIFIED
+ * (the hist_mode chosen, 0 or 1, is for this dt); for a
  * batch that does not, `trials` whole intervals for each block size of the separate
  * cloning stage.  Keeps the fastest of each.  Every trial starts again from interval 1
  * and the counters, activities and (for the cloning-stage trials) the population are

@@ -1233,25 +1233,34 @@ int pop_autotune(pop_t* h, double dt, const double* s, int32_t trials, int32_t* 
   }
   set_evolve_grid(h, best);
 
-  // (2) fused batches: the fused kernel's form (threads per block, clones per lane) and
-  // the chains of pop_run, by the time per interval of `trials` fused intervals
+  // (2) fused batches: the fused kernel's form (threads per block, clones per lane),
+  // the chains of pop_run and, where activities of 64 or more are very unlikely
+  // (dt * (largest L) <= 16, no MODIFIED weights), whether the fused stage counts them
+  // per tile, by the time per interval of `trials` fused intervals
   if (rc == POP_OK && fusable(h)) {
     const int forms[3][2] = {{128, 1}, {128, 2}, {256, 1}};
     const int wants[4] = {1, 2, 4, 8};
     const int def_threads = h->fuse_threads, def_clones = h->fuse_clones, def_nch = h->nch;
-    int bt = def_threads, bc = def_clones, bw = def_nch;
+    const int def_hist = h->hist_mode;
+    const bool def_on = h->B.hist_on != 0;
+    const bool hist_ok = !h->any_mod && (double)dt_f * h->max_L <= 16.0;
+    int bt = def_threads, bc = def_clones, bw = def_nch, bh = def_hist;
     float bms = 1e30f, def_ms = 0.0f;
     int last_nch = -1;
+    for (int hm = 0; hm < (hist_ok ? 2 : 1) && rc == POP_OK; ++hm)
     for (int f = 0; f < 3 && rc == POP_OK; ++f) {
       last_nch = -1;
       for (int w = 0; w < 4 && rc == POP_OK; ++w) {
         h->fuse_threads = forms[f][0];
         h->fuse_clones = forms[f][1];
+        h->hist_mode = hist_ok ? hm : def_hist;
         set_chains(h, wants[w]);
+        set_hist(h, dt_f);
         if (h->nch == last_nch) continue;  // the same split as the smaller want
         last_nch = h->nch;
         // `trials` fused intervals captured as a graph, as pop_run replays them (launched
-        // one by one, many short chains would be timed by their launch overhead)
+        // one by one, many short chains would be timed by their launch overhead); each
+        // follows a fused interval, as in pop_run's graph
         cudaGraph_t g = nullptr;
         cudaGraphExec_t ge = nullptr;
         if (cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -1260,7 +1269,7 @@ int pop_autotune(pop_t* h, double dt, const double* s, int32_t trials, int32_t* 
         }
         uint64_t* const count = h->count;
         h->count = h->graph_counts;  // launches made while tuning are not the batch's
-        const int lc = run_chains(h, h->capture_stream, dt_f, trials, false);
+        const int lc = run_chains(h, h->capture_stream, dt_f, trials, true);
         h->count = count;
         const cudaError_t ec = cudaStreamEndCapture(h->capture_stream, &g);
         if (lc != POP_OK || ec != cudaSuccess || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) {
@@ -1272,9 +1281,10 @@ int pop_autotune(pop_t* h, double dt, const double* s, int32_t trials, int32_t* 
         float ms = 0.0f;
         rc = timed([&](bool first) {
               int lr = POP_OK;
-              if (first) {
+              if (first) {  // as pop_run: the first fused interval follows the dynamical stage
                 lr = launch_evolve(h, h->stream, dt_f);
                 if (lr == POP_OK && copy_chain_counters(h, true) != cudaSuccess) lr = POP_ERR_CUDA;
+                if (lr == POP_OK) lr = run_chains(h, h->stream, dt_f, 1, false);
               }
               if (lr == POP_OK && cudaGraphLaunch(ge, h->stream) != cudaSuccess) lr = POP_ERR_CUDA;
               return lr;
@@ -1282,13 +1292,17 @@ int pop_autotune(pop_t* h, double dt, const double* s, int32_t trials, int32_t* 
         cudaGraphExecDestroy(ge);
         ms /= (float)trials;
         if (rc != POP_OK) break;
-        if (forms[f][0] == def_threads && forms[f][1] == def_clones && h->nch == def_nch) def_ms = ms;
-        if (ms < bms) { bms = ms; bt = forms[f][0]; bc = forms[f][1]; bw = wants[w]; }
+        if (forms[f][0] == def_threads && forms[f][1] == def_clones && h->nch == def_nch &&
+            (h->B.hist_on != 0) == def_on)
+          def_ms = ms;
+        if (ms < bms) { bms = ms; bt = forms[f][0]; bc = forms[f][1]; bw = wants[w]; bh = h->hist_mode; }
       }
     }
     h->fuse_threads = bt;
     h->fuse_clones = bc;
+    h->hist_mode = bh;
     set_chains(h, bw);
+    set_hist(h, dt_f);
     h->tuned_default_us = 1e3f * def_ms;
     h->tuned_us = 1e3f * bms;
   }
