@@ -544,9 +544,10 @@ def main():
 
     # dominant kernel: the launches pop_run makes for this batch in the tuned
     # configuration, each between CUDA events recorded by the library on the stream it
-    # launches on (pop_kernel_times), continuing the same run
-    # (with several chains an interval's fused launches run side by side: the time is
-    # their span per interval, and the operations those of the whole interval)
+    # launches on (pop_kernel_times; after the first fused interval, from one captured
+    # graph as pop_run replays it), continuing the same run.  With several chains the
+    # fused launches run side by side: the time is that during which at least one of
+    # them runs, per interval, and the operations those of the whole interval
     R = args.kernel_intervals
     torch.cuda.nvtx.range_push("fused_kernel_timing")
     kt = b.kernel_times(dt, s, R + 1)

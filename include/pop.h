@@ -327,28 +327,33 @@ int pop_events(pop_t* pop, uint64_t* h_events);
 
 /* Kernel kinds of pop_kernel_times and pop_launch_count. */
 #define POP_K_EVOLVE 0         /* dynamical stage (Sec. 2.3), one interval */
-#define POP_K_WEIGHTS 1        /* cloning weights, tile sums, activity histogram */
+#define POP_K_WEIGHTS 1        /* cloning weights, tile sums, activity histogram
+                                  (k_weights, or the tile scan that forms them from the
+                                  fused stage's per-tile activity counts) */
 #define POP_K_GATHER 2         /* cloning stage: [eq] copies, [iid] selection */
 #define POP_K_GATHER_EVOLVE 3  /* cloning stage of one interval fused with the
                                   dynamical stage of the next (pop_run, [eq], L <= 128) */
 #define POP_K_OTHER 4          /* initial state, estimates, density mode, ancestry
                                   (pop_lineage), and the scan of each population's tile
-                                  sums before a cloning stage */
+                                  sums before a cloning stage (when it does not also
+                                  form the weights) */
 #define POP_NKINDS 5
 
 /*
- * Measurement.  Advances the batch by n_intervals >= 1 intervals with the kernels
- * pop_run uses, over the whole batch (per_step = 0: never split into halves), or those
- * of pop_evolve + pop_resample
- * (per_step = 1: the separate dynamical and cloning stages), in the same order and so
- * with the same results, but launched one by one, each between two CUDA events
- * recorded on the handle's stream.  Any
- * output may be NULL; each is a host array of POP_NKINDS:
- *   h_us    mean device time of the launches of each kind, microseconds (0 if none)
+ * Measurement.  Advances the batch by n_intervals >= 1 intervals with the launches
+ * pop_run makes (per_step = 0: the same chains on the same streams, the intervals after
+ * the first fused one as one captured graph, as pop_run replays them) or those of
+ * pop_evolve + pop_resample (per_step = 1: the separate dynamical and cloning stages,
+ * launched one by one), in the same order and so with the same results, with a CUDA
+ * event recorded before and after every launch on its own stream (an event-record node
+ * inside the graph).  Any output may be NULL; each is a host array of POP_NKINDS:
+ *   h_us    per kind, the time during which at least one of its launches runs (the
+ *           union of their start-to-end ranges), divided by the number of intervals
+ *           that launch it, microseconds (one chain: the mean launch time; 0 if none)
  *   h_n     number of launches of each kind
  *   h_hops  hops executed by the launches of each kind (nonzero only for the kinds
  *           that run dynamical stages)
- * Fixes s like pop_evolve.  POP_ERR_STATE between pop_evolve and pop_resample.
+ * Between pop_evolve and pop_resample: POP_ERR_STATE.  Fixes s like pop_evolve.
  * Waits for the stream.
  */
 int pop_kernel_times(pop_t* pop, double dt, const double* s, int64_t n_intervals, int32_t per_step,

@@ -233,6 +233,8 @@ struct pop_batch {
   std::vector<int>* timer_kinds = nullptr;
   std::vector<int>* timer_intervals = nullptr;
   int timer_interval = 0;
+  int timer_base = -1;        // run_chains tags interval i of its call timer_base + i (if >= 0)
+  bool timer_capture = false; // the timed launches are being captured into a graph
 };
 
 namespace {
@@ -319,25 +321,27 @@ bool valid_dt(double dt) { return std::isfinite(dt) && dt > 0.0 && dt < 1e30; }
 
 // Bookkeeping around one kernel launch: the per-kind count and, under
 // pop_kernel_times, an event pair on the launching stream.
+// pop_kernel_times: an event before and after each launch (while a graph is being
+// captured, as an event-record node of the graph)
+void timer_record(pop_t* h, cudaStream_t st) {
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  if (h->timer_capture) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+  else cudaEventRecord(e, st);
+  h->timer_events->push_back(e);
+}
+
 void kernel_begin(pop_t* h, cudaStream_t st, int kind) {
   h->count[kind] += 1;
   if (h->timer_events != nullptr) {
-    cudaEvent_t e = nullptr;
-    cudaEventCreate(&e);
-    cudaEventRecord(e, st);
-    h->timer_events->push_back(e);
+    timer_record(h, st);
     h->timer_kinds->push_back(kind);
     if (h->timer_intervals) h->timer_intervals->push_back(h->timer_interval);
   }
 }
 
 void kernel_end(pop_t* h, cudaStream_t st) {
-  if (h->timer_events != nullptr) {
-    cudaEvent_t e = nullptr;
-    cudaEventCreate(&e);
-    cudaEventRecord(e, st);
-    h->timer_events->push_back(e);
-  }
+  if (h->timer_events != nullptr) timer_record(h, st);
 }
 
 int launch_evolve(pop_t* h, cudaStream_t st, float dt_f) {
@@ -585,9 +589,11 @@ int run_chains(pop_t* h, cudaStream_t st, float dt_f, int64_t n, bool after_fuse
   if (n > 0) h->hist_pending = h->B.hist_on != 0;
   if (h->nch == 1) {
     int lr = POP_OK;
-    for (int64_t i = 0; i < n && lr == POP_OK; ++i)
+    for (int64_t i = 0; i < n && lr == POP_OK; ++i) {
+      if (h->timer_base >= 0) h->timer_interval = h->timer_base + (int)i;
       lr = launch_resample_evolve_range(h, st, dt_f, h->chain[0], 0, h->lay.ntiles, 0, h->lay.P,
                                         after_fused || i > 0);
+    }
     return lr;
   }
   if (cudaEventRecord(h->ev_fork, st) != cudaSuccess) return POP_ERR_CUDA;
@@ -595,10 +601,12 @@ int run_chains(pop_t* h, cudaStream_t st, float dt_f, int64_t n, bool after_fuse
     if (cudaStreamWaitEvent(h->aux_stream[c], h->ev_fork, 0) != cudaSuccess) return POP_ERR_CUDA;
   int lr = POP_OK;
   for (int64_t i = 0; i < n && lr == POP_OK; ++i)
-    for (int c = 0; c < h->nch && lr == POP_OK; ++c)
+    for (int c = 0; c < h->nch && lr == POP_OK; ++c) {
+      if (h->timer_base >= 0) h->timer_interval = h->timer_base + (int)i;
       lr = launch_resample_evolve_range(h, c == 0 ? st : h->aux_stream[c - 1], dt_f, h->chain[c],
                                         h->chain_tile[c], h->chain_tile[c + 1] - h->chain_tile[c],
                                         h->chain_pop[c], h->chain_pop[c + 1], after_fused || i > 0);
+    }
   // the joins are made even after a failed launch, so a capture can end cleanly
   for (int c = 0; c + 1 < h->nch; ++c)
     if (cudaEventRecord(h->ev_join[c], h->aux_stream[c]) != cudaSuccess ||
@@ -988,9 +996,30 @@ int pop_kernel_times(pop_t* h, double dt, const double* s, int64_t n_intervals, 
     rc = launch_evolve(h, h->stream, dt_f);
     if (rc == POP_OK) rc = total_hops(&hops1);
     if (rc == POP_OK) rc = copy_chain_counters(h, true) == cudaSuccess ? POP_OK : POP_ERR_CUDA;
-    for (int64_t i = 1; i < n_intervals && rc == POP_OK; ++i) {
-      h->timer_interval = (int)i;
-      rc = run_chains(h, h->stream, dt_f, 1, i > 1);
+    // the first fused interval as pop_run launches it; the others as one captured graph
+    // of run_chains, as pop_run replays them, with event-record nodes around each launch
+    if (n_intervals > 1 && rc == POP_OK) {
+      h->timer_interval = 1;
+      rc = run_chains(h, h->stream, dt_f, 1, false);
+    }
+    if (n_intervals > 2 && rc == POP_OK) {
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t ge = nullptr;
+      if (cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        rc = POP_ERR_CUDA;
+      } else {
+        h->timer_capture = true;
+        h->timer_base = 2;
+        const int lc = run_chains(h, h->capture_stream, dt_f, n_intervals - 2, true);
+        h->timer_base = -1;
+        h->timer_capture = false;
+        const cudaError_t ec = cudaStreamEndCapture(h->capture_stream, &g);
+        if (lc != POP_OK || ec != cudaSuccess || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess ||
+            cudaGraphLaunch(ge, h->stream) != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess)
+          rc = POP_ERR_CUDA;
+        if (ge) cudaGraphExecDestroy(ge);
+        if (g) cudaGraphDestroy(g);
+      }
     }
     h->timer_interval = (int)n_intervals;
     if (rc == POP_OK) rc = copy_chain_counters(h, false) == cudaSuccess ? POP_OK : POP_ERR_CUDA;
@@ -1006,10 +1035,11 @@ int pop_kernel_times(pop_t* h, double dt, const double* s, int64_t n_intervals, 
   h->timer_kinds = nullptr;
   h->timer_intervals = nullptr;
   if (rc == POP_OK) rc = total_hops(&hops2);
-  // per kind and interval: the span from the first start to the last end of its launches
-  // (the launches of the chains run side by side), times from the common origin event
-  const int64_t nspan = (int64_t)POP_NKINDS * (n_intervals + 1);
-  std::vector<double> t0(nspan, 1e300), t1(nspan, -1e300);
+  // per kind: the time during which at least one of its launches runs (the union of
+  // the launches' [start, end] from the common origin event; the chains' launches run
+  // side by side and drift apart over the graph), per interval that launches the kind
+  std::vector<std::vector<std::pair<double, double>>> runs(POP_NKINDS);
+  std::vector<std::vector<char>> seen(POP_NKINDS, std::vector<char>((size_t)n_intervals + 1, 0));
   int64_t cnt[POP_NKINDS] = {};
   for (size_t i = 0; i < kinds.size() && rc == POP_OK; ++i) {
     float a = 0.0f, b = 0.0f;
@@ -1018,9 +1048,8 @@ int pop_kernel_times(pop_t* h, double dt, const double* s, int64_t n_intervals, 
       rc = POP_ERR_CUDA;
       break;
     }
-    const int64_t at = (int64_t)kinds[i] * (n_intervals + 1) + ivs[i];
-    t0[at] = std::min(t0[at], (double)a);
-    t1[at] = std::max(t1[at], (double)b);
+    runs[kinds[i]].emplace_back((double)a, (double)b);
+    seen[kinds[i]][ivs[i]] = 1;
     cnt[kinds[i]] += 1;
   }
   for (cudaEvent_t e : events) cudaEventDestroy(e);
@@ -1029,15 +1058,21 @@ int pop_kernel_times(pop_t* h, double dt, const double* s, int64_t n_intervals, 
   h->intervals += n_intervals;
   h->t_obs += (double)n_intervals * dt;
   for (int k = 0; k < POP_NKINDS; ++k) {
-    double sum = 0.0;
-    int64_t groups = 0;
-    for (int64_t i = 0; i <= n_intervals; ++i) {
-      const int64_t at = (int64_t)k * (n_intervals + 1) + i;
-      if (t1[at] >= t0[at]) {
-        sum += t1[at] - t0[at];
-        ++groups;
+    std::vector<std::pair<double, double>>& r = runs[k];
+    std::sort(r.begin(), r.end());
+    double sum = 0.0, lo = 0.0, hi = -1e300;
+    for (const auto& x : r) {
+      if (x.first > hi) {
+        if (hi > lo) sum += hi - lo;
+        lo = x.first;
+        hi = x.second;
+      } else {
+        hi = std::max(hi, x.second);
       }
     }
+    if (hi > lo) sum += hi - lo;
+    int64_t groups = 0;
+    for (char c : seen[k]) groups += c;
     if (h_us) h_us[k] = groups ? 1e3 * sum / (double)groups : 0.0;
     if (h_n) h_n[k] = cnt[k];
     if (h_hops) h_hops[k] = 0;

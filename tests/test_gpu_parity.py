@@ -511,7 +511,7 @@ def test_kernel_times_equals_run_and_counts(pg):
             assert np.array_equal(ga[key], gb[key]), key
     np.testing.assert_array_equal(a.events(), b.events())
     # two chains (below): each fused interval is two launches of each kind, and the
-    # reported time is the span of the two side by side
+    # reported time is the time during which either runs, per interval
     assert kt["evolve"][1] == 1 and kt["gather_evolve"][1] == 2 * (n - 1)
     assert kt["weights"][1] == 2 * (n - 1) + 1 and kt["gather"][1] == 1
     assert kt["evolve"][2] + kt["gather_evolve"][2] == int(b.events().sum())
