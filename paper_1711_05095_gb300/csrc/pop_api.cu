@@ -424,14 +424,21 @@ int launch_resample(pop_t* h, cudaStream_t st) {
 
 // The fused kernel in the handle's configuration: 128 threads per block with one or two
 // clones per lane, or 256 threads with one.
-template <int W, bool MOD, bool SCAN>
-void launch_fused(pop_t* h, unsigned grid, cudaStream_t st, const Batch& Bx, float dt_f, int tile0) {
+template <int W, bool MOD, bool SCAN, bool FULL>
+void launch_fused_form(pop_t* h, unsigned grid, cudaStream_t st, const Batch& Bx, float dt_f, int tile0) {
   if (h->fuse_threads == 256)
-    k_gather<W, 256, true, MOD, SCAN, 1><<<grid, 256, 0, st>>>(Bx, dt_f, tile0);
+    k_gather<W, 256, true, MOD, SCAN, 1, FULL><<<grid, 256, 0, st>>>(Bx, dt_f, tile0);
   else if (h->fuse_clones == 2)
-    k_gather<W, 128, true, MOD, SCAN, 2><<<grid, 128, 0, st>>>(Bx, dt_f, tile0);
+    k_gather<W, 128, true, MOD, SCAN, 2, FULL><<<grid, 128, 0, st>>>(Bx, dt_f, tile0);
   else
-    k_gather<W, 128, true, MOD, SCAN, 1><<<grid, 128, 0, st>>>(Bx, dt_f, tile0);
+    k_gather<W, 128, true, MOD, SCAN, 1, FULL><<<grid, 128, 0, st>>>(Bx, dt_f, tile0);
+}
+
+// full: every population of the launch has L = 64 W (the ring fills the lattice words)
+template <int W, bool MOD, bool SCAN>
+void launch_fused(pop_t* h, unsigned grid, cudaStream_t st, const Batch& Bx, float dt_f, int tile0, bool full) {
+  if (full) launch_fused_form<W, MOD, SCAN, true>(h, grid, st, Bx, dt_f, tile0);
+  else launch_fused_form<W, MOD, SCAN, false>(h, grid, st, Bx, dt_f, tile0);
 }
 
 // pop_run fuses the cloning stage of one interval with the dynamical stage of
@@ -458,22 +465,24 @@ int launch_resample_evolve_range(pop_t* h, cudaStream_t st, float dt_f, const Ba
     for (int p = pop0; p < pop1; ++p) scan = scan && h->desc[p].ntiles > kScanTiles;
     if (scan) launch_tile_scan(h, st, Bx, pop0, pop1);
   }
+  bool full = true;
+  for (int p = pop0; p < pop1; ++p) full = full && h->desc[p].L == 64 * h->lay.W;
   kernel_begin(h, st, POP_K_GATHER_EVOLVE);
   if (h->lay.W == 1) {
     if (h->any_mod) {
-      if (scan) launch_fused<1, true, true>(h, grid, st, Bx, dt_f, tile0);
-      else launch_fused<1, true, false>(h, grid, st, Bx, dt_f, tile0);
+      if (scan) launch_fused<1, true, true>(h, grid, st, Bx, dt_f, tile0, full);
+      else launch_fused<1, true, false>(h, grid, st, Bx, dt_f, tile0, full);
     } else {
-      if (scan) launch_fused<1, false, true>(h, grid, st, Bx, dt_f, tile0);
-      else launch_fused<1, false, false>(h, grid, st, Bx, dt_f, tile0);
+      if (scan) launch_fused<1, false, true>(h, grid, st, Bx, dt_f, tile0, full);
+      else launch_fused<1, false, false>(h, grid, st, Bx, dt_f, tile0, full);
     }
   } else {
     if (h->any_mod) {
-      if (scan) launch_fused<2, true, true>(h, grid, st, Bx, dt_f, tile0);
-      else launch_fused<2, true, false>(h, grid, st, Bx, dt_f, tile0);
+      if (scan) launch_fused<2, true, true>(h, grid, st, Bx, dt_f, tile0, full);
+      else launch_fused<2, true, false>(h, grid, st, Bx, dt_f, tile0, full);
     } else {
-      if (scan) launch_fused<2, false, true>(h, grid, st, Bx, dt_f, tile0);
-      else launch_fused<2, false, false>(h, grid, st, Bx, dt_f, tile0);
+      if (scan) launch_fused<2, false, true>(h, grid, st, Bx, dt_f, tile0, full);
+      else launch_fused<2, false, false>(h, grid, st, Bx, dt_f, tile0, full);
     }
   }
   kernel_end(h, st);

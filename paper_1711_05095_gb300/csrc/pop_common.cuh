@@ -313,15 +313,21 @@ __device__ __forceinline__ void join32(const uint32_t (&u)[2 * W], unsigned long
 }
 
 // a = x XOR rot(x) on 2W words; lm1 = L - 1 (site L-1's right neighbour is site 0).
-// p[j] = popc(a[j]).
-template <int NW>
+// p[j] = popc(a[j]).  FULL: L = 32 NW, the ring fills the words, and rot is a
+// rotation of the words' concatenation by one bit.
+template <int NW, bool FULL = false>
 __device__ __forceinline__ void active_bonds32(const uint32_t (&u)[NW], uint32_t lm1, uint32_t (&a)[NW],
                                                uint32_t (&p)[NW]) {
   const uint32_t c0 = u[0] & 1u;
 #pragma unroll
   for (int j = 0; j < NW; ++j) {
-    const uint32_t nxt = (j + 1 < NW) ? u[j + 1] : 0u;
-    const uint32_t rot = __funnelshift_r(u[j], nxt, 1) | __funnelshift_lc(0u, c0, lm1 - 32u * (uint32_t)j);
+    uint32_t rot;
+    if constexpr (FULL) {
+      rot = __funnelshift_r(u[j], u[(j + 1) % NW], 1);
+    } else {
+      const uint32_t nxt = (j + 1 < NW) ? u[j + 1] : 0u;
+      rot = __funnelshift_r(u[j], nxt, 1) | __funnelshift_lc(0u, c0, lm1 - 32u * (uint32_t)j);
+    }
     a[j] = u[j] ^ rot;
     p[j] = (uint32_t)__popc(a[j]);
   }

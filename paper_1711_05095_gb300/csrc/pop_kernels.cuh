@@ -119,14 +119,14 @@ __device__ __forceinline__ bool bkl_step(uint32_t (&u)[2 * W], float& t, float& 
 // step's predicate, so the lanes of a warp stay together.  r = 0 or t_new >= dt ends
 // the interval as in bkl_step (MOD: the last segment r (dt - t) is added when r > 0;
 // for r = 0 it adds nothing).  A step that does not hop passes bond 1024, which
-// hop32 turns into no change.
-template <int W, bool MOD>
+// hop32 turns into no change.  FULL: L = 64 W (see active_bonds32).
+template <int W, bool MOD, bool FULL = false>
 __device__ __forceinline__ bool bkl_step_pred(uint32_t (&u)[2 * W], float& t, float& acc, uint32_t lm1,
                                               const float* inv, float E, uint32_t wb, float dt_f,
                                               bool live, const uint8_t* kth8) {
   constexpr int NW = 2 * W;
   uint32_t a[NW], pc[NW];
-  active_bonds32<NW>(u, lm1, a, pc);
+  active_bonds32<NW, FULL>(u, lm1, a, pc);
   uint32_t r = 0u;
 #pragma unroll
   for (int j = 0; j < NW; ++j) r += pc[j];
@@ -571,7 +571,9 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(Batch B, int pop0) {
 // the extra path costs registers and scheduling when compiled into the same kernel).
 // NCL (FUSE only): clones each lane advances together in the dynamical stage, 1 or 2
 // (two independent Philox and bit-select chains in flight per lane).
-template <int W, int NT, bool FUSE = false, bool MOD = false, bool SCAN = true, int NCL = 1>
+// FULL (FUSE only): every population of the launch has L = 64 W, so the ring fills
+// the lattice words (active_bonds32<.., true>).
+template <int W, int NT, bool FUSE = false, bool MOD = false, bool SCAN = true, int NCL = 1, bool FULL = false>
 __global__ void __launch_bounds__(NT, FUSE ? (NCL == 1 ? POP_FUSE_MIN_BLOCKS * 128 / NT : POP_FUSE2_MIN_BLOCKS)
                                            : (NT == 128 ? 11 : (NT == 256 ? 6 : 3)))
     k_gather(Batch B, float dt_f, int tile0) {
@@ -855,10 +857,10 @@ __global__ void __launch_bounds__(NT, FUSE ? (NCL == 1 ? POP_FUSE_MIN_BLOCKS * 1
         uint32_t u[2 * W];
         split32<W>(x[k], u);
         const uint8_t* kth8 = reinterpret_cast<const uint8_t*>(s_kth8);
-        const bool h1 = bkl_step_pred<W, MOD>(u, t[k], acc[k], (uint32_t)L - 1u, s_inv, E1[k], d4[k].y, dt_f,
-                                              live, kth8);
-        const bool h2 = bkl_step_pred<W, MOD>(u, t[k], acc[k], (uint32_t)L - 1u, s_inv, E2[k], d4[k].w, dt_f,
-                                              h1, kth8);
+        const bool h1 = bkl_step_pred<W, MOD, FULL>(u, t[k], acc[k], (uint32_t)L - 1u, s_inv, E1[k], d4[k].y,
+                                                    dt_f, live, kth8);
+        const bool h2 = bkl_step_pred<W, MOD, FULL>(u, t[k], acc[k], (uint32_t)L - 1u, s_inv, E2[k], d4[k].w,
+                                                    dt_f, h1, kth8);
         join32<W>(u, x[k]);
         h[k] += (int)h1 + (int)h2;
         ++q[k];

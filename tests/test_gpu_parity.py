@@ -138,6 +138,12 @@ RUN_CASES = {
     # strong bias: a wide activity range and tiles whose old clones leave no copies
     "strong_bias": ([dict(L=64, N=32, n_clones=5000, seed=21), dict(L=128, N=64, n_clones=3000, seed=22)],
                     [2.0, 0.5], [34]),
+    # rings that fill the lattice words (L = 64 W: the fused kernel rotates the words
+    # without a closing bit), one and two words
+    "w1_full_ring": ([dict(L=64, N=20, n_clones=3000, seed=23), dict(L=64, N=40, n_clones=2100, seed=24)],
+                     [0.02, -0.05], [36]),
+    "w2_full_ring": ([dict(L=128, N=64, n_clones=3000, seed=25), dict(L=128, N=50, n_clones=2100, seed=26)],
+                     [0.01, -0.02], [35]),
 }
 
 
@@ -211,6 +217,25 @@ def test_full_size_s_sweep_sampled(pg):
         assert np.all(counts == w["pops"][p]["N"])
         assert np.all(np.diff(g["anc"]) >= 0)
         assert g["anc"].min() >= 0 and g["anc"].max() < w["pops"][p]["n_clones"]
+
+
+def test_full_size_large_population_run(pg):
+    # the bench's population shape (L = 128, N_c = 2^20) through pop_run: the fused
+    # kernel for rings that fill the words, with the per-tile activity counts, over
+    # three intervals, against the oracle
+    q = dict(L=128, N=64, n_clones=2**20, seed=2001)
+    s = 15.0 / 128**2
+    batch = pg.PopulationBatch([q])
+    assert batch.get_tuning()["hist_mode"] == -1
+    batch.run(0.05, [s], 3)
+    o = oracle.Population(q["L"], q["N"], q["n_clones"], q["seed"])
+    for _ in range(3):
+        o.evolve(0.05)
+        o.resample(s)
+    g = batch.copy_state(0)
+    assert np.array_equal(g["anc"], o.anc)
+    assert_state_equal(g, o, batch.W, "large population run")
+    np.testing.assert_allclose(batch.estimate_psi()[0][0], o.estimates()[0], rtol=PSI_RTOL)
 
 
 def test_full_size_large_population_one_interval(pg):
