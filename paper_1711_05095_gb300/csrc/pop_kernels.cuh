@@ -1014,17 +1014,26 @@ __global__ void __launch_bounds__(NT, FUSE ? (NCL == 1 ? POP_FUSE_MIN_BLOCKS * 1
 // ---------------------------------------------------------------------------
 // [iid] selection (Sec. 4.1): new clone j of the population pulls old clone k with
 // S_k <= alpha_j < S_{k+1}, alpha_j = floor(U64_j T / 2^64), U64_j from draw
-// (j, beta, 0, 4); a binary search over the population's prefix sums.  One block
-// per tile of new slots; populations with [eq] selection are skipped.  The last
-// block advances the interval counter.
+// (j, beta, 0, 4).  The search runs in two levels over the same non-decreasing prefix
+// sums: the last tile whose first prefix (k_tile_scan's tile_excl) is <= alpha_j,
+// from a shared-memory copy of the population's tile prefixes, then the last k of
+// that tile with S_k <= alpha_j.  One block per tile of new slots; populations with
+// [eq] selection are skipped.  The last block advances the interval counter.
 // ---------------------------------------------------------------------------
+constexpr int kIidSmemTiles = 2048;  // tile prefixes kept in shared memory (16 KB)
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_select_iid(Batch B) {
+  __shared__ unsigned long long s_te[kIidSmemTiles];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int tile = blockIdx.x;
   const int p = B.tile_pop[tile];
   const PopDesc d = B.pops[p];
   if (d.iid) {
+    const unsigned long long* te = B.tile_excl + d.first_tile;
+    const bool staged = d.ntiles <= kIidSmemTiles;
+    if (staged)
+      for (int i = tid; i < d.ntiles; i += kThreads) s_te[i] = te[i];
+    __syncthreads();
     const PopState* st = B.st + p;
     const unsigned long long T = st->T;
     const uint32_t beta = st->beta;
@@ -1039,7 +1048,13 @@ __global__ void __launch_bounds__(kThreads) k_select_iid(Batch B) {
       if (j >= d.nc) break;
       const uint4 r = philox4x32_10(make_uint4((uint32_t)j, beta, 0u, kTagIid), k0, k1);
       const unsigned long long alpha = __umul64hi(((unsigned long long)r.y << 32) | r.x, T);
-      long long lo = 0, hi = d.nc - 1;  // the last k with S_k <= alpha
+      int tlo = 0, thi = d.ntiles - 1;  // the last tile whose first prefix is <= alpha
+      while (tlo < thi) {
+        const int mid = (tlo + thi + 1) >> 1;
+        if ((staged ? s_te[mid] : te[mid]) <= alpha) tlo = mid; else thi = mid - 1;
+      }
+      long long lo = (long long)tlo * kTile;  // the last k of the tile with S_k <= alpha
+      long long hi = min((long long)d.nc, lo + kTile) - 1;
       while (lo < hi) {
         const long long mid = lo + (hi - lo + 1) / 2;
         if (S[mid] <= alpha) lo = mid; else hi = mid - 1;

@@ -344,6 +344,15 @@ def test_parity_mixed_modes_batch(pg):
     run_parity(pg, pops, [0.1, -0.05, 0.02, 0.3], 0.1, 4)
 
 
+def test_parity_iid_beyond_the_staged_tile_prefixes(pg):
+    # [iid] selection searches the tile prefixes first: from shared memory for up to
+    # 2048 tiles, from global memory beyond (here 2101 tiles with a ragged last one)
+    # next to a population of 3 tiles
+    pops = [dict(L=20, N=10, n_clones=2100 * 1024 + 5, seed=91, selection=IID),
+            dict(L=30, N=12, n_clones=2500, seed=92, selection=IID)]
+    run_parity(pg, pops, [0.05, -0.1], 0.1, 2)
+
+
 @pytest.mark.parametrize("L,dt", [(20, 10.0), (50, 1.0), (50, 10.0)])
 def test_selection_study_state_point_matches_oracle(pg, L, dt):
     # the cloning-interval and selection study's configuration (lambda = 28, [eq] and
