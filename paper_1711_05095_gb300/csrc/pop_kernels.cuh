@@ -607,6 +607,7 @@ __global__ void __launch_bounds__(NT, FUSE ? (NCL == 1 ? POP_FUSE_MIN_BLOCKS * 1
   // fall in (the rest go straight to global memory)
   __shared__ unsigned int s_th[(FUSE && !MOD) ? 3 * kTH : 1];
   __shared__ int s_take;
+  __shared__ unsigned int s_pack[2];  // FUSE: clones packed in the current / next tail round
   __shared__ int s_nmin, s_nmax, s_namin, s_namax;
   __shared__ unsigned int s_nev;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -636,6 +637,8 @@ __global__ void __launch_bounds__(NT, FUSE ? (NCL == 1 ? POP_FUSE_MIN_BLOCKS * 1
                                (uint32_t)(d.seed >> 32) + (uint32_t)tid * 0xBB67AE85u);
     if (tid == 0) {
       s_take = 0;
+      s_pack[0] = 0u;
+      s_pack[1] = 0u;
       s_nmin = INT_MAX;
       s_nmax = INT_MIN;
       s_namin = INT_MAX;
@@ -797,50 +800,9 @@ __global__ void __launch_bounds__(NT, FUSE ? (NCL == 1 ? POP_FUSE_MIN_BLOCKS * 1
 #pragma unroll
       for (int w = 0; w < W; ++w) x[k][w] = 0ull;
     }
-    for (;;) {
-      unsigned int m[NCL];
-      int tot = 0;
-#pragma unroll
-      for (int k = 0; k < NCL; ++k) {
-        m[k] = __ballot_sync(0xffffffffu, cl[k] < 0);
-        tot += __popc(m[k]);
-      }
-      if (tot != 0) {
-        // one read of the counter per warp keeps every branch below warp-uniform
-        int taken = 0;
-        if (lane == 0) taken = *(volatile int*)&s_take;
-        taken = __shfl_sync(0xffffffffu, taken, 0);
-        if (taken >= n) {
-          if (tot == 32 * NCL) break;  // nothing left to take and nothing running
-        } else {
-          int base_i = 0;
-          if (lane == 0) base_i = atomicAdd(&s_take, tot);
-          base_i = __shfl_sync(0xffffffffu, base_i, 0);
-#pragma unroll
-          for (int k = 0; k < NCL; ++k) {
-            const int idx = base_i + __popc(m[k] & lt_mask);
-            if (cl[k] < 0 && idx < n) {
-              cl[k] = idx;
-              const int sk = source(J0 + (uint32_t)idx);
-              kold[k] = KXo[base + sk];
-#pragma unroll
-              for (int w = 0; w < W; ++w) x[k][w] = s_x[sk][w];
-              t[k] = 0.0f;
-              acc[k] = 0.0f;
-              h[k] = 0;
-              q[k] = 0u;
-            }
-            base_i += __popc(m[k]);
-          }
-          if (tot == 32 * NCL) {
-            // every slot was empty and the claim may have come after the last clone
-            bool any = false;
-#pragma unroll
-            for (int k = 0; k < NCL; ++k) any = any || cl[k] >= 0;
-            if (__ballot_sync(0xffffffffu, any) == 0u) continue;
-          }
-        }
-      }
+    // one iteration of the lane's clones: a Philox draw each, two predicated BKL steps,
+    // and the write-back of a clone whose interval ended
+    auto iterate = [&]() {
       uint4 d4[NCL];
       float E1[NCL], E2[NCL];
 #pragma unroll
@@ -885,6 +847,102 @@ __global__ void __launch_bounds__(NT, FUSE ? (NCL == 1 ? POP_FUSE_MIN_BLOCKS * 1
           cl[k] = -1;
         }
       }
+    };
+    // lanes take new slots from the shared counter until it runs out
+    for (;;) {
+      unsigned int m[NCL];
+      int tot = 0;
+#pragma unroll
+      for (int k = 0; k < NCL; ++k) {
+        m[k] = __ballot_sync(0xffffffffu, cl[k] < 0);
+        tot += __popc(m[k]);
+      }
+      if (tot != 0) {
+        // one read of the counter per warp keeps every branch below warp-uniform
+        int taken = 0;
+        if (lane == 0) taken = *(volatile int*)&s_take;
+        taken = __shfl_sync(0xffffffffu, taken, 0);
+        if (taken >= n) break;  // the counter ran out: on to the packed rounds below
+        int base_i = 0;
+        if (lane == 0) base_i = atomicAdd(&s_take, tot);
+        base_i = __shfl_sync(0xffffffffu, base_i, 0);
+#pragma unroll
+        for (int k = 0; k < NCL; ++k) {
+          const int idx = base_i + __popc(m[k] & lt_mask);
+          if (cl[k] < 0 && idx < n) {
+            cl[k] = idx;
+            const int sk = source(J0 + (uint32_t)idx);
+            kold[k] = KXo[base + sk];
+#pragma unroll
+            for (int w = 0; w < W; ++w) x[k][w] = s_x[sk][w];
+            t[k] = 0.0f;
+            acc[k] = 0.0f;
+            h[k] = 0;
+            q[k] = 0u;
+          }
+          base_i += __popc(m[k]);
+        }
+        if (tot == 32 * NCL) {
+          // every slot was empty and the claim may have come after the last clone
+          bool any = false;
+#pragma unroll
+          for (int k = 0; k < NCL; ++k) any = any || cl[k] >= 0;
+          if (__ballot_sync(0xffffffffu, any) == 0u) continue;
+        }
+      }
+      iterate();
+    }
+    // The counter has run out.  Each round packs the block's remaining clones into the
+    // lowest threads (through the staging buffer of the old clones, no longer read),
+    // so that warps left without clones stop issuing, and runs one iteration.
+    struct Packed {
+      unsigned long long x[W];
+      float t, acc;
+      int cl, h, kold;
+      uint32_t q;
+    };
+    static_assert(sizeof(Packed) * NT * NCL <= sizeof(s_x), "the packed clones fit the staging buffer");
+    Packed* const s_packed = reinterpret_cast<Packed*>(&s_x[0][0]);
+    for (int rnd = 0;; ++rnd) {
+      __syncthreads();  // every warp is done with the staging buffer and the last round
+      unsigned int* const cnt = &s_pack[rnd & 1];
+#pragma unroll
+      for (int k = 0; k < NCL; ++k) {
+        if (cl[k] >= 0) {
+          Packed& e = s_packed[atomicAdd(cnt, 1u)];
+#pragma unroll
+          for (int w = 0; w < W; ++w) e.x[w] = x[k][w];
+          e.t = t[k];
+          e.acc = acc[k];
+          e.cl = cl[k];
+          e.h = h[k];
+          e.kold = kold[k];
+          e.q = q[k];
+        }
+      }
+      if (tid == 0) s_pack[(rnd + 1) & 1] = 0u;
+      __syncthreads();
+      const int count = (int)*cnt;
+      if (count == 0) break;
+      bool any = false;
+#pragma unroll
+      for (int k = 0; k < NCL; ++k) {
+        const int i = tid + k * NT;
+        cl[k] = -1;
+        if (i < count) {
+          const Packed& e = s_packed[i];
+#pragma unroll
+          for (int w = 0; w < W; ++w) x[k][w] = e.x[w];
+          t[k] = e.t;
+          acc[k] = e.acc;
+          cl[k] = e.cl;
+          h[k] = e.h;
+          kold[k] = e.kold;
+          q[k] = e.q;
+          any = true;
+        }
+      }
+      if (__ballot_sync(0xffffffffu, any) != 0u) iterate();
     }
     hmin = __reduce_min_sync(0xffffffffu, hmin);
     hmax = __reduce_max_sync(0xffffffffu, hmax);
