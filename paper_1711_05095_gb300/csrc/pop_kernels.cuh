@@ -1223,22 +1223,15 @@ __device__ __forceinline__ unsigned long long ring_window(const unsigned long lo
 }
 
 // Rate of the bond whose 18-site segment starts at bit o of window v (its sites at bits
-// o + 8 and o + 9): Q from the table if they differ, else 0.  PRED: load only for an
-// active bond (measured faster for two-word lattices); otherwise load in any case and
-// select, which keeps more loads in flight (faster for one-word lattices).
-template <bool PRED>
+// o + 8 and o + 9): Q from the table if they differ, else 0 (the table is read only for
+// an active bond).
 __device__ __forceinline__ unsigned long long guided_q_at(unsigned long long v, int o,
                                                           const unsigned long long* qtab) {
   const uint32_t seg = (uint32_t)(v >> o) & 0x3FFFFu;
   const bool act = ((seg >> 8) ^ (seg >> 9)) & 1u;
-  if constexpr (PRED) {
-    unsigned long long q = 0ull;
-    if (act) q = __ldg(qtab + guided_index(seg));
-    return q;
-  } else {
-    const unsigned long long q = __ldg(qtab + guided_index(seg));
-    return act ? q : 0ull;
-  }
+  unsigned long long q = 0ull;
+  if (act) q = __ldg(qtab + guided_index(seg));
+  return q;
 }
 
 // float(v) rounded to nearest (ties to even) for a 64-bit unsigned v, in 32-bit integer
@@ -1277,11 +1270,13 @@ __device__ __forceinline__ float i64_to_float_rn(long long v) {
 // (group-major: the lanes of a warp never share a bank); a newly taken clone's sums
 // are formed by the whole warp (each lane four or two bonds), so refills stay uniform.
 #ifndef POP_GUIDE_MIN_BLOCKS
-#define POP_GUIDE_MIN_BLOCKS 5   // two-word lattices: up to 96 registers
+#define POP_GUIDE_MIN_BLOCKS 8   // 64 registers, 32 warps per SM (5 blocks at 96 registers: 5 % slower)
 #endif
 #ifndef POP_GUIDE1_MIN_BLOCKS
-#define POP_GUIDE1_MIN_BLOCKS 1  // one-word lattices: every table load of a re-rate in flight
+#define POP_GUIDE1_MIN_BLOCKS 8  // one-word lattices too (1 block at 140 registers and
+                                 // unpredicated table loads: 1.3x slower)
 #endif
+
 template <int W>
 __global__ void __launch_bounds__(kGuideThreads, W == 1 ? POP_GUIDE1_MIN_BLOCKS : POP_GUIDE_MIN_BLOCKS)
     k_evolve_guided(Batch B, float dt_f, int spb) {
@@ -1376,7 +1371,7 @@ __global__ void __launch_bounds__(kGuideThreads, W == 1 ? POP_GUIDE1_MIN_BLOCKS 
           const unsigned long long win = ring_window<W>(xo, L, st0);
 #pragma unroll
           for (int i = 0; i < BPL; ++i)
-            if (b0 + i < L) v += guided_q_at<W == 2>(win, i, qtab);
+            if (b0 + i < L) v += guided_q_at(win, i, qtab);
         }
         // a group of eight bonds spans 8 / BPL lanes
 #pragma unroll
@@ -1437,7 +1432,7 @@ __global__ void __launch_bounds__(kGuideThreads, W == 1 ? POP_GUIDE1_MIN_BLOCKS 
         found = false;
 #pragma unroll
         for (int i = 0; i < kGuideGroup; ++i) {
-          const unsigned long long q = gb + i < L ? guided_q_at<W == 2>(gwin, i, qtab) : 0ull;
+          const unsigned long long q = gb + i < L ? guided_q_at(gwin, i, qtab) : 0ull;
           if (!found) {
             cum += q;
             if (cum > kk) {
@@ -1464,8 +1459,8 @@ __global__ void __launch_bounds__(kGuideThreads, W == 1 ? POP_GUIDE1_MIN_BLOCKS 
           int c = b + db;
           if (c < 0) c += L;
           if (c >= L) c -= L;
-          const unsigned long long qo = guided_q_at<W == 2>(wo, db + 9, qtab);
-          const unsigned long long qn = guided_q_at<W == 2>(wn, db + 9, qtab);
+          const unsigned long long qo = guided_q_at(wo, db + 9, qtab);
+          const unsigned long long qn = guided_q_at(wn, db + 9, qtab);
           if (qn != qo) {
             s_g[c / kGuideGroup][tid] += qn - qo;
             R += qn - qo;
