@@ -110,6 +110,8 @@ def parse():
                     help="the cloning-interval and selection study (Sec. 4.3) instead of the bench line")
     ap.add_argument("--profile-case", choices=["fused", "guided"], default=None,
                     help="a small run of one kernel shape, for a profiler capture, instead of the bench line")
+    ap.add_argument("--profile-dt", type=float, default=None,
+                    help="interval length of the 'fused' profiling case (default: the workload's 0.05)")
     return ap.parse_args()
 
 
@@ -421,8 +423,8 @@ def selection_study(args):
 
 def profile_case(args):
     """A small run of one kernel shape for a profiler: 'fused', the L = 128 batch shape
-    with 4 populations of 2^20 clones (lambda = 15, 20 intervals through pop_run, then 4
-    through pop_kernel_times); 'guided', 32 GUIDED populations of 2^14 clones at L = 128
+    with 4 populations of 2^20 clones (lambda = 15, 20 intervals of --profile-dt through
+    pop_run, then 4 through pop_kernel_times); 'guided', 32 GUIDED populations of 2^14 clones at L = 128
     (the guided batch of the bench line) under a seeded window potential (10 intervals)."""
     import torch
     import paper_1711_05095_gb300 as pg
@@ -432,10 +434,13 @@ def profile_case(args):
     torch.cuda.set_device(dev)
     if args.profile_case == "fused":
         w = workloads.large_population(lams=(15.0,), n_seeds=4)
+        dt = args.profile_dt if args.profile_dt is not None else w["dt"]
         b = pg.PopulationBatch(w["pops"], device=dev)
-        b.run(w["dt"], w["s"], 20)
-        kt = b.kernel_times(w["dt"], w["s"], 4)
-        print(json.dumps({"case": "fused", "chains": b.run_chains(), "kernel_us": kt}))
+        b.run(dt, w["s"], 20)
+        hops = int(b.events().sum()) / (20 * sum(q["n_clones"] for q in w["pops"]))
+        kt = b.kernel_times(dt, w["s"], 4)
+        print(json.dumps({"case": "fused", "dt": dt, "hops_per_clone_interval": hops, "chains": b.run_chains(),
+                          "kernel_us": kt}))
     else:
         pops = [dict(L=128, N=64, n_clones=1 << 14, seed=300 + i, weight_mode=pg.POP_GUIDED) for i in range(32)]
         b = pg.PopulationBatch(pops, device=dev)
