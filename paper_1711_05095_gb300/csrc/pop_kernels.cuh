@@ -603,6 +603,11 @@ __global__ void __launch_bounds__(NT, FUSE ? (NCL == 1 ? POP_FUSE_MIN_BLOCKS * 1
   __shared__ float s_inv[FUSE ? kMaxL + 1 : 1];
   __shared__ float2 s_logtab[FUSE ? 64 : 1];
   __shared__ uint2 s_keys[FUSE ? 10 : 1];
+  // FUSE: the first kWStage entries of the population's weight table (the activity
+  // spreads of nearly every interval), read from shared memory instead of a dependent
+  // global load (the separate cloning stage measured faster without the extra barrier)
+  constexpr int kWStage = 64;
+  __shared__ unsigned long long s_wt[FUSE ? kWStage : 1];
   __shared__ __align__(16) uint32_t s_kth8[FUSE ? 512 : 1];
   // FUSE, plain weights: activity histograms of the first three tiles the new clones
   // fall in (the rest go straight to global memory)
@@ -648,6 +653,8 @@ __global__ void __launch_bounds__(NT, FUSE ? (NCL == 1 ? POP_FUSE_MIN_BLOCKS * 1
     }
   }
 
+  const unsigned long long* wt = B.wtab + (size_t)p * kKcap;
+  if (FUSE && tid < kWStage) s_wt[tid] = wt[tid];
   // independent loads first: activities and the old clones of this tile
   int dkv[NI];
 #pragma unroll
@@ -696,15 +703,20 @@ __global__ void __launch_bounds__(NT, FUSE ? (NCL == 1 ? POP_FUSE_MIN_BLOCKS * 1
   }
 
   // weights of this tile's clones and their scan within each warp
-  const unsigned long long* wt = B.wtab + (size_t)p * kKcap;
+  if constexpr (FUSE) __syncthreads();  // s_wt
   unsigned long long w[NI];
   unsigned long long tsum = 0ull;
 #pragma unroll
   for (int i = 0; i < NI; ++i) {
     w[i] = 0ull;
     if (j0 + i < d.nc) {
-      unsigned int k;
-      clone_weight(d, dkv[i], kref, av[i], a_ref, wt, B.exp2tab, w[i], k);
+      if (FUSE && !d.modified) {  // plain: wtab[|dK - k_ref|] (0 beyond the table: k_weights reports it)
+        const unsigned int k = abs_diff(dkv[i], kref);
+        w[i] = k < (unsigned int)kWStage ? s_wt[k] : (k < (unsigned int)kKcap ? __ldg(wt + k) : 0ull);
+      } else {
+        unsigned int k;
+        clone_weight(d, dkv[i], kref, av[i], a_ref, wt, B.exp2tab, w[i], k);
+      }
     }
     tsum += w[i];
   }
@@ -743,7 +755,55 @@ __global__ void __launch_bounds__(NT, FUSE ? (NCL == 1 ? POP_FUSE_MIN_BLOCKS * 1
 
   const uint32_t J0 = s_J[0], J1 = s_J[1];
   const bool mapped = (J1 - J0) <= (uint32_t)kMap;
-  if (mapped) {
+  if (FUSE && mapped) {
+    // the thread's old clones own the new slots [jl[0], jl[NI]): a marker at the first
+    // slot of each old clone with copies, then an inclusive max scan over the slots
+    // (markers grow with the slot, and the first slot always has one); no divergent
+    // loops, at the cost of two more barriers (the separate cloning stage, bound by
+    // memory, measured faster with the loops below)
+    constexpr int SP = kMap / NT;  // slots per thread in the scan
+    static_assert(SP % 8 == 0, "whole 16-byte words of the map per thread");
+    const int nsl = (int)(J1 - J0);
+    for (int e = tid; e < kMap / 2; e += NT) s_rng[e] = 0u;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NI; ++i)
+      if (jl[i + 1] > jl[i]) s_src[jl[i] - J0] = (uint16_t)(tid * NI + i);
+    __syncthreads();
+    uint4 pk[SP / 8];
+    int m = 0;
+#pragma unroll
+    for (int v = 0; v < SP / 8; ++v) {
+      pk[v] = reinterpret_cast<const uint4*>(s_src)[tid * (SP / 8) + v];
+      const uint32_t wd[4] = {pk[v].x, pk[v].y, pk[v].z, pk[v].w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) m = max(m, (int)max(wd[q] & 0xffffu, wd[q] >> 16));
+    }
+    int inc = m;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc = max(inc, y);
+    }
+    __shared__ int s_mx[NWARP];
+    if (lane == 31) s_mx[wid] = inc;
+    int run = __shfl_up_sync(0xffffffffu, inc, 1);
+    if (lane == 0) run = 0;
+    __syncthreads();
+    for (int q = 0; q < wid; ++q) run = max(run, s_mx[q]);
+#pragma unroll
+    for (int v = 0; v < SP / 8; ++v) {
+      uint32_t wd[4] = {pk[v].x, pk[v].y, pk[v].z, pk[v].w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        run = max(run, (int)(wd[q] & 0xffffu));
+        const uint32_t lo = (uint32_t)run;
+        run = max(run, (int)(wd[q] >> 16));
+        wd[q] = lo | ((uint32_t)run << 16);
+      }
+      if (tid * SP + 8 * v < nsl) reinterpret_cast<uint4*>(s_src)[tid * (SP / 8) + v] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+    }
+  } else if (mapped) {
     // the thread's old clones own the new slots [jl[0], jl[NI]), held in its registers
 #pragma unroll
     for (int i = 0; i < NI; ++i)
