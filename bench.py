@@ -78,10 +78,10 @@ ISSUE_OPS_PER_SM_CLK = 128                      # 4 schedulers x 32 lanes
 # of a smaller batch of the same shape scaled to a full launch: DRAM bytes (read +
 # write), issue slots busy, ALU pipe and active lanes per instruction; valid only for
 # the kernel sources they were taken on (hash of the two device headers).
-KERNEL_TRAFFIC = {"bytes_per_tile": 27045, "issue_slots_busy": 0.6357, "alu_pipe": 0.5443,
-                  "lanes_per_instruction": 28.43, "sources": "99d17913d7960d11",
+KERNEL_TRAFFIC = {"bytes_per_tile": 27086, "issue_slots_busy": 0.6520, "alu_pipe": 0.5550,
+                  "lanes_per_instruction": 28.42, "sources": "0373849f1c8587ee",
                   "captured": "one 2048-tile launch of k_gather<2, 128, FUSE> (bench.py --profile-case fused): "
-                              "51.45 MB read + 3.94 MB written"}
+                              "51.36 MB read + 4.11 MB written"}
 
 
 def kernel_sources_digest():
