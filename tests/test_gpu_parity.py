@@ -650,3 +650,11 @@ def test_an_interval_that_cannot_end_stops_at_the_step_limit(pg):
         b.events()
     assert e.value.status == pg.POP_ERR_RANGE
     b.close()
+    # the same through pop_run: the fused cloning + dynamical stage of the second
+    # interval stops at the limit too
+    b = pg.PopulationBatch([dict(L=128, N=1, n_clones=1, seed=6)])
+    b.run(1e7, [0.0], 2)
+    with pytest.raises(pg.PopError) as e:
+        b.events()
+    assert e.value.status == pg.POP_ERR_RANGE
+    b.close()
